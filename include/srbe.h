@@ -1,0 +1,158 @@
+/*
+ * srbe.h - C ABI of the GB300 (sm_103a) implementation of the symmetry-preserving
+ * random batch Ewald (SRBE) method for constant-potential electrode/electrolyte
+ * slabs (Gao, Zhou, Zhang, Xu, arXiv 2509.24742).
+ *
+ * Equation numbers count the paper's displayed equations in order: Eq. 7 the
+ * potential split, Eqs. 9-11 the neutral charge solve, Eq. 13 the real-space
+ * energy, Eq. 15 the structure factors, Eq. 17 the self/slab corrections,
+ * Eq. 18 the matrix A, Eq. 19 the vector b, Eq. 24 the SRBE vector b, Eq. 25
+ * the SRBE force, Eqs. 26-29 the sampling law and Metropolis step; Algorithm 1
+ * is the MD loop.
+ *
+ * Units: nm, ps, amu, e, kJ/mol; potentials in volts at the interface.  Arrays of
+ * vectors are row-major [n][3] doubles.  Host-pointer calls copy in and out;
+ * the context owns every device buffer.  Every call returns an srbe_status;
+ * srbe_last_error() gives the text of the last failure.  Calls made in the wrong
+ * order return SRBE_ESTATE.  A context is used by one host thread at a time.
+ */
+#ifndef SRBE_H
+#define SRBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct srbe_ctx srbe_ctx;
+
+enum srbe_status {
+  SRBE_OK = 0,
+  SRBE_EINVAL = 1,   /* bad argument (null pointer, size, non-finite value, box) */
+  SRBE_ENOMEM = 2,   /* device or host allocation failed */
+  SRBE_ECUDA = 3,    /* a CUDA call failed; the message names it */
+  SRBE_ESTATE = 4,   /* call out of order (e.g. forces before positions) */
+  SRBE_ENOTCONV = 5, /* iterative solve did not reach its tolerance */
+  SRBE_ETIMEOUT = 6  /* a bounded device wait gave up */
+};
+
+enum srbe_precision {
+  SRBE_FP64 = 0,  /* every sum, phase and pair term in FP64 */
+  SRBE_MIXED = 1  /* FP32 phases/sums/pairs with compensated accumulation; FP64 neutrality, slab, solve */
+};
+
+enum srbe_sampler {
+  SRBE_SAMPLER_METROPOLIS = 0, /* Eqs. 28-29: rounded-Gaussian proposals, Metropolis acceptance */
+  SRBE_SAMPLER_EXACT = 1       /* i.i.d. inverse-CDF draws of P(k) (Eq. 26), rejecting I u {0} */
+};
+
+/* Creates a context for a slab in the box [0,Lx) x [0,Ly) x [0,Lz), periodic in x and y,
+ * with Lz the Fourier period in z that already contains the vacuum padding (§2, the
+ * slab-correction paragraph: L_z = lambda H).
+ *   alpha      Ewald splitting parameter of Eq. 12 used for the dynamics (nm^-1)
+ *   eta        width of the Gaussian electrode charges of Eq. 1, as a LENGTH (nm)
+ *   rc         real-space cutoff (nm); every in-plane image within rc is summed
+ *   P          sampled Fourier modes per step (Eq. 26), P >= 0
+ *   kz0        M: the deterministic set I = {(0,0,2 pi m_z / Lz): 1 <= |m_z| <= M}
+ *   psi_left, psi_right  electrode potentials (V); only dpsi = psi_right - psi_left enters
+ *              (Eqs. 9-11, d = -1/2 on the left electrode, +1/2 on the right, Eq. 7)
+ * Errors: SRBE_EINVAL for a non-positive box/alpha/eta/rc or negative P/kz0. */
+int srbe_create(const double box[3], double alpha, double eta, double rc, int P, int kz0,
+                double psi_left, double psi_right, srbe_ctx **out);
+
+/* Releases every device and host resource of the context. NULL is accepted. */
+int srbe_destroy(srbe_ctx *ctx);
+
+/* Text of the last error on this context (never NULL; "" when none). */
+const char *srbe_last_error(const srbe_ctx *ctx);
+
+/* Runs the context's work on this CUDA stream (a cudaStream_t passed as void*; NULL = the
+ * context's own stream).  The caller keeps ownership of the stream. */
+int srbe_set_stream(srbe_ctx *ctx, void *stream);
+
+/* Chooses the arithmetic of the hot path (enum srbe_precision). */
+int srbe_set_precision(srbe_ctx *ctx, int mode);
+
+/* Parameters of the one-time build of A (Eq. 18): A is independent of its Ewald parameter
+ * up to the pi/(V alpha_A^2) e e^T background constant, which drops out under e^T Q = 0, so
+ * it is built with its own alpha_A (<= 0: chosen automatically, never below 6.5 / (Lz - H)
+ * so that the in-plane-only real-space sum stays exact) and truncated where
+ * exp(-k^2/4 alpha_A^2) and erfc(alpha_A r) fall below tol (<= 0: 1e-17). */
+int srbe_set_A_params(srbe_ctx *ctx, double alpha_A, double tol);
+
+/* Fixes the electrode: n_ele sites R [n_ele][3] and their side (0 = left, 1 = right).
+ * Builds A (Eq. 18, slab term (4 pi / V) Z_i Z_j), inverts it on the GPU, and stores the
+ * projected inverse J A^-1 (Eqs. 10-11) and A^-1 e.  Cost is paid once (§2: A is constant).
+ * Errors: SRBE_EINVAL (n_ele < 2, a side other than 0/1, one side empty, non-finite R),
+ * SRBE_ENOTCONV if A is not positive definite. */
+int srbe_set_electrode(srbe_ctx *ctx, int64_t n_ele, const double *R, const int8_t *side);
+
+/* Sets the n_ion electrolyte positions r [n_ion][3] (nm) and charges q (e).  n_ion may be 0.
+ * Positions outside [0,L) in x or y are wrapped.  Errors: SRBE_EINVAL on non-finite input. */
+int srbe_set_positions(srbe_ctx *ctx, int64_t n_ion, const double *r, const double *q);
+
+/* Copies the current ion positions and velocities out (either pointer may be NULL). */
+int srbe_get_positions(srbe_ctx *ctx, double *r, double *v);
+
+/* MD support terms for srbe_step: masses (amu), velocities (nm/ps, may be NULL = 0), a site
+ * type per ion (0..ntype-2; type ntype-1 is the electrode), a molecule id per ion (LJ is
+ * excluded inside a molecule), ntype x ntype LJ sigma (nm) and epsilon (kJ/mol) tables,
+ * nb harmonic bonds (pairs of ion indices, rest lengths r0, force constant kb) and the time
+ * step dt (ps).  Must follow srbe_set_positions with the same n_ion. */
+int srbe_set_md(srbe_ctx *ctx, const double *mass, const double *v, int ntype, const int32_t *itype,
+                const int32_t *mol, const double *lj_sigma, const double *lj_eps, int64_t nb,
+                const int32_t *bonds, const double *r0, double kb, double dt);
+
+/* Chooses the sampler (enum srbe_sampler) and an optional truncation box |m_d| <= mmax[d]
+ * for the sampled modes (mmax NULL or entries <= 0: the whole lattice L_k \ I). */
+int srbe_set_sampler(srbe_ctx *ctx, int kind, const int32_t *mmax);
+
+/* Draws the P modes of one step from P(k) = exp(-k^2/4 alpha^2)/G on L_k \ I (Eqs. 26-29) on
+ * the host with a Philox4x64-10 stream keyed by seed and indexed by step, and computes G
+ * (Eq. 27).  The same (seed, step) always gives the same list. */
+int srbe_sample_k(srbe_ctx *ctx, uint64_t seed, uint64_t step);
+
+/* Copies out the current sampled modes (m [P][3] integers, k = 2 pi m / L) and G. */
+int srbe_get_k(const srbe_ctx *ctx, int32_t *m, double *G);
+
+/* Sets the P sampled modes explicitly (m [P][3]); weights follow Eq. 24/25 with the
+ * context's G.  P may differ from srbe_create's.  Errors: SRBE_EINVAL for a mode in I u {0}. */
+int srbe_set_k(srbe_ctx *ctx, const int32_t *m, int P);
+
+/* Replaces the whole mode list by an explicit deterministic list m [K][3] with per-mode
+ * weights w [K] (the factor c_k multiplying Re/Im terms in Eqs. 20-21; for full Ewald
+ * w = 4 pi exp(-k^2/4 alpha^2) / (V k^2)).  Used to evaluate full Ewald on the same path. */
+int srbe_set_mode_list(srbe_ctx *ctx, const int32_t *m, const double *w, int K);
+
+/* Electrode-charge update of Algorithm 1 ("compute b, update Q"): S1 (Eq. 15), b (Eq. 24 with
+ * the near and slab parts of Eq. 19), then psi_bar and Q (Eqs. 9-10).  Outputs (host, any
+ * may be NULL): Q [n_ele] (e), psi_bar (V), b [n_ele] (V).  Needs electrode, positions, modes. */
+int srbe_solve_electrode_charges(srbe_ctx *ctx, double *Q, double *psi_bar, double *b);
+
+/* One force evaluation: the charge update above, then S2, the SRBE k-space force (Eq. 25),
+ * the slab force -(4 pi / V) q_i M_z, the real-space Coulomb forces of Eq. 13 and, after
+ * srbe_set_md, LJ and bond forces.  Outputs (host, any may be NULL): F [n_ion][3] (kJ/mol/nm),
+ * Q [n_ele] (e), psi_bar (V), energy[8] (kJ/mol): U_N ion-ion, U_N ion-electrode, U_N
+ * electrode-electrode (within rc), U_F (1/2 sum_k c_k |S|^2), U_self, U_slab, U_LJ, U_bond. */
+int srbe_forces(srbe_ctx *ctx, double *F, double *Q, double *psi_bar, double *energy);
+
+/* Algorithm 1 for nsteps velocity-Verlet steps of dt: per step, draw the P modes with
+ * srbe_sample_k(seed0, step_counter++), update Q, compute forces, integrate.  Electrode
+ * sites stay fixed, ions wrap in x and y.  State stays on the device. */
+int srbe_step(srbe_ctx *ctx, int nsteps, uint64_t seed0);
+
+/* Device-resident variants: same as the host calls, with device pointers on the context's
+ * stream and no host copies.  F_dev [n_ion*3], Q_dev [n_ele] may be NULL. */
+int srbe_set_positions_dev(srbe_ctx *ctx, int64_t n_ion, const double *r_dev, const double *q_dev);
+int srbe_forces_dev(srbe_ctx *ctx, double *F_dev, double *Q_dev);
+
+/* Counters for benchmarking: kernels launched by this context since creation, and the
+ * k-space work units (particle x mode evaluations) of the last force evaluation. */
+int srbe_get_counters(const srbe_ctx *ctx, int64_t *kernel_launches, int64_t *mode_evals);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SRBE_H */

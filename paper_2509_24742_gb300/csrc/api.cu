@@ -1,0 +1,820 @@
+// C ABI of the SRBE library (declared in include/srbe.h): argument checks, host-side mode
+// sampling (Eqs. 26-29), mode weights (Eqs. 24-25), the normalisation G (Eq. 27), staging of
+// host arrays, and the order of the device passes of Algorithm 1.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "srbe_internal.cuh"
+
+namespace srbe {
+
+constexpr double kVolt = 0.694461;   // 1 V as a Coulomb potential in e/nm (96.4853 / 138.935458)
+constexpr double kKeHost = 138.935458;
+
+// ------------------------------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11)
+// ------------------------------------------------------------------------------------------------
+struct Philox4x64 {
+  static void mul(uint64_t a, uint64_t b, uint64_t &hi, uint64_t &lo) {
+    const unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    hi = (uint64_t)(p >> 64);
+    lo = (uint64_t)p;
+  }
+  static void block(const uint64_t in[4], uint64_t k0, uint64_t k1, uint64_t out[4]) {
+    uint64_t x0 = in[0], x1 = in[1], x2 = in[2], x3 = in[3];
+    for (int r = 0; r < 10; ++r) {
+      uint64_t hA, lA, hB, lB;
+      mul(0xD2E7470EE14C6C93ull, x0, hA, lA);
+      mul(0xCA5A826395121157ull, x2, hB, lB);
+      const uint64_t y0 = hB ^ x1 ^ k0, y2 = hA ^ x3 ^ k1;
+      x0 = y0;
+      x1 = lB;
+      x2 = y2;
+      x3 = lA;
+      k0 += 0x9E3779B97F4A7C15ull;   // key schedule: Weyl increments between rounds
+      k1 += 0xBB67AE8584CAA73Bull;
+    }
+    out[0] = x0;
+    out[1] = x1;
+    out[2] = x2;
+    out[3] = x3;
+  }
+};
+
+inline double unit_open0(uint64_t w) { return ((double)(w >> 11) + 1.0) * (1.0 / 9007199254740992.0); }
+
+// The sampling law of Eq. 26 factorises: exp(-k^2/4a^2) = prod_d exp(-pi^2 m_d^2 / (a L_d)^2), a discrete
+// Gaussian per dimension of width sigma_d = a L_d / (sqrt 2 pi).
+struct ModeSampler {
+  double L[3], alpha;
+  int M;
+  int32_t box[3];
+  double sig[3];
+  int tabhalf[3];
+  std::vector<double> qtab[3];   // q_d(m) of Eq. 28 for |m| <= tabhalf
+
+  void init(const double Lb[3], double a, int Mdet, const int32_t mmax[3]) {
+    alpha = a;
+    M = Mdet;
+    for (int d = 0; d < 3; ++d) {
+      L[d] = Lb[d];
+      box[d] = mmax[d];
+      sig[d] = alpha * L[d] / (std::sqrt(2.0) * kPi);
+      tabhalf[d] = (int)std::ceil(12.0 * sig[d]) + 2;
+      qtab[d].resize(2 * tabhalf[d] + 1);
+      for (int m = -tabhalf[d]; m <= tabhalf[d]; ++m) qtab[d][m + tabhalf[d]] = qd_direct(m, d);
+    }
+  }
+  double qd_direct(int32_t m, int d) const {
+    const double s = std::sqrt(2.0) * sig[d];
+    return 0.5 * (std::erf((m + 0.5) / s) - std::erf((m - 0.5) / s));
+  }
+  double qd(int32_t m, int d) const {
+    return (m >= -tabhalf[d] && m <= tabhalf[d]) ? qtab[d][m + tabhalf[d]] : qd_direct(m, d);
+  }
+  bool rejected(const int32_t m[3]) const {
+    for (int d = 0; d < 3; ++d)
+      if (box[d] > 0 && std::abs(m[d]) > box[d]) return true;
+    return m[0] == 0 && m[1] == 0 && std::abs(m[2]) <= M;
+  }
+  double target(const int32_t m[3]) const {
+    double k2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double kd = 2.0 * kPi * m[d] / L[d];
+      k2 += kd * kd;
+    }
+    return std::exp(-k2 / (4.0 * alpha * alpha));
+  }
+  // proposal j of step `step`: three rounded normals and the acceptance uniform
+  void proposal(uint64_t seed, uint64_t step, uint64_t j, int32_t m[3], double &u) const {
+    const uint64_t c0[4] = {2 * j, step, 0, 0}, c1[4] = {2 * j + 1, step, 0, 0};
+    uint64_t w0[4], w1[4];
+    Philox4x64::block(c0, seed, 0x5352424500000001ull, w0);
+    Philox4x64::block(c1, seed, 0x5352424500000001ull, w1);
+    const double ra = std::sqrt(-2.0 * std::log(unit_open0(w0[0]))), ta = 2.0 * kPi * unit_open0(w0[1]);
+    const double rb = std::sqrt(-2.0 * std::log(unit_open0(w0[2]))), tb = 2.0 * kPi * unit_open0(w0[3]);
+    const double g[3] = {ra * std::cos(ta), ra * std::sin(ta), rb * std::cos(tb)};
+    for (int d = 0; d < 3; ++d) m[d] = (int32_t)std::floor(sig[d] * g[d] + 0.5);
+    u = unit_open0(w1[0]);
+  }
+  // Metropolis chain of Eq. 29 with independent proposals; first admissible proposal starts it
+  void metropolis(uint64_t seed, uint64_t step, int P, int32_t *out) const {
+    uint64_t j = 0;
+    int32_t cur[3];
+    double u;
+    do {
+      proposal(seed, step, j++, cur, u);
+    } while (rejected(cur));
+    double pc = target(cur), qc = qd(cur[0], 0) * qd(cur[1], 1) * qd(cur[2], 2);
+    for (int l = 0; l < P; ++l) {
+      if (l > 0) {
+        int32_t pr[3];
+        proposal(seed, step, j++, pr, u);
+        if (!rejected(pr)) {
+          const double pp = target(pr), qp = qd(pr[0], 0) * qd(pr[1], 1) * qd(pr[2], 2);
+          if (u <= (pp * qc) / (pc * qp)) {
+            std::memcpy(cur, pr, sizeof cur);
+            pc = pp;
+            qc = qp;
+          }
+        }
+      }
+      std::memcpy(out + 3 * l, cur, sizeof cur);
+    }
+  }
+  int32_t support(int d) const {
+    return box[d] > 0 ? box[d] : (int32_t)std::ceil(alpha * L[d] * std::sqrt(21.0 * std::log(10.0)) / kPi);
+  }
+  // exact i.i.d. draws: inverse CDF per dimension, rejection of I u {0}
+  void exact(uint64_t seed, uint64_t step, int P, int32_t *out) const {
+    std::vector<double> cdf[3];
+    int32_t sup[3];
+    for (int d = 0; d < 3; ++d) {
+      sup[d] = support(d);
+      cdf[d].resize(2 * sup[d] + 1);
+      double acc = 0.0;
+      for (int i = 0; i < 2 * sup[d] + 1; ++i) {
+        const double kd = 2.0 * kPi * (i - sup[d]) / L[d];
+        acc += std::exp(-kd * kd / (4.0 * alpha * alpha));
+        cdf[d][i] = acc;
+      }
+      for (double &v : cdf[d]) v /= acc;
+    }
+    uint64_t tries = 0;
+    for (int l = 0; l < P;) {
+      const uint64_t c[4] = {tries++, step, 1, 0};
+      uint64_t w[4];
+      Philox4x64::block(c, seed, 0x5352424500000002ull, w);
+      int32_t m[3];
+      for (int d = 0; d < 3; ++d) {
+        const double u = unit_open0(w[d]);
+        const auto it = std::lower_bound(cdf[d].begin(), cdf[d].end() - 1, u);
+        m[d] = (int32_t)(it - cdf[d].begin()) - sup[d];
+      }
+      if (rejected(m)) continue;
+      std::memcpy(out + 3 * l, m, sizeof m);
+      ++l;
+    }
+  }
+  // Eq. 27 in product form over dimensions, minus k = 0 and the 2M deterministic modes
+  double G() const {
+    double th[3];
+    for (int d = 0; d < 3; ++d) {
+      const int32_t s = support(d);
+      double acc = 0.0;
+      for (int32_t m = -s; m <= s; ++m) {
+        const double x = kPi * m / (alpha * L[d]);
+        acc += std::exp(-x * x);
+      }
+      th[d] = acc;
+    }
+    double det = 0.0;
+    const int top = box[2] > 0 ? std::min(M, (int)box[2]) : M;
+    for (int m = 1; m <= top; ++m) {
+      const double x = kPi * m / (alpha * L[2]);
+      det += std::exp(-x * x);
+    }
+    return th[0] * th[1] * th[2] - 1.0 - 2.0 * det;
+  }
+};
+
+}  // namespace srbe
+
+using namespace srbe;
+
+namespace {
+
+int fail(srbe_ctx *c, const Error &e) {
+  if (c) c->err = e.msg;
+  return e.code;
+}
+
+template <class Fn>
+int guarded(srbe_ctx *c, Fn &&fn) {
+  if (!c) return SRBE_EINVAL;
+  try {
+    c->err.clear();
+    fn();
+    return SRBE_OK;
+  } catch (const Error &e) {
+    return fail(c, e);
+  } catch (const std::bad_alloc &) {
+    return fail(c, Error{SRBE_ENOMEM, "host allocation failed"});
+  } catch (const std::exception &e) {
+    return fail(c, Error{SRBE_EINVAL, e.what()});
+  }
+}
+
+bool finite_all(const double *a, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+// ---- staging kernels
+__global__ void k_deinterleave(int64_t n, const double *__restrict__ r, double Lx, double Ly, double *__restrict__ x,
+                               double *__restrict__ y, double *__restrict__ z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double X = r[3 * i], Y = r[3 * i + 1];
+  X -= Lx * floor(X / Lx);
+  Y -= Ly * floor(Y / Ly);
+  if (X >= Lx) X -= Lx;
+  if (Y >= Ly) Y -= Ly;
+  x[i] = X;
+  y[i] = Y;
+  z[i] = r[3 * i + 2];
+}
+
+__global__ void k_interleave(int64_t n, const double *__restrict__ F, double *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[3 * i] = F[i];
+  out[3 * i + 1] = F[n + i];
+  out[3 * i + 2] = F[2 * n + i];
+}
+
+__global__ void k_interleave3(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                              const double *__restrict__ z, double *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[3 * i] = x[i];
+  out[3 * i + 1] = y[i];
+  out[3 * i + 2] = z[i];
+}
+
+}  // namespace
+
+// per-context host state that the kernels never see
+struct srbe::HostExt {
+  ModeSampler sampler;
+  DevBuf<double> aos;      // AoS staging for positions / forces
+  bool forces_valid = false;
+};
+
+namespace {
+using Extra = srbe::HostExt;
+Extra *extra(srbe_ctx *c) { return c->hx; }
+}  // namespace
+
+namespace srbe {
+
+void upload_table(srbe_ctx *c) {
+  std::vector<double2> h(kTab);
+  for (int j = 0; j < kTab; ++j) {
+    const long double a = 2.0L * 3.141592653589793238462643383279502884L * (long double)j / (long double)kTab;
+    h[j] = make_double2((double)cosl(a), (double)sinl(a));
+  }
+  c->tab.ensure(kTab);
+  SRBE_CUDA(cudaMemcpyAsync(c->tab.p, h.data(), sizeof(double2) * kTab, cudaMemcpyHostToDevice, c->stream));
+  SRBE_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void reserve(srbe_ctx *c) {
+  const int K = std::max(c->K, 1);
+  int64_t ch;
+  const int64_t nch = std::max(sfac_chunks(c->ni, c->K, &ch), sfac_chunks(c->ne, c->K, &ch));
+  c->partial.ensure((size_t)std::max<int64_t>(nch, 1) * K);
+  c->mpart.ensure((size_t)std::max<int64_t>(nch, 1));
+  c->coef.ensure((size_t)K);
+  const size_t nblk = blocks_for(std::max<int64_t>(c->ni, 1), 128);
+  const size_t neb = blocks_for(std::max<int64_t>(c->ne, 1), 128);
+  c->epart.ensure(nblk * 4 + 4 + neb + 8);
+  c->scal.ensure(kScalCount);
+}
+
+}  // namespace srbe
+
+namespace {
+
+void upload_modes(srbe_ctx *c) {
+  const int K = (int)c->hc.size();
+  if ((size_t)K > c->stage_cap) {
+    if (c->h_mode_stage) cudaFreeHost(c->h_mode_stage);
+    if (c->h_w_stage) cudaFreeHost(c->h_w_stage);
+    c->h_mode_stage = nullptr;
+    c->h_w_stage = nullptr;
+    SRBE_CUDA(cudaMallocHost((void **)&c->h_mode_stage, sizeof(int4) * std::max(K, 1)));
+    SRBE_CUDA(cudaMallocHost((void **)&c->h_w_stage, sizeof(double) * std::max(K, 1)));
+    c->stage_cap = (size_t)K;
+  }
+  // the previous copy out of the pinned buffer must have finished before it is overwritten
+  SRBE_CUDA(cudaEventSynchronize(c->stage_done));
+  for (int k = 0; k < K; ++k) {
+    c->h_mode_stage[k] = make_int4(c->hm[4 * k], c->hm[4 * k + 1], c->hm[4 * k + 2], 0);
+    c->h_w_stage[k] = c->hc[k];
+  }
+  c->dm.ensure(std::max(K, 1));
+  c->dc.ensure(std::max(K, 1));
+  c->S1.ensure(std::max(K, 1));
+  c->S2.ensure(std::max(K, 1));
+  if (K > 0) {
+    SRBE_CUDA(cudaMemcpyAsync(c->dm.p, c->h_mode_stage, sizeof(int4) * K, cudaMemcpyHostToDevice, c->stream));
+    SRBE_CUDA(cudaMemcpyAsync(c->dc.p, c->h_w_stage, sizeof(double) * K, cudaMemcpyHostToDevice, c->stream));
+  }
+  SRBE_CUDA(cudaEventRecord(c->stage_done, c->stream));
+  c->K = K;
+  c->have_modes = true;
+}
+
+// SRBE mode list (Eqs. 24-25): I folded to +m_z with twice the Ewald weight, then the samples with
+// (G / P) 4 pi / (V k^2)
+void srbe_list_from_samples(srbe_ctx *c, const int32_t *samp, int P) {
+  c->hm.clear();
+  c->hc.clear();
+  const double V = c->V;
+  for (int mz = 1; mz <= c->M; ++mz) {
+    const double kz = 2.0 * kPi * mz / c->L[2];
+    const double k2 = kz * kz;
+    c->hm.insert(c->hm.end(), {0, 0, mz, 0});
+    c->hc.push_back(2.0 * 4.0 * kPi / (V * k2) * std::exp(-k2 / (4.0 * c->alpha * c->alpha)));
+  }
+  c->Kdet = c->M;
+  for (int l = 0; l < P; ++l) {
+    const int32_t *m = samp + 3 * l;
+    double k2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double kd = 2.0 * kPi * m[d] / c->L[d];
+      k2 += kd * kd;
+    }
+    c->hm.insert(c->hm.end(), {m[0], m[1], m[2], 0});
+    c->hc.push_back((c->G / P) * 4.0 * kPi / (V * k2));
+  }
+  c->hsamp.assign(samp, samp + 3 * P);
+  c->explicit_list = false;
+  upload_modes(c);
+}
+
+void require_state(srbe_ctx *c, bool pos) {
+  SRBE_REQUIRE(c->have_ele, SRBE_ESTATE, "srbe_set_electrode has not been called");
+  if (pos) SRBE_REQUIRE(c->have_pos, SRBE_ESTATE, "srbe_set_positions has not been called");
+  SRBE_REQUIRE(c->have_modes, SRBE_ESTATE, "no mode list: call srbe_sample_k, srbe_set_k or srbe_set_mode_list");
+}
+
+void charges_pass(srbe_ctx *c) {
+  reserve(c);
+  build_cells(c, c->icells, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->have_md ? c->itype.p : nullptr,
+              c->have_md ? c->mol.p : nullptr, true);
+  structure_factor(c, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->S1.p, nullptr, kScalMion);
+  electrode_rhs(c);
+  charge_update(c);
+}
+
+void forces_pass(srbe_ctx *c, bool energies) {
+  charges_pass(c);
+  structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele);
+  ion_forces(c, energies);
+  if (energies) energy_scalars(c);
+}
+
+void sample_into(srbe_ctx *c, uint64_t seed, uint64_t step) {
+  Extra *e = extra(c);
+  std::vector<int32_t> s((size_t)3 * c->P);
+  if (c->sampler == SRBE_SAMPLER_EXACT) e->sampler.exact(seed, step, c->P, s.data());
+  else e->sampler.metropolis(seed, step, c->P, s.data());
+  srbe_list_from_samples(c, s.data(), c->P);
+}
+
+void download_outputs(srbe_ctx *c, double *F, double *Q, double *psi, double *energy, double *b) {
+  Extra *e = extra(c);
+  if (F && c->ni > 0) {
+    double *aos = e->aos.ensure((size_t)3 * c->ni);
+    k_interleave<<<blocks_for(c->ni, 256), 256, 0, c->stream>>>(c->ni, c->F.p, aos);
+    c->launches++;
+    SRBE_CUDA(cudaGetLastError());
+    SRBE_CUDA(cudaMemcpyAsync(F, aos, sizeof(double) * 3 * c->ni, cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (Q) SRBE_CUDA(cudaMemcpyAsync(Q, c->Q.p, sizeof(double) * c->ne, cudaMemcpyDeviceToHost, c->stream));
+  if (b) SRBE_CUDA(cudaMemcpyAsync(b, c->bvec.p, sizeof(double) * c->ne, cudaMemcpyDeviceToHost, c->stream));
+  SRBE_CUDA(cudaMemcpyAsync(c->h_scal, c->scal.p, sizeof(double) * kScalCount, cudaMemcpyDeviceToHost, c->stream));
+  SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  if (b)
+    for (int64_t j = 0; j < c->ne; ++j) b[j] /= kVolt;
+  if (psi) *psi = c->h_scal[kScalPsi] / kVolt;
+  if (energy) {
+    const double *s = c->h_scal;
+    const double Mz = s[kScalMion] + s[kScalMele];
+    const double self = (1.0 / (std::sqrt(2.0 * kPi) * c->eta) - c->alpha / std::sqrt(kPi)) * s[kScalQ2] -
+                        c->alpha / std::sqrt(kPi) * s[kScalq2];
+    energy[0] = kKeHost * s[kScalEii];
+    energy[1] = kKeHost * s[kScalEie];
+    energy[2] = kKeHost * s[kScalEee];
+    energy[3] = kKeHost * s[kScalUF];
+    energy[4] = kKeHost * self;
+    energy[5] = kKeHost * 2.0 * kPi / c->V * Mz * Mz;
+    energy[6] = s[kScalElj];
+    energy[7] = s[kScalEbond];
+  }
+}
+
+}  // namespace
+
+// ================================================================================================
+// C ABI
+// ================================================================================================
+extern "C" {
+
+int srbe_create(const double box[3], double alpha, double eta, double rc, int P, int kz0, double psi_left,
+                double psi_right, srbe_ctx **out) {
+  if (!out) return SRBE_EINVAL;
+  *out = nullptr;
+  if (!box || !(box[0] > 0) || !(box[1] > 0) || !(box[2] > 0) || !std::isfinite(box[0]) || !std::isfinite(box[1]) ||
+      !std::isfinite(box[2]) || !(alpha > 0) || !(eta > 0) || !(rc > 0) || P < 0 || kz0 < 0 ||
+      !std::isfinite(psi_left) || !std::isfinite(psi_right) || !std::isfinite(alpha) || !std::isfinite(eta) ||
+      !std::isfinite(rc))
+    return SRBE_EINVAL;
+  srbe_ctx *c = new (std::nothrow) srbe_ctx();
+  if (!c) return SRBE_ENOMEM;
+  c->hx = new (std::nothrow) srbe::HostExt();
+  if (!c->hx) {
+    delete c;
+    return SRBE_ENOMEM;
+  }
+  for (int d = 0; d < 3; ++d) c->L[d] = box[d];
+  c->V = box[0] * box[1] * box[2];
+  c->alpha = alpha;
+  c->eta = eta;
+  c->rc = rc;
+  c->P = P;
+  c->M = kz0;
+  c->psi_left = psi_left;
+  c->psi_right = psi_right;
+  c->dpsi = (psi_right - psi_left) * kVolt;
+  int rcode = guarded(c, [&] {
+    SRBE_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+    SRBE_CUDA(cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming));
+    SRBE_CUDA(cudaEventRecord(c->stage_done, c->stream));
+    upload_table(c);
+    c->scal.ensure(kScalCount);
+    SRBE_CUDA(cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScalCount, c->stream));
+    c->hx->sampler.init(c->L, c->alpha, c->M, c->mmax);
+    c->G = c->hx->sampler.G();
+  });
+  if (rcode != SRBE_OK) {
+    srbe_destroy(c);
+    return rcode;
+  }
+  *out = c;
+  return SRBE_OK;
+}
+
+int srbe_destroy(srbe_ctx *c) {
+  if (!c) return SRBE_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->h_mode_stage) cudaFreeHost(c->h_mode_stage);
+  if (c->h_w_stage) cudaFreeHost(c->h_w_stage);
+  if (c->stage_done) cudaEventDestroy(c->stage_done);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  c->stream = nullptr;
+  delete c->hx;
+  c->hx = nullptr;
+  delete c;
+  return SRBE_OK;
+}
+
+const char *srbe_last_error(const srbe_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int srbe_set_stream(srbe_ctx *c, void *stream) {
+  return guarded(c, [&] {
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    if (stream) {
+      if (c->own_stream) SRBE_CUDA(cudaStreamDestroy(c->stream));
+      c->stream = (cudaStream_t)stream;
+      c->own_stream = false;
+    } else if (!c->own_stream) {
+      SRBE_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    SRBE_CUDA(cudaEventRecord(c->stage_done, c->stream));
+  });
+}
+
+int srbe_set_precision(srbe_ctx *c, int mode) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(mode == SRBE_FP64 || mode == SRBE_MIXED, SRBE_EINVAL, "unknown precision mode");
+    c->precision = mode;
+  });
+}
+
+int srbe_set_A_params(srbe_ctx *c, double alpha_A, double tol) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(std::isfinite(alpha_A) && std::isfinite(tol) && tol < 1.0, SRBE_EINVAL, "bad A parameters");
+    SRBE_REQUIRE(!c->have_ele, SRBE_ESTATE, "A parameters must be set before srbe_set_electrode");
+    c->alpha_A = alpha_A;
+    c->tol_A = tol;
+  });
+}
+
+int srbe_set_electrode(srbe_ctx *c, int64_t n_ele, const double *R, const int8_t *side) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(R && side && n_ele >= 2, SRBE_EINVAL, "need at least two electrode sites");
+    SRBE_REQUIRE(n_ele <= 65535, SRBE_EINVAL, "at most 65535 electrode sites are supported");
+    SRBE_REQUIRE(finite_all(R, 3 * n_ele), SRBE_EINVAL, "non-finite electrode position");
+    int64_t nl = 0, nr = 0;
+    for (int64_t j = 0; j < n_ele; ++j) {
+      SRBE_REQUIRE(side[j] == 0 || side[j] == 1, SRBE_EINVAL, "side must be 0 (left) or 1 (right)");
+      (side[j] ? nr : nl)++;
+    }
+    SRBE_REQUIRE(nl > 0 && nr > 0, SRBE_EINVAL, "both electrodes need at least one site");
+    c->ne = n_ele;
+    c->hR.assign(R, R + 3 * n_ele);
+    c->hside.assign(side, side + n_ele);
+    std::vector<double> x(n_ele), y(n_ele), z(n_ele), d(n_ele);
+    for (int64_t j = 0; j < n_ele; ++j) {
+      double X = R[3 * j], Y = R[3 * j + 1];
+      X -= c->L[0] * std::floor(X / c->L[0]);
+      Y -= c->L[1] * std::floor(Y / c->L[1]);
+      if (X >= c->L[0]) X -= c->L[0];
+      if (Y >= c->L[1]) Y -= c->L[1];
+      x[j] = X;
+      y[j] = Y;
+      z[j] = R[3 * j + 2];
+      d[j] = side[j] ? 0.5 : -0.5;
+    }
+    c->ex.ensure(n_ele);
+    c->ey.ensure(n_ele);
+    c->ez.ensure(n_ele);
+    c->ed.ensure(n_ele);
+    c->Q.ensure(n_ele);
+    c->bvec.ensure(n_ele);
+    SRBE_CUDA(cudaMemcpyAsync(c->ex.p, x.data(), sizeof(double) * n_ele, cudaMemcpyHostToDevice, c->stream));
+    SRBE_CUDA(cudaMemcpyAsync(c->ey.p, y.data(), sizeof(double) * n_ele, cudaMemcpyHostToDevice, c->stream));
+    SRBE_CUDA(cudaMemcpyAsync(c->ez.p, z.data(), sizeof(double) * n_ele, cudaMemcpyHostToDevice, c->stream));
+    SRBE_CUDA(cudaMemcpyAsync(c->ed.p, d.data(), sizeof(double) * n_ele, cudaMemcpyHostToDevice, c->stream));
+    SRBE_CUDA(cudaMemsetAsync(c->Q.p, 0, sizeof(double) * n_ele, c->stream));
+    // one cell grid for ions and electrode sites: the whole periodic length in z, centred on the walls
+    const double zmin = *std::min_element(z.begin(), z.end()), zmax = *std::max_element(z.begin(), z.end());
+    const double pad = 0.5 * (c->L[2] - (zmax - zmin));
+    choose_grid(c, c->ecells.g, zmin - pad, zmax + pad);
+    c->icells.g = c->ecells.g;
+    build_cells(c, c->ecells, n_ele, c->ex.p, c->ey.p, c->ez.p, nullptr, nullptr, nullptr, false);
+    build_A_and_inverse(c);
+    c->have_ele = true;
+    extra(c)->forces_valid = false;
+  });
+}
+
+int srbe_set_positions(srbe_ctx *c, int64_t n_ion, const double *r, const double *q) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(n_ion >= 0 && (n_ion == 0 || (r && q)), SRBE_EINVAL, "null positions or charges");
+    SRBE_REQUIRE(n_ion < (1ll << 31), SRBE_EINVAL, "too many ions");
+    SRBE_REQUIRE(finite_all(r, 3 * n_ion) && finite_all(q, n_ion), SRBE_EINVAL, "non-finite ion position or charge");
+    if (c->have_md && n_ion != c->ni) c->have_md = false;
+    c->ni = n_ion;
+    const size_t n = (size_t)std::max<int64_t>(n_ion, 1);
+    c->x.ensure(n);
+    c->y.ensure(n);
+    c->z.ensure(n);
+    c->q.ensure(n);
+    c->F.ensure(3 * n);
+    Extra *e = extra(c);
+    if (n_ion > 0) {
+      double *aos = e->aos.ensure(3 * n);
+      SRBE_CUDA(cudaMemcpyAsync(aos, r, sizeof(double) * 3 * n_ion, cudaMemcpyHostToDevice, c->stream));
+      SRBE_CUDA(cudaMemcpyAsync(c->q.p, q, sizeof(double) * n_ion, cudaMemcpyHostToDevice, c->stream));
+      k_deinterleave<<<blocks_for(n_ion, 256), 256, 0, c->stream>>>(n_ion, aos, c->L[0], c->L[1], c->x.p, c->y.p,
+                                                                   c->z.p);
+      c->launches++;
+      SRBE_CUDA(cudaGetLastError());
+    }
+    c->have_pos = true;
+    e->forces_valid = false;
+  });
+}
+
+int srbe_set_positions_dev(srbe_ctx *c, int64_t n_ion, const double *r_dev, const double *q_dev) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(n_ion >= 0 && (n_ion == 0 || (r_dev && q_dev)), SRBE_EINVAL, "null positions or charges");
+    if (c->have_md && n_ion != c->ni) c->have_md = false;
+    c->ni = n_ion;
+    const size_t n = (size_t)std::max<int64_t>(n_ion, 1);
+    c->x.ensure(n);
+    c->y.ensure(n);
+    c->z.ensure(n);
+    c->q.ensure(n);
+    c->F.ensure(3 * n);
+    if (n_ion > 0) {
+      SRBE_CUDA(cudaMemcpyAsync(c->q.p, q_dev, sizeof(double) * n_ion, cudaMemcpyDeviceToDevice, c->stream));
+      k_deinterleave<<<blocks_for(n_ion, 256), 256, 0, c->stream>>>(n_ion, r_dev, c->L[0], c->L[1], c->x.p, c->y.p,
+                                                                   c->z.p);
+      c->launches++;
+      SRBE_CUDA(cudaGetLastError());
+    }
+    c->have_pos = true;
+    extra(c)->forces_valid = false;
+  });
+}
+
+int srbe_get_positions(srbe_ctx *c, double *r, double *v) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(c->have_pos, SRBE_ESTATE, "no positions");
+    if (c->ni == 0) return;
+    double *aos = extra(c)->aos.ensure((size_t)3 * c->ni);
+    if (r) {
+      k_interleave3<<<blocks_for(c->ni, 256), 256, 0, c->stream>>>(c->ni, c->x.p, c->y.p, c->z.p, aos);
+      SRBE_CUDA(cudaMemcpyAsync(r, aos, sizeof(double) * 3 * c->ni, cudaMemcpyDeviceToHost, c->stream));
+      SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    if (v) {
+      SRBE_REQUIRE(c->have_md, SRBE_ESTATE, "no velocities (srbe_set_md)");
+      k_interleave3<<<blocks_for(c->ni, 256), 256, 0, c->stream>>>(c->ni, c->vx.p, c->vy.p, c->vz.p, aos);
+      SRBE_CUDA(cudaMemcpyAsync(v, aos, sizeof(double) * 3 * c->ni, cudaMemcpyDeviceToHost, c->stream));
+      SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    }
+  });
+}
+
+int srbe_set_md(srbe_ctx *c, const double *mass, const double *v, int ntype, const int32_t *itype,
+                const int32_t *mol, const double *lj_sigma, const double *lj_eps, int64_t nb, const int32_t *bonds,
+                const double *r0, double kb, double dt) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(c->have_pos, SRBE_ESTATE, "srbe_set_md needs srbe_set_positions first");
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    const int64_t n = c->ni;
+    SRBE_REQUIRE(n == 0 || (mass && itype && mol), SRBE_EINVAL, "null mass / type / molecule array");
+    SRBE_REQUIRE(ntype >= 1 && ntype <= 64 && lj_sigma && lj_eps, SRBE_EINVAL, "bad LJ tables");
+    SRBE_REQUIRE(nb >= 0 && (nb == 0 || (bonds && r0)), SRBE_EINVAL, "bad bond list");
+    SRBE_REQUIRE(dt > 0 && std::isfinite(dt) && std::isfinite(kb), SRBE_EINVAL, "bad dt or kb");
+    std::vector<double> minv(n), lj(2 * ntype * ntype);
+    for (int64_t i = 0; i < n; ++i) {
+      SRBE_REQUIRE(mass[i] > 0 && std::isfinite(mass[i]), SRBE_EINVAL, "masses must be positive");
+      SRBE_REQUIRE(itype[i] >= 0 && itype[i] < ntype - 1, SRBE_EINVAL, "ion type out of range");
+      minv[i] = 1.0 / mass[i];
+    }
+    for (int a = 0; a < ntype * ntype; ++a) {
+      lj[2 * a] = lj_sigma[a] * lj_sigma[a];
+      lj[2 * a + 1] = lj_eps[a];
+    }
+    // bonds as a CSR list per ion (each bond stored from both ends)
+    std::vector<int32_t> start(n + 1, 0), bj(2 * nb);
+    std::vector<double> br(2 * nb);
+    for (int64_t b = 0; b < nb; ++b) {
+      SRBE_REQUIRE(bonds[2 * b] >= 0 && bonds[2 * b] < n && bonds[2 * b + 1] >= 0 && bonds[2 * b + 1] < n &&
+                       bonds[2 * b] != bonds[2 * b + 1],
+                   SRBE_EINVAL, "bond index out of range");
+      start[bonds[2 * b] + 1]++;
+      start[bonds[2 * b + 1] + 1]++;
+    }
+    for (int64_t i = 0; i < n; ++i) start[i + 1] += start[i];
+    std::vector<int32_t> fill(start.begin(), start.end() - 1);
+    for (int64_t b = 0; b < nb; ++b) {
+      const int32_t i = bonds[2 * b], j = bonds[2 * b + 1];
+      bj[fill[i]] = j;
+      br[fill[i]++] = r0[b];
+      bj[fill[j]] = i;
+      br[fill[j]++] = r0[b];
+    }
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    c->vx.ensure(nn);
+    c->vy.ensure(nn);
+    c->vz.ensure(nn);
+    c->minv.ensure(nn);
+    c->itype.ensure(nn);
+    c->mol.ensure(nn);
+    c->lj.ensure(lj.size());
+    c->bond_start.ensure(n + 1);
+    c->bond_j.ensure(std::max<int64_t>(2 * nb, 1));
+    c->bond_r0.ensure(std::max<int64_t>(2 * nb, 1));
+    if (n > 0) {
+      std::vector<double> vx(n, 0.0), vy(n, 0.0), vz(n, 0.0);
+      if (v)
+        for (int64_t i = 0; i < n; ++i) {
+          vx[i] = v[3 * i];
+          vy[i] = v[3 * i + 1];
+          vz[i] = v[3 * i + 2];
+        }
+      SRBE_CUDA(cudaMemcpy(c->vx.p, vx.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+      SRBE_CUDA(cudaMemcpy(c->vy.p, vy.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+      SRBE_CUDA(cudaMemcpy(c->vz.p, vz.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+      SRBE_CUDA(cudaMemcpy(c->minv.p, minv.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+      SRBE_CUDA(cudaMemcpy(c->itype.p, itype, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+      SRBE_CUDA(cudaMemcpy(c->mol.p, mol, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    }
+    SRBE_CUDA(cudaMemcpy(c->lj.p, lj.data(), sizeof(double) * lj.size(), cudaMemcpyHostToDevice));
+    SRBE_CUDA(cudaMemcpy(c->bond_start.p, start.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+    if (nb > 0) {
+      SRBE_CUDA(cudaMemcpy(c->bond_j.p, bj.data(), sizeof(int32_t) * 2 * nb, cudaMemcpyHostToDevice));
+      SRBE_CUDA(cudaMemcpy(c->bond_r0.p, br.data(), sizeof(double) * 2 * nb, cudaMemcpyHostToDevice));
+    }
+    c->ntype = ntype;
+    c->kb = kb;
+    c->dt = dt;
+    c->have_md = true;
+    extra(c)->forces_valid = false;
+  });
+}
+
+int srbe_set_sampler(srbe_ctx *c, int kind, const int32_t *mmax) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(kind == SRBE_SAMPLER_METROPOLIS || kind == SRBE_SAMPLER_EXACT, SRBE_EINVAL, "unknown sampler");
+    c->sampler = kind;
+    for (int d = 0; d < 3; ++d) c->mmax[d] = mmax ? std::max(mmax[d], 0) : 0;
+    Extra *e = extra(c);
+    e->sampler.init(c->L, c->alpha, c->M, c->mmax);
+    c->G = e->sampler.G();
+  });
+}
+
+int srbe_sample_k(srbe_ctx *c, uint64_t seed, uint64_t step) {
+  return guarded(c, [&] { sample_into(c, seed, step); });
+}
+
+int srbe_get_k(const srbe_ctx *cc, int32_t *m, double *G) {
+  srbe_ctx *c = const_cast<srbe_ctx *>(cc);
+  return guarded(c, [&] {
+    SRBE_REQUIRE(c->have_modes && !c->explicit_list, SRBE_ESTATE, "no sampled mode list");
+    if (m) std::memcpy(m, c->hsamp.data(), sizeof(int32_t) * c->hsamp.size());
+    if (G) *G = c->G;
+  });
+}
+
+int srbe_set_k(srbe_ctx *c, const int32_t *m, int P) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(P >= 0 && (P == 0 || m), SRBE_EINVAL, "bad sampled-mode list");
+    for (int l = 0; l < P; ++l)
+      SRBE_REQUIRE(!(m[3 * l] == 0 && m[3 * l + 1] == 0 && std::abs(m[3 * l + 2]) <= c->M), SRBE_EINVAL,
+                   "sampled mode lies in I u {0}");
+    srbe_list_from_samples(c, m, P);
+  });
+}
+
+int srbe_set_mode_list(srbe_ctx *c, const int32_t *m, const double *w, int K) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(K >= 0 && (K == 0 || (m && w)), SRBE_EINVAL, "bad mode list");
+    SRBE_REQUIRE(finite_all(w, K), SRBE_EINVAL, "non-finite mode weight");
+    c->hm.clear();
+    c->hc.assign(w, w + K);
+    for (int k = 0; k < K; ++k) {
+      SRBE_REQUIRE(m[3 * k] || m[3 * k + 1] || m[3 * k + 2], SRBE_EINVAL, "mode k = 0 is not allowed");
+      c->hm.insert(c->hm.end(), {m[3 * k], m[3 * k + 1], m[3 * k + 2], 0});
+    }
+    c->Kdet = K;
+    c->explicit_list = true;
+    upload_modes(c);
+  });
+}
+
+int srbe_solve_electrode_charges(srbe_ctx *c, double *Q, double *psi_bar, double *b) {
+  return guarded(c, [&] {
+    require_state(c, true);
+    charges_pass(c);
+    download_outputs(c, nullptr, Q, psi_bar, nullptr, b);
+  });
+}
+
+int srbe_forces(srbe_ctx *c, double *F, double *Q, double *psi_bar, double *energy) {
+  return guarded(c, [&] {
+    require_state(c, true);
+    forces_pass(c, energy != nullptr);
+    extra(c)->forces_valid = true;
+    download_outputs(c, F, Q, psi_bar, energy, nullptr);
+  });
+}
+
+int srbe_forces_dev(srbe_ctx *c, double *F_dev, double *Q_dev) {
+  return guarded(c, [&] {
+    require_state(c, true);
+    forces_pass(c, false);
+    extra(c)->forces_valid = true;
+    if (F_dev && c->ni > 0) {
+      k_interleave<<<blocks_for(c->ni, 256), 256, 0, c->stream>>>(c->ni, c->F.p, F_dev);
+      c->launches++;
+      SRBE_CUDA(cudaGetLastError());
+    }
+    if (Q_dev) SRBE_CUDA(cudaMemcpyAsync(Q_dev, c->Q.p, sizeof(double) * c->ne, cudaMemcpyDeviceToDevice, c->stream));
+  });
+}
+
+int srbe_step(srbe_ctx *c, int nsteps, uint64_t seed0) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(nsteps >= 0, SRBE_EINVAL, "negative step count");
+    SRBE_REQUIRE(c->have_ele && c->have_pos, SRBE_ESTATE, "electrode and positions are required");
+    SRBE_REQUIRE(c->have_md, SRBE_ESTATE, "srbe_set_md has not been called");
+    Extra *e = extra(c);
+    if (!e->forces_valid) {
+      // forces at the starting positions use the modes of step md_step
+      sample_into(c, seed0, c->md_step);
+      forces_pass(c, false);
+      e->forces_valid = true;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+      c->md_step++;
+      sample_into(c, seed0, c->md_step);
+      integrate_kick_drift(c, 0.5 * c->dt, true);
+      forces_pass(c, false);
+      integrate_kick_drift(c, 0.5 * c->dt, false);
+    }
+    SRBE_CUDA(cudaGetLastError());
+  });
+}
+
+int srbe_get_counters(const srbe_ctx *cc, int64_t *kernel_launches, int64_t *mode_evals) {
+  if (!cc) return SRBE_EINVAL;
+  if (kernel_launches) *kernel_launches = cc->launches;
+  if (mode_evals) *mode_evals = cc->mode_evals;
+  return SRBE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// Fourier-space part of SRBE: structure factors S(k) = sum_j w_j exp(i k . r_j) (Eq. 15) over a
+// weighted mode list (the deterministic set I and the P sampled modes, Eqs. 24-25), the
+// far-field electrode right-hand side b_F (Eq. 24), and the reductions that finish S.
+//
+// Layout: positions are SoA doubles; the mode list is int4 (m_x, m_y, m_z, 0) plus one double
+// weight c_k per mode.  Phases are exact 64-bit fixed-point turns (srbe_internal.cuh).
+//
+// S(k) is computed in two deterministic passes: each block sums a fixed chunk of particles for
+// a tile of 128 modes (one mode per thread, particles staged in shared memory), writing one
+// partial per (chunk, mode); a second kernel adds the partials in chunk order.
+#include "srbe_internal.cuh"
+
+namespace srbe {
+
+constexpr int kSfThreads = 128;
+
+// FP32 Kahan-compensated accumulator (the mixed form's "compensated sums").
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <bool F32>
+__global__ void __launch_bounds__(kSfThreads)
+k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+               const double *__restrict__ w, int K, const int4 *__restrict__ modes, double3 invL,
+               const double2 *__restrict__ gtab, int64_t chunk, double2 *__restrict__ partial,
+               double *__restrict__ mpart) {
+  __shared__ double2 tab[F32 ? 1 : kTab];
+  __shared__ uint64_t sux[kSfThreads], suy[kSfThreads], suz[kSfThreads];
+  __shared__ double sw[kSfThreads];
+  __shared__ double red[kSfThreads];
+  const int t = threadIdx.x;
+  if (!F32)
+    for (int i = t; i < kTab; i += kSfThreads) tab[i] = gtab[i];
+  const int kidx = blockIdx.y * kSfThreads + t;
+  const int4 m = kidx < K ? modes[kidx] : make_int4(0, 0, 0, 0);
+  const int64_t i0 = (int64_t)blockIdx.x * chunk;
+  const int64_t i1 = min(n, i0 + chunk);
+  double are = 0.0, aim = 0.0, mz = 0.0;
+  KahanF fre, fim;
+  for (int64_t base = i0; base < i1; base += kSfThreads) {
+    __syncthreads();
+    const int64_t i = base + t;
+    if (i < i1) {
+      sux[t] = to_turns64(x[i], invL.x);
+      suy[t] = to_turns64(y[i], invL.y);
+      suz[t] = to_turns64(z[i], invL.z);
+      sw[t] = w[i];
+      if (blockIdx.y == 0) mz = fma(w[i], z[i], mz);
+    }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)kSfThreads, i1 - base);
+    if (kidx < K) {
+      if (!F32) {
+        for (int j = 0; j < cnt; ++j) {
+          double c, s;
+          sincos_turns(phase64(m, sux[j], suy[j], suz[j]), tab, c, s);
+          are = fma(sw[j], c, are);
+          aim = fma(sw[j], s, aim);
+        }
+      } else {
+        for (int j = 0; j < cnt; ++j) {
+          const uint32_t th = (uint32_t)m.x * (uint32_t)(sux[j] >> 32) + (uint32_t)m.y * (uint32_t)(suy[j] >> 32) +
+                              (uint32_t)m.z * (uint32_t)(suz[j] >> 32);
+          float c, s;
+          sincos_turns32(th, c, s);
+          const float wf = (float)sw[j];
+          fre.add(wf * c);
+          fim.add(wf * s);
+        }
+      }
+    }
+  }
+  if (F32) {
+    are = fre.value();
+    aim = fim.value();
+  }
+  if (kidx < K) partial[(int64_t)blockIdx.x * K + kidx] = make_double2(are, aim);
+  if (blockIdx.y == 0) {
+    // fixed-order block reduction of sum w z
+    red[t] = mz;
+    __syncthreads();
+    for (int s = kSfThreads / 2; s > 0; s >>= 1) {
+      if (t < s) red[t] += red[t + s];
+      __syncthreads();
+    }
+    if (t == 0) mpart[blockIdx.x] = red[0];
+  }
+}
+
+// S[k] = sum over chunks (in order) of the partials (+ S_add[k]); thread K sums the dipole
+// partials into scal[mslot].
+__global__ void k_sfac_reduce(int K, int nchunk, const double2 *__restrict__ partial, const double *__restrict__ mpart,
+                              double2 *__restrict__ S, const double2 *__restrict__ S_add, double *__restrict__ scal,
+                              int mslot) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < K) {
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      const double2 p = partial[(int64_t)c * K + k];
+      re += p.x;
+      im += p.y;
+    }
+    if (S_add) {
+      re += S_add[k].x;
+      im += S_add[k].y;
+    }
+    S[k] = make_double2(re, im);
+  } else if (k == K) {
+    double m = 0.0;
+    for (int c = 0; c < nchunk; ++c) m += mpart[c];
+    scal[mslot] = m;
+  }
+}
+
+// chunking of the particle sum: about four waves of blocks over the 152 SMs, chunks of whole
+// 128-particle batches
+int64_t sfac_chunks(int64_t n, int K, int64_t *chunk) {
+  const int ktiles = std::max(1, (K + kSfThreads - 1) / kSfThreads);
+  if (n <= 0) {
+    *chunk = kSfThreads;
+    return 0;
+  }
+  int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (4 * 152 + ktiles - 1) / ktiles));
+  int64_t ch = (n + nchunk - 1) / nchunk;
+  ch = ((ch + kSfThreads - 1) / kSfThreads) * kSfThreads;
+  *chunk = ch;
+  return (n + ch - 1) / ch;
+}
+
+void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *w,
+                      double2 *S, const double2 *S_add, int mslot) {
+  const int K = c->K;
+  const int ktiles = std::max(1, (K + kSfThreads - 1) / kSfThreads);
+  int64_t chunk;
+  const int64_t nchunk = sfac_chunks(n, K, &chunk);
+  SRBE_REQUIRE(c->partial.cap >= (size_t)std::max<int64_t>(nchunk * K, 1) && c->mpart.cap >= (size_t)std::max<int64_t>(nchunk, 1),
+               SRBE_ESTATE, "scratch buffers not reserved for this size");
+  const double3 invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
+  if (nchunk > 0) {
+    dim3 grid((unsigned)nchunk, (unsigned)ktiles);
+    if (c->precision == SRBE_MIXED)
+      k_sfac_partial<true><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, w, K, c->dm.p, invL, c->tab.p, chunk,
+                                                               c->partial.p, c->mpart.p);
+    else
+      k_sfac_partial<false><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, w, K, c->dm.p, invL, c->tab.p, chunk,
+                                                                c->partial.p, c->mpart.p);
+    c->launches++;
+    c->mode_evals += n * (int64_t)K;
+  }
+  k_sfac_reduce<<<blocks_for(K + 1, 128), 128, 0, c->stream>>>(K, (int)nchunk, c->partial.p, c->mpart.p, S, S_add,
+                                                               c->scal.p, mslot);
+  c->launches++;
+  SRBE_CUDA(cudaGetLastError());
+}
+
+}  // namespace srbe

@@ -1,0 +1,350 @@
+// The constant-potential charge solve.
+//
+// One-time (srbe_set_electrode): A of Eq. 18 on the GPU -
+//   k-space  (1/V) sum_k 4 pi / k^2 exp(-k^2/4a^2) cos(k.(R_i - R_j)), evaluated as
+//            sum over half the lattice of w_k [C_ki C_kj + S_ki S_kj] with per-site cos/sin tables;
+//   real     sum over in-plane images of [erfc(a R) - erfc(R / (sqrt 2 eta))] / R within r_A;
+//   self     2 (1 / (sqrt(2 pi) eta) - a / sqrt(pi)) on the diagonal;
+//   slab     (4 pi / V) Z_i Z_j (the Hessian of the slab energy (2 pi / V) M_z^2);
+// then its inverse by Gauss-Jordan elimination (A is symmetric positive definite, so the
+// diagonal pivots stay positive), w_e = A^-1 e, s = e^T w_e and the projected inverse
+// B = J A^-1 = A^-1 - w_e w_e^T / s (Eq. 11), and q_d = B d.
+//
+// Per step (Eqs. 9-10):  Q = B b + dpsi q_d,  psi_bar = -(w_e^T b + dpsi w_e^T d) / s,
+// one dense FP64 matrix-vector product, one warp per row with a fixed-order shuffle reduction.
+#include "srbe_internal.cuh"
+
+namespace srbe {
+
+// per-site cos / sin of k . R for the A-modes (mode-major, [K][ne])
+__global__ void k_site_trig(int K, int64_t ne, const int4 *__restrict__ modes, const double *__restrict__ ex,
+                            const double *__restrict__ ey, const double *__restrict__ ez, double3 invL,
+                            const double2 *__restrict__ tab, double *__restrict__ C, double *__restrict__ S) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (j >= ne || k >= K) return;
+  double c, s;
+  sincos_turns(phase64(modes[k], to_turns64(ex[j], invL.x), to_turns64(ey[j], invL.y), to_turns64(ez[j], invL.z)),
+               tab, c, s);
+  C[(int64_t)k * ne + j] = c;
+  S[(int64_t)k * ne + j] = s;
+}
+
+// A[i][j] += sum_k w_k (C_ki C_kj + S_ki S_kj), 64 x 64 output tiles, 16 x 16 threads x (4 x 4)
+constexpr int kAT = 64, kAK = 16;
+__global__ void __launch_bounds__(256)
+k_A_kspace(int K, int64_t ne, const double *__restrict__ w, const double *__restrict__ C,
+           const double *__restrict__ S, double *__restrict__ A) {
+  __shared__ double ci[kAK][kAT], si[kAK][kAT], cj[kAK][kAT], sj[kAK][kAT];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t i0 = (int64_t)blockIdx.y * kAT, j0 = (int64_t)blockIdx.x * kAT;
+  if (j0 + kAT <= i0) return;   // strictly-lower tiles are mirrored at the end
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += kAK) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kAK * kAT; e += 256) {
+      const int kk = e / kAT, ii = e % kAT;
+      const int k = k0 + kk;
+      const bool ok = k < K;
+      const double wk = ok ? w[k] : 0.0;
+      const int64_t gi = i0 + ii, gj = j0 + ii;
+      ci[kk][ii] = (ok && gi < ne) ? wk * C[(int64_t)k * ne + gi] : 0.0;
+      si[kk][ii] = (ok && gi < ne) ? wk * S[(int64_t)k * ne + gi] : 0.0;
+      cj[kk][ii] = (ok && gj < ne) ? C[(int64_t)k * ne + gj] : 0.0;
+      sj[kk][ii] = (ok && gj < ne) ? S[(int64_t)k * ne + gj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kAK; ++kk) {
+      double a[4], b[4], c[4], d[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = ci[kk][ty + 16 * u];
+        b[u] = si[kk][ty + 16 * u];
+        c[u] = cj[kk][tx + 16 * u];
+        d[u] = sj[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], c[v], fma(b[u], d[v], acc[u][v]));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t gi = i0 + ty + 16 * u, gj = j0 + tx + 16 * v;
+      if (gi < ne && gj < ne && gj >= gi) A[gi * ne + gj] += acc[u][v];
+    }
+}
+
+// real-space images, self and slab terms of Eq. 18 (upper triangle incl. diagonal); writes A
+__global__ void k_A_real(int64_t ne, const double *__restrict__ ex, const double *__restrict__ ey,
+                         const double *__restrict__ ez, double Lx, double Ly, double alpha, double eta, double rcut,
+                         int nimx, int nimy, double self, double slab, double *__restrict__ A) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= ne || j < i) return;
+  double dx0 = ex[i] - ex[j], dy0 = ey[i] - ey[j];
+  const double dz = ez[i] - ez[j];
+  dx0 -= Lx * floor(dx0 / Lx + 0.5);
+  dy0 -= Ly * floor(dy0 / Ly + 0.5);
+  const double rc2 = rcut * rcut, eg = 1.4142135623730951 * eta;
+  double acc = 0.0;
+  for (int a = -nimx; a <= nimx; ++a)
+    for (int b = -nimy; b <= nimy; ++b) {
+      const double dx = dx0 + a * Lx, dy = dy0 + b * Ly;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 > 0.0 && r2 < rc2) {
+        const double r = sqrt(r2);
+        acc += (erfc(alpha * r) - erfc(r / eg)) / r;
+      }
+    }
+  if (i == j) acc += self;
+  acc = fma(slab * ez[i], ez[j], acc);
+  A[i * ne + j] = acc;
+}
+
+__global__ void k_mirror_upper(int64_t ne, double *__restrict__ A) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j < i && j < ne) A[i * ne + j] = A[j * ne + i];
+}
+
+// Gauss-Jordan step p, part 1: rowp[j] = A[p][j] / A[p][p] (j != p), rowp[p] = 1 / A[p][p];
+// colp[i] = A[i][p].  A non-positive pivot raises the flag.
+__global__ void k_gj_pivot(int64_t ne, int64_t p, const double *__restrict__ A, double *__restrict__ rowp,
+                           double *__restrict__ colp, int *__restrict__ flag) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ne) return;
+  const double piv = A[p * ne + p];
+  if (!(piv > 0.0)) {
+    if (j == 0) atomicExch(flag, 1);
+    rowp[j] = 0.0;
+    colp[j] = 0.0;
+    return;
+  }
+  const double inv = 1.0 / piv;
+  rowp[j] = (j == p) ? inv : A[p * ne + j] * inv;
+  colp[j] = A[j * ne + p];
+}
+
+// part 2: A[i][j] -= colp[i] rowp[j] (i, j != p); A[p][j] = rowp[j]; A[i][p] = -colp[i] rowp[p]
+__global__ void k_gj_update(int64_t ne, int64_t p, double *__restrict__ A, const double *__restrict__ rowp,
+                            const double *__restrict__ colp) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= ne) return;
+  double *a = A + i * ne + j;
+  if (i == p) *a = rowp[j];
+  else if (j == p) *a = -colp[i] * rowp[p];
+  else *a = fma(-colp[i], rowp[j], *a);
+}
+
+// y[i] = sum_j M[i][j] v[j] (+ dpsi * add[i]) for i < nrow; warp per row, fixed-order reduction.
+// When wrow != nullptr, "row" nrow is the vector wrow and its result r gives
+// psi_bar = -(r + dpsi * wd) / s_e, written to scal[kScalPsi].
+template <class T>
+__global__ void k_gemv_rows(int64_t nrow, int64_t ncol, const T *__restrict__ M, const double *__restrict__ v,
+                            double dpsi, const double *__restrict__ add, double *__restrict__ y,
+                            const double *__restrict__ wrow, double wd, double s_e, double *__restrict__ scal) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row > nrow || (row == nrow && !wrow)) return;
+  double acc = 0.0;
+  if (row < nrow) {
+    const T *r = M + row * ncol;
+    for (int64_t j = lane; j < ncol; j += 32) acc = fma((double)r[j], __ldg(v + j), acc);
+  } else {
+    for (int64_t j = lane; j < ncol; j += 32) acc = fma(wrow[j], __ldg(v + j), acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    if (row < nrow) y[row] = add ? fma(dpsi, add[row], acc) : acc;
+    else scal[kScalPsi] = -(acc + dpsi * wd) / s_e;
+  }
+}
+
+__global__ void k_rowsum(int64_t ne, const double *__restrict__ A, double *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= ne) return;
+  double acc = 0.0;
+  for (int64_t j = lane; j < ne; j += 32) acc += A[row * ne + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[row] = acc;
+}
+
+__global__ void k_project(int64_t ne, double *__restrict__ B, const double *__restrict__ w, double inv_s) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j < ne) B[i * ne + j] = fma(-w[i] * inv_s, w[j], B[i * ne + j]);
+}
+
+__global__ void k_to_float(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+static double host_dot(const std::vector<double> &a, const std::vector<double> &b) {
+  double s = 0.0;
+  for (size_t i = 0; i < a.size(); ++i) s += a[i] * b[i];
+  return s;
+}
+
+void build_A_and_inverse(srbe_ctx *c) {
+  const int64_t ne = c->ne;
+  const double Lx = c->L[0], Ly = c->L[1], Lz = c->L[2];
+  // alpha_A: in-plane-only real-space images are exact only if erfc(alpha_A * gap) is negligible
+  double zmin = 1e300, zmax = -1e300;
+  for (int64_t j = 0; j < ne; ++j) {
+    zmin = std::min(zmin, c->hR[3 * j + 2]);
+    zmax = std::max(zmax, c->hR[3 * j + 2]);
+  }
+  const double gap = Lz - (zmax - zmin);
+  SRBE_REQUIRE(gap > 0.0, SRBE_EINVAL, "electrode sites span the whole periodic length Lz");
+  const double tol = c->tol_A > 0 ? c->tol_A : 1e-17;
+  const double xk = std::sqrt(-std::log(tol));   // exp(-x^2) = tol
+  double xr = 1.0;                               // erfc(xr) = tol
+  while (std::erfc(xr) >= tol) xr += 0.01;
+  double aA = c->alpha_A;
+  if (!(aA > 0.0)) aA = std::max(0.5, (xr + 0.6) / gap);
+  c->alpha_A = aA;
+  // half lattice: first nonzero of (m_z, m_y, m_x) positive, exp(-k^2/4a^2) >= tol, weight doubled
+  const double kmax = 2.0 * aA * xk;
+  const int mx = (int)std::floor(kmax * Lx / (2 * kPi)), my = (int)std::floor(kmax * Ly / (2 * kPi)),
+            mz = (int)std::floor(kmax * Lz / (2 * kPi));
+  std::vector<int4> hm;
+  std::vector<double> hw;
+  for (int a = -mx; a <= mx; ++a)
+    for (int b = -my; b <= my; ++b)
+      for (int cc = 0; cc <= mz; ++cc) {
+        if (cc == 0 && (b < 0 || (b == 0 && a <= 0))) continue;
+        const double kx = 2 * kPi * a / Lx, ky = 2 * kPi * b / Ly, kz = 2 * kPi * cc / Lz;
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        const double g = std::exp(-k2 / (4 * aA * aA));
+        if (g < tol) continue;
+        hm.push_back(make_int4(a, b, cc, 0));
+        hw.push_back(2.0 * 4.0 * kPi / (c->V * k2) * g);
+      }
+  const int KA = (int)hm.size();
+  DevBuf<int4> dmA;
+  DevBuf<double> dw, Ct, St, rowp, colp;
+  dmA.ensure(KA);
+  dw.ensure(KA);
+  SRBE_CUDA(cudaMemcpyAsync(dmA.p, hm.data(), sizeof(int4) * KA, cudaMemcpyHostToDevice, c->stream));
+  SRBE_CUDA(cudaMemcpyAsync(dw.p, hw.data(), sizeof(double) * KA, cudaMemcpyHostToDevice, c->stream));
+  double *A = c->Bmat.ensure((size_t)ne * ne);
+  const double rcut = xr / aA;
+  const int nimx = (int)std::ceil(rcut / Lx) + 1, nimy = (int)std::ceil(rcut / Ly) + 1;
+  const double self = 2.0 * (1.0 / (std::sqrt(2.0 * kPi) * c->eta) - aA / std::sqrt(kPi));
+  {
+    dim3 g(blocks_for(ne, 128), (unsigned)ne);
+    k_A_real<<<g, 128, 0, c->stream>>>(ne, c->ex.p, c->ey.p, c->ez.p, Lx, Ly, aA, c->eta, rcut, nimx, nimy, self,
+                                       4.0 * kPi / c->V, A);
+    c->launches++;
+  }
+  // k-space in slabs of modes so that the cos/sin tables stay within ~1 GB
+  const int64_t kslab = std::max<int64_t>(16, std::min<int64_t>(KA, (int64_t)(1ll << 26) / std::max<int64_t>(ne, 1)));
+  Ct.ensure((size_t)kslab * ne);
+  St.ensure((size_t)kslab * ne);
+  const double3 invL = make_double3(1.0 / Lx, 1.0 / Ly, 1.0 / Lz);
+  for (int64_t k0 = 0; k0 < KA; k0 += kslab) {
+    const int kn = (int)std::min<int64_t>(kslab, KA - k0);
+    dim3 gt(blocks_for(ne, 128), (unsigned)kn);
+    k_site_trig<<<gt, 128, 0, c->stream>>>(kn, ne, dmA.p + k0, c->ex.p, c->ey.p, c->ez.p, invL, c->tab.p, Ct.p, St.p);
+    const unsigned nt = (unsigned)((ne + kAT - 1) / kAT);
+    k_A_kspace<<<dim3(nt, nt), 256, 0, c->stream>>>(kn, ne, dw.p + k0, Ct.p, St.p, A);
+    c->launches += 2;
+  }
+  {
+    dim3 g(blocks_for(ne, 128), (unsigned)ne);
+    k_mirror_upper<<<g, 128, 0, c->stream>>>(ne, A);
+    c->launches++;
+  }
+  // keep A for residual checks
+  double *Akeep = c->Amat.ensure((size_t)ne * ne);
+  SRBE_CUDA(cudaMemcpyAsync(Akeep, A, sizeof(double) * ne * ne, cudaMemcpyDeviceToDevice, c->stream));
+  // Gauss-Jordan inversion in place
+  rowp.ensure(ne);
+  colp.ensure(ne);
+  int *flag = c->flag.ensure(1);
+  SRBE_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  for (int64_t p = 0; p < ne; ++p) {
+    k_gj_pivot<<<blocks_for(ne, 256), 256, 0, c->stream>>>(ne, p, A, rowp.p, colp.p, flag);
+    k_gj_update<<<dim3(blocks_for(ne, 256), (unsigned)ne), 256, 0, c->stream>>>(ne, p, A, rowp.p, colp.p);
+  }
+  c->launches += 2 * ne;
+  SRBE_CUDA(cudaGetLastError());
+  int hflag = 0;
+  SRBE_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  // w_e = A^-1 e, s = e^T w_e, w_e^T d
+  double *we = c->we.ensure(ne);
+  k_rowsum<<<blocks_for(ne * 32, 256), 256, 0, c->stream>>>(ne, A, we);
+  std::vector<double> hwe(ne), hd(ne);
+  SRBE_CUDA(cudaMemcpyAsync(hwe.data(), we, sizeof(double) * ne, cudaMemcpyDeviceToHost, c->stream));
+  SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  SRBE_REQUIRE(hflag == 0, SRBE_ENOTCONV, "A is not positive definite (non-positive pivot in Gauss-Jordan)");
+  for (int64_t j = 0; j < ne; ++j) hd[j] = c->hside[j] ? 0.5 : -0.5;
+  double s = 0.0;
+  for (int64_t j = 0; j < ne; ++j) s += hwe[j];
+  SRBE_REQUIRE(s > 0.0, SRBE_ENOTCONV, "e^T A^-1 e is not positive");
+  c->s_e = s;
+  c->wd = host_dot(hwe, hd);
+  // B = A^-1 - w_e w_e^T / s ; q_d = B d
+  k_project<<<dim3(blocks_for(ne, 256), (unsigned)ne), 256, 0, c->stream>>>(ne, A, we, 1.0 / s);
+  double *qd = c->qd.ensure(ne);
+  k_gemv_rows<double><<<blocks_for(ne * 32, 256), 256, 0, c->stream>>>(ne, ne, A, c->ed.p, 0.0, nullptr, qd, nullptr,
+                                                                      0.0, 1.0, nullptr);
+  float *B32 = c->Bmat32.ensure((size_t)ne * ne);
+  k_to_float<<<blocks_for(ne * ne, 256), 256, 0, c->stream>>>(ne * ne, A, B32);
+  c->launches += 4;
+  SRBE_CUDA(cudaGetLastError());
+  SRBE_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void charge_update(srbe_ctx *c) {
+  const int64_t ne = c->ne;
+  const unsigned nb = blocks_for((ne + 1) * 32, 256);
+  k_gemv_rows<double><<<nb, 256, 0, c->stream>>>(ne, ne, c->Bmat.p, c->bvec.p, c->dpsi, c->qd.p, c->Q.p, c->we.p,
+                                                 c->wd, c->s_e, c->scal.p);
+  c->launches++;
+  SRBE_CUDA(cudaGetLastError());
+}
+
+// 1/2 sum_k c_k |S(k)|^2, sum Q^2, sum q^2 into scal (one block, fixed order)
+__global__ void k_energy_scalars(int K, const double *__restrict__ cw, const double2 *__restrict__ S, int64_t ne,
+                                 const double *__restrict__ Q, int64_t ni, const double *__restrict__ q,
+                                 double *__restrict__ scal) {
+  __shared__ double red[3][256];
+  const int t = threadIdx.x;
+  double a = 0, b = 0, d = 0;
+  for (int k = t; k < K; k += 256) a += 0.5 * cw[k] * (S[k].x * S[k].x + S[k].y * S[k].y);
+  for (int64_t j = t; j < ne; j += 256) b += Q[j] * Q[j];
+  for (int64_t i = t; i < ni; i += 256) d += q[i] * q[i];
+  red[0][t] = a;
+  red[1][t] = b;
+  red[2][t] = d;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (t < s)
+      for (int e = 0; e < 3; ++e) red[e][t] += red[e][t + s];
+    __syncthreads();
+  }
+  if (t == 0) {
+    scal[kScalUF] = red[0][0];
+    scal[kScalQ2] = red[1][0];
+    scal[kScalq2] = red[2][0];
+  }
+}
+
+void energy_scalars(srbe_ctx *c) {
+  k_energy_scalars<<<1, 256, 0, c->stream>>>(c->K, c->dc.p, c->S2.p, c->ne, c->Q.p, c->ni, c->q.p, c->scal.p);
+  c->launches++;
+  SRBE_CUDA(cudaGetLastError());
+}
+
+}  // namespace srbe

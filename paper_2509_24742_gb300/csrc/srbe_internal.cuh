@@ -1,0 +1,254 @@
+// Internal declarations of the SRBE library: context layout, device buffers, launch helpers and
+// the fixed-point phase / sin-cos primitives shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/srbe.h"
+
+namespace srbe {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kTabBits = 10;                  // sin/cos table of 1024 entries per turn
+constexpr int kTab = 1 << kTabBits;
+
+// ------------------------------------------------------------------------------------------------
+// error plumbing
+// ------------------------------------------------------------------------------------------------
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define SRBE_CUDA(call)                                                                         \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      throw ::srbe::Error{SRBE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};      \
+  } while (0)
+
+#define SRBE_REQUIRE(cond, code, text)                  \
+  do {                                                  \
+    if (!(cond)) throw ::srbe::Error{(code), (text)};   \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------------
+// device buffer with grow-only capacity
+// ------------------------------------------------------------------------------------------------
+template <class T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t cap = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  T *ensure(size_t n) {
+    if (n <= cap && p) return p;
+    release();
+    size_t bytes = (n ? n : 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)&p, bytes);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw Error{SRBE_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e)};
+    }
+    cap = n ? n : 1;
+    return p;
+  }
+};
+
+// Cell list of a point set: 2D-periodic bins in x, y and open bins in z.
+struct CellGrid {
+  int nc[3] = {1, 1, 1};       // cells per dimension
+  double cs[3] = {1, 1, 1};    // cell edge
+  double z0 = 0.0;             // z of the lower edge of cell 0
+  int span[3] = {1, 1, 1};     // stencil half-width in cells, so that span * cs >= rc
+  int ncell() const { return nc[0] * nc[1] * nc[2]; }
+};
+
+struct Cells {
+  CellGrid g;
+  DevBuf<int32_t> cell, rank, start, order;   // order: sorted position -> original index
+  DevBuf<double> xs, ys, zs, ws;              // positions / charges in sorted order
+  DevBuf<int32_t> ts, ms;                     // type, molecule in sorted order
+  DevBuf<float> xf, yf, zf;                   // FP32 copies for the cheap distance pre-check
+};
+
+struct HostExt;   // host-only per-context state (sampler, staging), defined in api.cu
+
+}  // namespace srbe
+
+// ------------------------------------------------------------------------------------------------
+// the context
+// ------------------------------------------------------------------------------------------------
+struct srbe_ctx {
+  // problem parameters
+  double L[3] = {0, 0, 0};
+  double V = 0;
+  double alpha = 0, eta = 0, rc = 0;
+  int P = 0, M = 0;
+  double psi_left = 0, psi_right = 0;
+  double dpsi = 0;              // (psi_right - psi_left) in e/nm
+  double alpha_A = 0, tol_A = 1e-17;
+  int precision = SRBE_FP64;
+  int sampler = SRBE_SAMPLER_METROPOLIS;
+  int32_t mmax[3] = {0, 0, 0};
+  double G = 0;
+
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+
+  bool have_ele = false, have_pos = false, have_modes = false, have_md = false;
+
+  // electrode (fixed sites)
+  int64_t ne = 0;
+  srbe::DevBuf<double> ex, ey, ez, ed;         // positions and d (-1/2 | +1/2)
+  srbe::DevBuf<double> Bmat;                   // projected inverse J A^-1, ne x ne row-major
+  srbe::DevBuf<float> Bmat32;                  // its FP32 copy (mixed form)
+  srbe::DevBuf<double> Amat;                   // A itself (kept for the refinement residual)
+  srbe::DevBuf<double> we, qd;                 // A^-1 e and (J A^-1) d
+  srbe::DevBuf<double> bvec, Q;                // per-step b and charges
+  double s_e = 0, wd = 0;                      // e^T A^-1 e and (A^-1 e)^T d
+  std::vector<double> hR;                      // host copy of R
+  std::vector<int8_t> hside;
+  srbe::Cells ecells;
+
+  // electrolyte
+  int64_t ni = 0;
+  srbe::DevBuf<double> x, y, z, q;
+  srbe::DevBuf<double> vx, vy, vz, minv;
+  srbe::DevBuf<double> F;                      // [3][ni] SoA force
+  srbe::DevBuf<int32_t> itype, mol;
+  srbe::DevBuf<int32_t> bond_start, bond_j;
+  srbe::DevBuf<double> bond_r0;
+  int ntype = 0;
+  srbe::DevBuf<double> lj;                     // [ntype*ntype] (sigma^2, 4 eps) pairs as double2
+  double kb = 0, dt = 0;
+  srbe::Cells icells;
+
+  // modes
+  int K = 0;                                   // modes evaluated on the device
+  int Kdet = 0;                                // of which deterministic (folded +m_z with weight x2)
+  std::vector<int32_t> hm;                     // host mode list [K][4]
+  std::vector<double> hc;                      // host weights [K]
+  std::vector<int32_t> hsamp;                  // last sampled modes [P][3]
+  bool explicit_list = false;
+  srbe::DevBuf<int4> dm;
+  srbe::DevBuf<double> dc;
+  srbe::DevBuf<double2> S1, S2;                // structure factors (S2 holds S1 + S2 after the update)
+  srbe::DevBuf<double2> tab;                   // sin/cos table
+
+  // pinned staging for mode lists
+  int4 *h_mode_stage = nullptr;
+  double *h_w_stage = nullptr;
+  size_t stage_cap = 0;
+  cudaEvent_t stage_done = nullptr;
+
+  // scratch (sized by srbe::reserve before any launch so that steps allocate nothing)
+  srbe::DevBuf<double2> partial;               // structure-factor partials [chunks][K]
+  srbe::DevBuf<double> mpart;                  // dipole partials [chunks]
+  srbe::DevBuf<double2> coef;                  // per-mode c_k S(k) coefficients [K]
+  srbe::DevBuf<double> scal;                   // device scalars (see kScal* indices)
+  srbe::DevBuf<double> epart;                  // per-block energy partials
+  srbe::DevBuf<int> flag;                      // device error flag
+  double h_scal[16];
+
+  srbe::HostExt *hx = nullptr;
+
+  // counters
+  int64_t launches = 0;
+  int64_t mode_evals = 0;
+  uint64_t md_step = 0;
+};
+
+namespace srbe {
+
+// indices into ctx->scal (16 device scalars): dipoles sum q z and sum Q Z, psi_bar (e/nm), then the
+// energy accumulators: U_N ion-ion, U_N ion-electrode, LJ, bonds, U_N electrode-electrode,
+// 1/2 sum c |S|^2, sum Q^2, sum q^2
+enum {
+  kScalMion = 0, kScalMele = 1, kScalPsi = 2,
+  kScalEnergy = 4, kScalEii = 4, kScalEie = 5, kScalElj = 6, kScalEbond = 7, kScalEee = 8,
+  kScalUF = 9, kScalQ2 = 10, kScalq2 = 11, kScalCount = 16
+};
+
+// ------------------------------------------------------------------------------------------------
+// fixed-point phases and sin/cos
+// ------------------------------------------------------------------------------------------------
+// A coordinate x in a period L is stored as u = frac(x / L) * 2^64 (uint64), so that the phase
+// k . r = 2 pi (m_x u_x + m_y u_y + m_z u_z) / 2^64 is exact modulo one turn in integer
+// arithmetic, whatever the size of m.
+__device__ __forceinline__ uint64_t to_turns64(double x, double invL) {
+  double t = x * invL;
+  t -= floor(t);
+  if (t >= 1.0) t = 0.0;
+  return (uint64_t)__double2ull_rz(t * 18446744073709551616.0);
+}
+
+__device__ __forceinline__ uint64_t phase64(int4 m, uint64_t ux, uint64_t uy, uint64_t uz) {
+  return (uint64_t)(int64_t)m.x * ux + (uint64_t)(int64_t)m.y * uy + (uint64_t)(int64_t)m.z * uz;
+}
+
+// cos and sin of 2 pi th / 2^64.  The top 10 bits (rounded) select a table angle
+// a_j = 2 pi j / 1024; the remainder x (|x| <= pi / 1024) enters through
+// sin x = x - x^3/6 + x^5/120 and cos x - 1 = -x^2/2 + x^4/24 (truncation below 1e-18) and the
+// angle-addition formulas.  The remainder is turned into a double exactly by adding it to the
+// bit pattern of 1.5 * 2^52.
+__device__ __forceinline__ void sincos_turns(uint64_t th, const double2 *__restrict__ tab, double &c, double &s) {
+  const uint64_t t = th + (1ull << 53);
+  const unsigned idx = (unsigned)(t >> 54);
+  const int64_t rem = (int64_t)(th - ((uint64_t)idx << 54));     // in [-2^53, 2^53)
+  const int64_t v = rem >> 2;                                      // |v| <= 2^51
+  const double xv = __longlong_as_double(0x4338000000000000LL + v) - 6755399441055744.0;
+  constexpr double kTurn62 = 2.0 * kPi / 4611686018427387904.0;    // 2 pi / 2^62
+  const double x = xv * kTurn62;
+  const double x2 = x * x;
+  const double sx = fma(x * x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
+  const double cm1 = x2 * fma(x2, 1.0 / 24.0, -0.5);
+  const double2 T = tab[idx];
+  c = fma(T.x, cm1, fma(-T.y, sx, T.x));
+  s = fma(T.y, cm1, fma(T.x, sx, T.y));
+}
+
+// FP32 form: phase in turns from 32-bit fixed point (top half), reduced to [-pi, pi).
+__device__ __forceinline__ uint32_t to_turns32(double x, double invL) { return (uint32_t)(to_turns64(x, invL) >> 32); }
+__device__ __forceinline__ void sincos_turns32(uint32_t th, float &c, float &s) {
+  constexpr float kTurn32 = (float)(2.0 * kPi / 4294967296.0);     // 2 pi / 2^32
+  const float a = (float)(int32_t)th * kTurn32;
+  __sincosf(a, &s, &c);
+}
+
+// ------------------------------------------------------------------------------------------------
+// kernels' host launchers (defined in the .cu files)
+// ------------------------------------------------------------------------------------------------
+void upload_table(srbe_ctx *c);
+void build_cells(srbe_ctx *c, Cells &cl, int64_t n, const double *x, const double *y, const double *z,
+                 const double *w, const int32_t *typ, const int32_t *mol, bool is_ion);
+void choose_grid(const srbe_ctx *c, CellGrid &g, double zlo, double zhi);
+void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *w,
+                      double2 *S, const double2 *S_add, int mslot);
+void electrode_rhs(srbe_ctx *c);
+void charge_update(srbe_ctx *c);
+void ion_forces(srbe_ctx *c, bool energies);
+void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift);
+void build_A_and_inverse(srbe_ctx *c);
+void energy_scalars(srbe_ctx *c);
+void reserve(srbe_ctx *c);
+int64_t sfac_chunks(int64_t n, int K, int64_t *chunk);
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace srbe

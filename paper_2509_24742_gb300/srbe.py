@@ -1,0 +1,243 @@
+"""Thin Python binding of the SRBE C ABI (include/srbe.h): argument marshalling only.
+
+Every computation happens in libsrbe.so (CUDA kernels for sm_103a).  There is no CPU fallback:
+if the library cannot be built or loaded, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SRBE_OK, SRBE_EINVAL, SRBE_ENOMEM, SRBE_ECUDA, SRBE_ESTATE, SRBE_ENOTCONV, SRBE_ETIMEOUT = range(7)
+FP64, MIXED = 0, 1
+METROPOLIS, EXACT = 0, 1
+VOLT = 0.694461
+K_E = 138.935458
+ENERGY_TERMS = ("U_N ion-ion", "U_N ion-electrode", "U_N electrode-electrode", "U_F", "U_self", "U_slab",
+                "U_LJ", "U_bond")
+
+_STATUS = {SRBE_EINVAL: "invalid argument", SRBE_ENOMEM: "out of memory", SRBE_ECUDA: "CUDA error",
+           SRBE_ESTATE: "call out of order", SRBE_ENOTCONV: "not converged", SRBE_ETIMEOUT: "timeout"}
+
+
+class SrbeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_STATUS.get(code, "error"), code, msg))
+        self.code = code
+
+
+_lib = None
+_vp, _dp, _i64, _int, _u64, _dbl = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int, \
+    ctypes.c_uint64, ctypes.c_double
+_ip = ctypes.POINTER(ctypes.c_int32)
+_bp = ctypes.POINTER(ctypes.c_int8)
+
+EXPORTS = {
+    "srbe_create": ([_dp, _dbl, _dbl, _dbl, _int, _int, _dbl, _dbl, ctypes.POINTER(_vp)], _int),
+    "srbe_destroy": ([_vp], _int),
+    "srbe_last_error": ([_vp], ctypes.c_char_p),
+    "srbe_set_stream": ([_vp, _vp], _int),
+    "srbe_set_precision": ([_vp, _int], _int),
+    "srbe_set_A_params": ([_vp, _dbl, _dbl], _int),
+    "srbe_set_electrode": ([_vp, _i64, _dp, _bp], _int),
+    "srbe_set_positions": ([_vp, _i64, _dp, _dp], _int),
+    "srbe_get_positions": ([_vp, _dp, _dp], _int),
+    "srbe_set_md": ([_vp, _dp, _dp, _int, _ip, _ip, _dp, _dp, _i64, _ip, _dp, _dbl, _dbl], _int),
+    "srbe_set_sampler": ([_vp, _int, _ip], _int),
+    "srbe_sample_k": ([_vp, _u64, _u64], _int),
+    "srbe_get_k": ([_vp, _ip, _dp], _int),
+    "srbe_set_k": ([_vp, _ip, _int], _int),
+    "srbe_set_mode_list": ([_vp, _ip, _dp, _int], _int),
+    "srbe_solve_electrode_charges": ([_vp, _dp, _dp, _dp], _int),
+    "srbe_forces": ([_vp, _dp, _dp, _dp, _dp], _int),
+    "srbe_step": ([_vp, _int, _u64], _int),
+    "srbe_set_positions_dev": ([_vp, _i64, _vp, _vp], _int),
+    "srbe_forces_dev": ([_vp, _vp, _vp], _int),
+    "srbe_get_counters": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _int),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build=True):
+    """Loads libsrbe.so (building it first when sources changed)."""
+    global _lib
+    if _lib is None:
+        if build:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libsrbe.so is missing; run paper_2509_24742_gb300.build.build()")
+        L = ctypes.CDLL(_build.LIB)
+        for name, (args, res) in EXPORTS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _d(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+def _ptr(a, t=_dp):
+    return a.ctypes.data_as(t) if a is not None and a.size else None
+
+
+class Context:
+    """One SRBE problem on the GPU.  Units: nm, ps, amu, e, kJ/mol, V."""
+
+    def __init__(self, box, alpha, eta, rc, P, M, psi_left=0.0, psi_right=1.0):
+        self.lib = load()
+        h = _vp()
+        b = _d(box, 3)
+        self._check(self.lib.srbe_create(_ptr(b), alpha, eta, rc, int(P), int(M), psi_left, psi_right,
+                                         ctypes.byref(h)), None)
+        self.h = h
+        self.P, self.M = int(P), int(M)
+        self.n_ion = 0
+        self.n_ele = 0
+
+    def _check(self, code, h="self"):
+        if code != SRBE_OK:
+            msg = self.lib.srbe_last_error(self.h if h == "self" else None)
+            raise SrbeError(code, (msg or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.srbe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- configuration
+    def set_stream(self, stream_ptr):
+        self._check(self.lib.srbe_set_stream(self.h, _vp(stream_ptr) if stream_ptr else None))
+
+    def set_precision(self, mode):
+        self._check(self.lib.srbe_set_precision(self.h, int(mode)))
+
+    def set_A_params(self, alpha_A=0.0, tol=0.0):
+        self._check(self.lib.srbe_set_A_params(self.h, float(alpha_A), float(tol)))
+
+    def set_electrode(self, R, side):
+        R = _d(R).reshape(-1, 3)
+        side = np.ascontiguousarray(side, dtype=np.int8)
+        self.n_ele = R.shape[0]
+        self._check(self.lib.srbe_set_electrode(self.h, R.shape[0], _ptr(R), _ptr(side, _bp)))
+
+    def set_positions(self, r, q):
+        r = _d(r).reshape(-1, 3)
+        q = _d(q, r.shape[0])
+        self.n_ion = r.shape[0]
+        self._check(self.lib.srbe_set_positions(self.h, r.shape[0], _ptr(r), _ptr(q)))
+
+    def set_positions_dev(self, n, r_ptr, q_ptr):
+        self.n_ion = int(n)
+        self._check(self.lib.srbe_set_positions_dev(self.h, int(n), _vp(r_ptr), _vp(q_ptr)))
+
+    def get_positions(self, velocities=False):
+        r = np.empty((self.n_ion, 3))
+        v = np.empty((self.n_ion, 3)) if velocities else None
+        self._check(self.lib.srbe_get_positions(self.h, _ptr(r), _ptr(v) if velocities else None))
+        return (r, v) if velocities else r
+
+    def set_md(self, mass, itype, mol, lj_sigma, lj_eps, bonds=None, r0=None, kb=0.0, dt=0.002, v=None):
+        n = self.n_ion
+        mass = _d(mass, n)
+        itype = np.ascontiguousarray(itype, dtype=np.int32)
+        mol = np.ascontiguousarray(mol, dtype=np.int32)
+        sig = _d(lj_sigma)
+        eps = _d(lj_eps)
+        nt = int(round(np.sqrt(sig.size)))
+        bonds = np.zeros((0, 2), np.int32) if bonds is None else np.ascontiguousarray(bonds, dtype=np.int32)
+        r0 = np.zeros(0) if r0 is None else _d(r0, bonds.shape[0])
+        vv = None if v is None else _d(v, 3 * n)
+        self._check(self.lib.srbe_set_md(self.h, _ptr(mass), _ptr(vv) if vv is not None else None, nt,
+                                         _ptr(itype, _ip), _ptr(mol, _ip), _ptr(sig), _ptr(eps), bonds.shape[0],
+                                         _ptr(bonds, _ip), _ptr(r0), float(kb), float(dt)))
+
+    def set_sampler(self, kind=METROPOLIS, mmax=None):
+        mm = None if mmax is None else np.ascontiguousarray(mmax, dtype=np.int32)
+        self._check(self.lib.srbe_set_sampler(self.h, int(kind), _ptr(mm, _ip) if mm is not None else None))
+
+    # --- modes
+    def sample_k(self, seed, step=0):
+        self._check(self.lib.srbe_sample_k(self.h, int(seed), int(step)))
+
+    def get_k(self):
+        m = np.empty((self.P, 3), np.int32)
+        G = ctypes.c_double()
+        self._check(self.lib.srbe_get_k(self.h, _ptr(m, _ip), ctypes.byref(G)))
+        return m, G.value
+
+    def set_k(self, m):
+        m = np.ascontiguousarray(m, dtype=np.int32).reshape(-1, 3)
+        self.P = m.shape[0]
+        self._check(self.lib.srbe_set_k(self.h, _ptr(m, _ip), m.shape[0]))
+
+    def set_mode_list(self, m, w):
+        m = np.ascontiguousarray(m, dtype=np.int32).reshape(-1, 3)
+        w = _d(w, m.shape[0])
+        self._check(self.lib.srbe_set_mode_list(self.h, _ptr(m, _ip), _ptr(w), m.shape[0]))
+
+    # --- evaluation
+    def solve_charges(self):
+        Q = np.empty(self.n_ele)
+        b = np.empty(self.n_ele)
+        psi = ctypes.c_double()
+        self._check(self.lib.srbe_solve_electrode_charges(self.h, _ptr(Q), ctypes.byref(psi), _ptr(b)))
+        return Q, psi.value, b
+
+    def forces(self, energy=False):
+        F = np.empty((self.n_ion, 3))
+        Q = np.empty(self.n_ele)
+        psi = ctypes.c_double()
+        E = np.empty(8) if energy else None
+        self._check(self.lib.srbe_forces(self.h, _ptr(F), _ptr(Q), ctypes.byref(psi),
+                                         _ptr(E) if energy else None))
+        return (F, Q, psi.value, E) if energy else (F, Q, psi.value)
+
+    def forces_dev(self, F_ptr=None, Q_ptr=None):
+        self._check(self.lib.srbe_forces_dev(self.h, _vp(F_ptr) if F_ptr else None, _vp(Q_ptr) if Q_ptr else None))
+
+    def step(self, nsteps, seed0):
+        self._check(self.lib.srbe_step(self.h, int(nsteps), int(seed0)))
+
+    def counters(self):
+        a, b = _i64(), _i64()
+        self._check(self.lib.srbe_get_counters(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+
+def from_slab(slab, precision=FP64, alpha_A=0.0, md=False):
+    """Convenience: a Context set up from a workloads.Slab (electrode, positions, optionally MD terms)."""
+    ctx = Context(slab.box, slab.alpha, slab.eta, slab.rc, slab.P, slab.M, 0.0, slab.dpsi_volt)
+    ctx.set_precision(precision)
+    ctx.set_A_params(alpha_A, 0.0)
+    ctx.set_electrode(slab.R, slab.side)
+    ctx.set_positions(slab.r, slab.q)
+    if md:
+        sig, eps = slab.lj_tables()
+        ctx.set_md(slab.mass, slab.itype, slab.mol, sig, eps, slab.bonds, slab.bond_r0, slab.bond_k, slab.dt,
+                   v=slab.v if slab.v is not None else np.zeros((slab.n_ion, 3)))
+    return ctx

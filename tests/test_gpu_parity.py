@@ -1,0 +1,161 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same seeded inputs.
+
+Bars: FP64 path within 1e-10 normwise relative on forces and charges (and psi_bar, b);
+integer work (the mode sampler) bit-exact; the mixed form within RMS force error 1e-3 of the
+FP64 GPU path.  Mode lists come from the oracle's sampler, never from the library."""
+import numpy as np
+import pytest
+
+from paper_2509_24742_gb300 import srbe, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+ALPHA_A = 1.7          # A-build Ewald parameter shared by both sides (alpha_A (Lz - H) = 6.8)
+TOL = 1e-10
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module")
+def slab784():
+    return wl.one_shot_784()
+
+
+@pytest.fixture(scope="module")
+def ref784(orc, slab784):
+    return orc.System(slab784, alpha_A=ALPHA_A)
+
+
+def gpu_ctx(slab, precision=srbe.FP64, alpha_A=ALPHA_A, md=False):
+    return srbe.from_slab(slab, precision=precision, alpha_A=alpha_A, md=md)
+
+
+def test_fp64_forces_charges_match_oracle(orc, slab784, ref784):
+    samples = orc.sample_metropolis(slab784.box, slab784.alpha, slab784.M, slab784.P, 3001, 0)
+    m, c = ref784.modes(samples)
+    ev = ref784.evaluate(m, c, with_lj=False)
+    with gpu_ctx(slab784) as ctx:
+        ctx.set_k(samples)
+        F, Q, psi, E = ctx.forces(energy=True)
+        Q2, psi2, b = ctx.solve_charges()
+    assert rel(F, ev["F"]) < TOL
+    assert rel(Q, ev["Q"]) < TOL
+    assert abs(psi * srbe.VOLT - ev["psi_bar"]) < TOL * abs(ev["psi_bar"])
+    assert rel(b * srbe.VOLT, ev["b"]) < TOL
+    assert np.array_equal(Q, Q2)
+    assert abs(Q.sum()) < 1e-12 * np.abs(Q).sum()
+    np.testing.assert_allclose(E[:6], ev["E"], rtol=1e-9, atol=1e-9 * np.abs(ev["E"]).max())
+
+
+def test_full_ewald_mode_list_matches_oracle(orc, slab784, ref784):
+    """The same kernels evaluate full Ewald (kmax 8 x 8 x 48) from an explicit mode list."""
+    m = orc.full_modes(slab784.box, slab784.alpha, (8, 8, 48))
+    c = orc.ewald_weight(slab784.box, slab784.alpha, m)
+    ev = ref784.evaluate(m, c, with_lj=False)
+    with gpu_ctx(slab784) as ctx:
+        ctx.set_mode_list(m, c)
+        F, Q, psi = ctx.forces()
+    assert rel(F, ev["F"]) < TOL
+    assert rel(Q, ev["Q"]) < TOL
+
+
+def test_sampler_bit_exact_with_oracle(orc, slab784):
+    with gpu_ctx(slab784) as ctx:
+        for step in (0, 1, 17):
+            ctx.sample_k(3001, step)
+            m, G = ctx.get_k()
+            ref = orc.sample_metropolis(slab784.box, slab784.alpha, slab784.M, slab784.P, 3001, step)
+            assert np.array_equal(m, ref)
+            assert abs(G - orc.G_closed(slab784.box, slab784.alpha, slab784.M)) < 1e-12 * G
+        ctx.set_sampler(srbe.EXACT, (8, 8, 48))
+        ctx.sample_k(5, 2)
+        m, G = ctx.get_k()
+        ref = orc.sample_exact(slab784.box, slab784.alpha, slab784.M, slab784.P, 5, 2, (8, 8, 48))
+        assert np.array_equal(m, ref)
+        assert abs(G - orc.G_closed(slab784.box, slab784.alpha, slab784.M, (8, 8, 48))) < 1e-12 * G
+
+
+def test_mixed_precision_error_bounds(orc, slab784):
+    samples = orc.sample_metropolis(slab784.box, slab784.alpha, slab784.M, slab784.P, 3001, 4)
+    with gpu_ctx(slab784) as c64:
+        c64.set_k(samples)
+        F64, Q64, _ = c64.forces()
+    with gpu_ctx(slab784, precision=srbe.MIXED) as c32:
+        c32.set_k(samples)
+        F32, Q32, _ = c32.forces()
+    rms_f = np.sqrt(((F32 - F64) ** 2).sum(1).mean()) / np.sqrt((F64 ** 2).sum(1).mean())
+    assert rms_f < 1e-3, rms_f
+    assert rel(Q32, Q64) < 1e-3
+
+
+@pytest.mark.parametrize("case", ["no_ions", "no_samples", "no_deterministic", "ragged"])
+def test_edge_cases_match_oracle(orc, case):
+    s = wl.one_shot_784()
+    if case == "no_ions":
+        s.r, s.q = np.zeros((0, 3)), np.zeros(0)
+        s.mol, s.itype, s.mass = s.mol[:0], s.itype[:0], s.mass[:0]
+    elif case == "ragged":
+        keep = 2 * 67 + 1          # odd count, not a multiple of the 128-thread tiles
+        s.r, s.q = s.r[:keep].copy(), s.q[:keep].copy()
+        s.q -= s.q.mean()
+        s.mol, s.itype, s.mass = s.mol[:keep], s.itype[:keep], s.mass[:keep]
+    P = 0 if case == "no_samples" else 37
+    M = 0 if case == "no_deterministic" else s.M
+    s.P, s.M = P, M
+    ref = orc.System(s, alpha_A=ALPHA_A)
+    samples = orc.sample_metropolis(s.box, s.alpha, M, P, 11, 0) if P else np.zeros((0, 3), np.int32)
+    m, c = ref.modes(samples)
+    ev = ref.evaluate(m, c, with_lj=False)
+    with gpu_ctx(s) as ctx:
+        ctx.set_k(samples)
+        F, Q, psi = ctx.forces()
+    assert rel(Q, ev["Q"]) < TOL
+    if s.n_ion:
+        assert rel(F, ev["F"]) < TOL
+
+
+def test_results_are_bitwise_reproducible(orc, slab784):
+    samples = orc.sample_metropolis(slab784.box, slab784.alpha, slab784.M, slab784.P, 1, 1)
+    out = []
+    for _ in range(2):
+        with gpu_ctx(slab784) as ctx:
+            ctx.set_k(samples)
+            out.append(ctx.forces())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_errors_are_reported(slab784):
+    with srbe.Context(slab784.box, slab784.alpha, slab784.eta, slab784.rc, 10, 2) as ctx:
+        with pytest.raises(srbe.SrbeError) as e:
+            ctx.forces()
+        assert e.value.code == srbe.SRBE_ESTATE
+        ctx.set_electrode(slab784.R, slab784.side)
+        with pytest.raises(srbe.SrbeError) as e:
+            ctx.set_k(np.array([[0, 0, 1]]))      # inside I
+        assert e.value.code == srbe.SRBE_EINVAL
+
+
+def test_md_steps_match_oracle(orc):
+    """Algorithm 1 with velocity Verlet: a few steps of the MD slab (3-site cations, LJ, bonds)
+    on a reduced copy, with the mode list of each step drawn by the oracle's own sampler."""
+    s = wl.make_slab("md_small", (2.0, 2.0, 12.0), 8, 8, 60, 3, alpha=3.5, eta_inv=19.79, rc=1.2, P=50, M=2,
+                     dpsi_volt=1.0, seed=21, ax=0.25, ay=0.25, with_md=True)
+    seed, nsteps = 77, 4
+    ref = orc.System(s, alpha_A=ALPHA_A)
+    r, v = s.r.copy(), s.v.copy()
+    m, c = ref.modes(orc.sample_metropolis(s.box, s.alpha, s.M, s.P, seed, 0))
+    F = orc.evaluate(ref.at(r), ref.factor, m, c)["F"]
+    for step in range(1, nsteps + 1):
+        m, c = ref.modes(orc.sample_metropolis(s.box, s.alpha, s.M, s.P, seed, step))
+        r, v, ev = ref.md_step(r, v, F, m, c)
+        F = ev["F"]
+    with gpu_ctx(s, md=True) as ctx:
+        ctx.step(nsteps, seed)
+        rg, vg = ctx.get_positions(velocities=True)
+    d = rg - r
+    d[:, :2] -= np.asarray(s.box[:2]) * np.round(d[:, :2] / np.asarray(s.box[:2]))
+    assert np.abs(d).max() < 1e-9
+    assert rel(vg, v) < 1e-8
