@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark: SRBE constant-potential MD steps/s on one GB300.
+
+Workload: the 4.0 x 4.0 x 16.0 nm slab with 2 x 3 walls of 32 x 16 electrode sites (3,072) and
+2,000 three-site cations + 2,000 anions (8,000 ion sites), P = 200 sampled modes, M = 4
+deterministic modes, alpha = 3.5 nm^-1, rc = 1.2 nm, 1 V, velocity Verlet with dt = 2 fs; seeded
+synthetic input (paper_2509_24742_gb300/workloads.py).  One step = Algorithm 1: sample the modes,
+S1, b, the charge solve, S2, forces (k-space, slab, real-space Coulomb, LJ, bonds), integrate.
+
+The headline arm is the mixed-precision form when its RMS force error against the FP64 GPU
+path at the same configuration and mode list is <= 1e-3; the FP64 path is timed beside it.
+L2 is flushed (a 256 MB write) between timed steps; each step is timed with CUDA events on the
+library's stream and the per-phase device times come from the library's own event tracing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SRBE MD steps/sec and ns/day on 1 GB300 at RMS force err <=1e-3 vs plain FP64 GPU"
+UNIT = "steps/s"
+DT_NS = 2e-6                        # 2 fs
+SEED = 3002
+FLUSH_BYTES = 256 << 20             # larger than the 129 MB L2
+PEAKS = {"hbm_gbs": 6694.5, "fp32_tflops": 152 * 128 * 2 * 2.070e9 / 1e12, "fp64_tflops": 1.25}
+# algorithmic flop counts per work unit (a transcendental counts as one flop):
+#   k-space mode evaluation: phase (5) + sin, cos (2) + accumulate into S or the gather (4..8) -> 12
+#   real-space pair within rc: distance (8) + erfc, exp (2) + kernel (8) + force accumulate (6)
+#   + LJ 12-6 (6) -> 30
+FLOP_MODE = 12
+FLOP_PAIR = 30
+
+
+def peaks():
+    p = dict(PEAKS)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        p["hbm_gbs"] = float(m.get("hbm_gbs", p["hbm_gbs"]))
+        p["hbm_source"] = "measured"
+    except (OSError, ValueError):
+        p["hbm_gbs"] = 6800.0
+        p["hbm_source"] = "fallback"
+    return p
+
+
+# ---------------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------- helpers
+def pair_counts(slab, r):
+    """Ion-ion pairs and ion-electrode pairs within rc (all in-plane images)."""
+    from scipy.spatial import cKDTree
+    Lx, Ly, _ = slab.box
+    big = 1e4
+    rr = np.array(r, float)
+    rr[:, 0] %= Lx
+    rr[:, 1] %= Ly
+    R = np.array(slab.R, float)
+    R[:, 0] %= Lx
+    R[:, 1] %= Ly
+    zoff = 1e3      # keep z inside the non-wrapping box
+    t = cKDTree(np.c_[rr[:, :2], rr[:, 2] + zoff], boxsize=[Lx, Ly, big])
+    te = cKDTree(np.c_[R[:, :2], R[:, 2] + zoff], boxsize=[Lx, Ly, big])
+    n_ii = len(t.query_pairs(slab.rc))
+    n_ie = int(t.count_neighbors(te, slab.rc))
+    return n_ii, n_ie
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel, precision):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if the kernel sources
+    have not changed since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = source_hash(["paper_2509_24742_gb300/csrc/realspace.cu", "paper_2509_24742_gb300/csrc/kspace.cu",
+                       "paper_2509_24742_gb300/csrc/solve.cu", "paper_2509_24742_gb300/csrc/srbe_internal.cuh"])
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == precision:
+            return float(parts[3]) if parts[2] == cur else None
+    return None
+
+
+def roofline(phase, ms_per_launch, slab, K, n_ii, n_ie, precision, pk):
+    """Roofline of the dominant phase: algorithmic work per launch / its event-timed duration."""
+    t = ms_per_launch * 1e-3
+    if phase == "solve":
+        byts = slab.n_ele ** 2 * 8 + 4 * slab.n_ele * 8     # FP64 projected inverse + vectors
+        ach = byts / t / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                "peak_source": pk["hbm_source"], "algorithmic_bytes": byts, "kernel": "k_gemv_rows"}
+    if phase == "forces":
+        flops = slab.n_ion * K * FLOP_MODE + (2 * n_ii + n_ie) * FLOP_PAIR
+        kern = "k_ion_forces"
+    elif phase in ("S1", "S2"):
+        n = slab.n_ion if phase == "S1" else slab.n_ele
+        flops = n * K * FLOP_MODE
+        kern = "k_sfac_partial"
+    elif phase == "rhs":
+        flops = slab.n_ele * K * FLOP_MODE + n_ie * FLOP_PAIR
+        kern = "k_electrode_rhs"
+    else:
+        return None
+    peak = pk["fp32_tflops"] if precision == "mixed" else pk["fp64_tflops"]
+    ach = flops / t / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "peak_source": "nominal (152 SMs x 128 FP32 lanes x 2 x 2070 MHz)" if precision == "mixed"
+            else "nominal GB300 FP64 1.25 TFLOP/s", "algorithmic_flops": flops, "kernel": kern}
+
+
+# ---------------------------------------------------------------------------------------------- GPU arm
+def gpu_arm(args, rank, world):
+    import torch
+    from paper_2509_24742_gb300 import srbe, workloads
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    pk = peaks()
+    slab = workloads.md_11072()
+    K = 2 * slab.M + slab.P
+    K_dev = slab.M + slab.P
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # accuracy gate: mixed vs FP64 GPU at the starting configuration, same mode list
+    ctxs = {}
+    for name, prec in (("fp64", srbe.FP64), ("mixed", srbe.MIXED)):
+        c = srbe.from_slab(slab, precision=prec, md=True)
+        c.set_stream(stream.cuda_stream)
+        c.sample_k(SEED, 0)
+        ctxs[name] = c
+    F64, Q64, _ = ctxs["fp64"].forces()
+    F32, Q32, _ = ctxs["mixed"].forces()
+    rms_f = float(np.sqrt(((F32 - F64) ** 2).sum(1).mean() / (F64 ** 2).sum(1).mean()))
+    rms_q = float(np.sqrt(((Q32 - Q64) ** 2).mean() / (Q64 ** 2).mean()))
+    head = "mixed" if rms_f <= 1e-3 else "fp64"
+
+    def timed(ctx, steps, warm):
+        ctx.step(warm, SEED)
+        torch.cuda.synchronize()
+        ctx.set_profiling(True)
+        l0, _ = ctx.counters()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            ev[i][0].record(stream)
+            ctx.step(1, SEED)
+            ev[i][1].record(stream)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        l1, _ = ctx.counters()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        phases = ctx.phase_times()
+        ctx.set_profiling(False)
+        return ms, phases, l1 - l0
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_head, ph_head, launches = timed(ctxs[head], args.steps, args.warmup)
+    clk = clocks.stop()
+    other = "fp64" if head == "mixed" else "mixed"
+    n_other = max(3, min(args.steps, 50))
+    ms_other, ph_other, _ = timed(ctxs[other], n_other, max(3, min(args.warmup, 5)))
+
+    if world > 1:
+        t = torch.tensor([ms_head], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_head = float(t.item())
+    value = world * args.steps / (ms_head * 1e-3)
+
+    # dominant phase and its roofline
+    per_step = {p: v[0] / args.steps for p, v in ph_head.items() if v[1]}
+    dom = max((p for p in per_step if p not in ("upload",)), key=lambda p: per_step[p])
+    r_end = ctxs[head].get_positions()
+    n_ii, n_ie = pair_counts(slab, r_end)
+    launches_dom = ph_head[dom][1]
+    roof = roofline(dom, ph_head[dom][0] / launches_dom, slab, K_dev, n_ii, n_ie, head, pk)
+    if roof is not None:
+        roof["traffic"] = committed_traffic(roof["kernel"], head)
+
+    # end to end through the host-pointer API: positions + charges in (pinned), forces + charges out
+    e2e = e2e_arm(ctxs[head], slab, stream, flush, max(5, min(args.steps, 50)))
+
+    for c in ctxs.values():
+        c.close()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_head / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
+        "ns_per_day": value * DT_NS * 86400 / world,
+        "config": {"workload": "md11072_P200: 4x4x16 nm slab, 3072 electrode + 8000 ion sites (2000 3-site "
+                               "cations, 2000 anions), P=200, M=4, alpha=3.5, rc=1.2, 1 V, dt=2 fs",
+                   "form": head, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "accuracy": {"rms_force_err_vs_fp64_gpu": rms_f, "rms_charge_err_vs_fp64_gpu": rms_q},
+        "roofline": roof,
+        "phases_ms_per_step": {p: round(v, 5) for p, v in per_step.items()},
+        "other_form": {"form": other, "steps_per_s": n_other / (ms_other * 1e-3),
+                       "phases_ms_per_step": {p: round(v[0] / n_other, 5) for p, v in ph_other.items() if v[1]}},
+        "pairs_within_rc": {"ion_ion": n_ii, "ion_electrode": n_ie},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    return out
+
+
+def e2e_arm(ctx, slab, stream, flush, steps):
+    import torch
+    n, ne = slab.n_ion, slab.n_ele
+    r_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    q_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    F_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    Q_h = torch.empty(ne, dtype=torch.float64).pin_memory()
+    r_h.numpy()[:] = slab.r
+    q_h.numpy()[:] = slab.q
+    rn, qn, Fn, Qn = r_h.numpy(), q_h.numpy(), F_h.numpy(), Q_h.numpy()
+    for i in range(3):
+        ctx.set_positions(rn, qn)
+        ctx.sample_k(SEED, 10_000 + i)
+        ctx.forces(out=(Fn, Qn))
+    tot = 0.0
+    for i in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_positions(rn, qn)
+        ctx.sample_k(SEED, 20_000 + i)
+        ctx.forces(out=(Fn, Qn))
+        tot += time.perf_counter() - t0
+        with torch.cuda.stream(stream):
+            flush.zero_()
+    return {"value": steps / tot, "unit": UNIT, "h2d_bytes_per_step": int(rn.nbytes + qn.nbytes),
+            "d2h_bytes_per_step": int(Fn.nbytes + Qn.nbytes),
+            "what": "host-pointer force provider: srbe_set_positions + srbe_sample_k + srbe_forces per step"}
+
+
+# ---------------------------------------------------------------------------------------------- CPU oracle
+def oracle_steps(budget_s, max_steps, min_steps=2):
+    """Full oracle MD steps (plain FP64 C, OpenMP over independent output elements) on the same
+    workload; the one-time A build is not timed.  Returns (steps, seconds, threads)."""
+    from oracle import oracle
+    from paper_2509_24742_gb300 import workloads
+    slab = workloads.md_11072()
+    sysm = oracle.System(slab, alpha_A=1.25)
+    r, v = slab.r.copy(), slab.v.copy()
+    m, c = sysm.modes(oracle.sample_metropolis(slab.box, slab.alpha, slab.M, slab.P, SEED, 0))
+    F = oracle.evaluate(sysm.at(r), sysm.factor, m, c)["F"]
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps and (n < min_steps or time.perf_counter() - t0 < budget_s):
+        m, c = sysm.modes(oracle.sample_metropolis(slab.box, slab.alpha, slab.M, slab.P, SEED, n + 1))
+        r, v, ev = sysm.md_step(r, v, F, m, c)
+        F = ev["F"]
+        n += 1
+    return n, time.perf_counter() - t0, int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline():
+    n, t, cores = oracle_steps(budget_s=12.0, max_steps=50)
+    return {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d full oracle MD steps of the same workload (A built once, untimed)" % n}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return None
+    n, t, cores = oracle_steps(budget_s=90.0, max_steps=args.steps)
+    value = n / t
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n,
+            "warmup": 0, "ms_per_step": 1e3 * t / n, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "md11072_P200 (as the GPU arm)", "form": "CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "first %d of %d requested full MD steps (bounded to ~90 s)" % (n, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        out = reference_arm(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = gpu_arm(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -149,8 +149,18 @@ int srbe_set_positions_dev(srbe_ctx *ctx, int64_t n_ion, const double *r_dev, co
 int srbe_forces_dev(srbe_ctx *ctx, double *F_dev, double *Q_dev);
 
 /* Counters for benchmarking: kernels launched by this context since creation, and the
- * k-space work units (particle x mode evaluations) of the last force evaluation. */
+ * k-space work units (particle x mode evaluations) since creation. */
 int srbe_get_counters(const srbe_ctx *ctx, int64_t *kernel_launches, int64_t *mode_evals);
+
+/* Phase tracing (no counterpart in the paper; a measurement aid).  When on, every pass records a
+ * CUDA event pair on the context's stream around each phase of Algorithm 1:
+ *   0 mode-list upload, 1 cell lists, 2 S1 (ions), 3 b (electrode right-hand side),
+ *   4 charge solve, 5 S2 (electrode), 6 ion forces, 7 integration, 8 energies.
+ * srbe_get_phase_times synchronises the stream and returns, per phase, the summed device time
+ * (ms) and the number of timed intervals since tracing was switched on (arrays of 9; either
+ * may be NULL).  Switching tracing on resets the sums. */
+int srbe_set_profiling(srbe_ctx *ctx, int on);
+int srbe_get_phase_times(srbe_ctx *ctx, double *ms, int64_t *count);
 
 #ifdef __cplusplus
 }

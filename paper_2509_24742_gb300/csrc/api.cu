@@ -251,12 +251,59 @@ struct srbe::HostExt {
   ModeSampler sampler;
   DevBuf<double> aos;      // AoS staging for positions / forces
   bool forces_valid = false;
+  // phase tracing: a pool of event pairs, drained into per-phase sums when full or on request
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_phase;
+  size_t ev_used = 0;
+  int open_phase[kPhCount];
+  double ms[kPhCount];
+  int64_t count[kPhCount];
+  ~HostExt() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
 };
 
 namespace {
 using Extra = srbe::HostExt;
 Extra *extra(srbe_ctx *c) { return c->hx; }
+
+constexpr size_t kEventPool = 4096;   // event pairs per drain
+
+void drain_events(srbe_ctx *c) {
+  Extra *e = extra(c);
+  if (!e->ev_used) return;
+  SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < e->ev_used; ++i) {
+    float t = 0.f;
+    SRBE_CUDA(cudaEventElapsedTime(&t, e->ev[2 * i], e->ev[2 * i + 1]));
+    e->ms[e->ev_phase[i]] += t;
+    e->count[e->ev_phase[i]]++;
+  }
+  e->ev_used = 0;
+}
 }  // namespace
+
+namespace srbe {
+void phase_begin(srbe_ctx *c, int ph) {
+  if (!c->profiling) return;
+  Extra *e = extra(c);
+  if (e->ev_used == kEventPool) drain_events(c);
+  if (e->ev.empty()) {
+    e->ev.resize(2 * kEventPool);
+    e->ev_phase.resize(kEventPool);
+    for (auto &x : e->ev) SRBE_CUDA(cudaEventCreate(&x));
+  }
+  e->open_phase[ph] = (int)e->ev_used;
+  e->ev_phase[e->ev_used] = ph;
+  SRBE_CUDA(cudaEventRecord(e->ev[2 * e->ev_used], c->stream));
+  e->ev_used++;
+}
+void phase_end(srbe_ctx *c, int ph) {
+  if (!c->profiling) return;
+  Extra *e = extra(c);
+  SRBE_CUDA(cudaEventRecord(e->ev[2 * e->open_phase[ph] + 1], c->stream));
+}
+}  // namespace srbe
 
 namespace srbe {
 
@@ -309,10 +356,12 @@ void upload_modes(srbe_ctx *c) {
   c->dc.ensure(std::max(K, 1));
   c->S1.ensure(std::max(K, 1));
   c->S2.ensure(std::max(K, 1));
+  phase_begin(c, kPhUpload);
   if (K > 0) {
     SRBE_CUDA(cudaMemcpyAsync(c->dm.p, c->h_mode_stage, sizeof(int4) * K, cudaMemcpyHostToDevice, c->stream));
     SRBE_CUDA(cudaMemcpyAsync(c->dc.p, c->h_w_stage, sizeof(double) * K, cudaMemcpyHostToDevice, c->stream));
   }
+  phase_end(c, kPhUpload);
   SRBE_CUDA(cudaEventRecord(c->stage_done, c->stream));
   c->K = K;
   c->have_modes = true;
@@ -354,18 +403,34 @@ void require_state(srbe_ctx *c, bool pos) {
 
 void charges_pass(srbe_ctx *c) {
   reserve(c);
+  phase_begin(c, kPhCells);
   build_cells(c, c->icells, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->have_md ? c->itype.p : nullptr,
               c->have_md ? c->mol.p : nullptr, true);
+  phase_end(c, kPhCells);
+  phase_begin(c, kPhS1);
   structure_factor(c, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->S1.p, nullptr, kScalMion);
+  phase_end(c, kPhS1);
+  phase_begin(c, kPhRhs);
   electrode_rhs(c);
+  phase_end(c, kPhRhs);
+  phase_begin(c, kPhSolve);
   charge_update(c);
+  phase_end(c, kPhSolve);
 }
 
 void forces_pass(srbe_ctx *c, bool energies) {
   charges_pass(c);
+  phase_begin(c, kPhS2);
   structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele);
+  phase_end(c, kPhS2);
+  phase_begin(c, kPhForces);
   ion_forces(c, energies);
-  if (energies) energy_scalars(c);
+  phase_end(c, kPhForces);
+  if (energies) {
+    phase_begin(c, kPhEnergy);
+    energy_scalars(c);
+    phase_end(c, kPhEnergy);
+  }
 }
 
 void sample_into(srbe_ctx *c, uint64_t seed, uint64_t step) {
@@ -802,11 +867,40 @@ int srbe_step(srbe_ctx *c, int nsteps, uint64_t seed0) {
     for (int s = 0; s < nsteps; ++s) {
       c->md_step++;
       sample_into(c, seed0, c->md_step);
+      phase_begin(c, kPhIntegrate);
       integrate_kick_drift(c, 0.5 * c->dt, true);
+      phase_end(c, kPhIntegrate);
       forces_pass(c, false);
+      phase_begin(c, kPhIntegrate);
       integrate_kick_drift(c, 0.5 * c->dt, false);
+      phase_end(c, kPhIntegrate);
     }
     SRBE_CUDA(cudaGetLastError());
+  });
+}
+
+int srbe_set_profiling(srbe_ctx *c, int on) {
+  return guarded(c, [&] {
+    Extra *e = extra(c);
+    if (on) {
+      drain_events(c);
+      for (int p = 0; p < kPhCount; ++p) {
+        e->ms[p] = 0.0;
+        e->count[p] = 0;
+      }
+    }
+    c->profiling = on != 0;
+  });
+}
+
+int srbe_get_phase_times(srbe_ctx *c, double *ms, int64_t *count) {
+  return guarded(c, [&] {
+    drain_events(c);
+    Extra *e = extra(c);
+    for (int p = 0; p < kPhCount; ++p) {
+      if (ms) ms[p] = e->ms[p];
+      if (count) count[p] = e->count[p];
+    }
   });
 }
 

@@ -168,6 +168,9 @@ struct srbe_ctx {
 
   srbe::HostExt *hx = nullptr;
 
+  // phase tracing
+  bool profiling = false;
+
   // counters
   int64_t launches = 0;
   int64_t mode_evals = 0;
@@ -246,6 +249,9 @@ void ion_forces(srbe_ctx *c, bool energies);
 void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift);
 void build_A_and_inverse(srbe_ctx *c);
 void energy_scalars(srbe_ctx *c);
+enum Phase { kPhUpload = 0, kPhCells, kPhS1, kPhRhs, kPhSolve, kPhS2, kPhForces, kPhIntegrate, kPhEnergy, kPhCount };
+void phase_begin(srbe_ctx *c, int ph);
+void phase_end(srbe_ctx *c, int ph);
 void reserve(srbe_ctx *c);
 int64_t sfac_chunks(int64_t n, int K, int64_t *chunk);
 

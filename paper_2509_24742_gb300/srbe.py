@@ -58,7 +58,10 @@ EXPORTS = {
     "srbe_set_positions_dev": ([_vp, _i64, _vp, _vp], _int),
     "srbe_forces_dev": ([_vp, _vp, _vp], _int),
     "srbe_get_counters": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _int),
+    "srbe_set_profiling": ([_vp, _int], _int),
+    "srbe_get_phase_times": ([_vp, _dp, ctypes.POINTER(_i64)], _int),
 }
+PHASES = ("upload", "cells", "S1", "rhs", "solve", "S2", "forces", "integrate", "energy")
 
 
 def library_path():
@@ -208,9 +211,16 @@ class Context:
         self._check(self.lib.srbe_solve_electrode_charges(self.h, _ptr(Q), ctypes.byref(psi), _ptr(b)))
         return Q, psi.value, b
 
-    def forces(self, energy=False):
-        F = np.empty((self.n_ion, 3))
-        Q = np.empty(self.n_ele)
+    def forces(self, energy=False, out=None):
+        """F (kJ/mol/nm), Q (e), psi_bar (V)[, energy terms].  `out=(F, Q)` writes into given
+        C-contiguous float64 arrays (e.g. views of pinned host memory) instead of new ones."""
+        if out is not None:
+            F, Q = out
+            assert F.dtype == np.float64 and F.flags.c_contiguous and F.size == 3 * self.n_ion
+            assert Q.dtype == np.float64 and Q.flags.c_contiguous and Q.size == self.n_ele
+        else:
+            F = np.empty((self.n_ion, 3))
+            Q = np.empty(self.n_ele)
         psi = ctypes.c_double()
         E = np.empty(8) if energy else None
         self._check(self.lib.srbe_forces(self.h, _ptr(F), _ptr(Q), ctypes.byref(psi),
@@ -222,6 +232,16 @@ class Context:
 
     def step(self, nsteps, seed0):
         self._check(self.lib.srbe_step(self.h, int(nsteps), int(seed0)))
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.srbe_set_profiling(self.h, 1 if on else 0))
+
+    def phase_times(self):
+        """{phase: (total ms, intervals)} since profiling was switched on."""
+        ms = np.zeros(len(PHASES))
+        cnt = (_i64 * len(PHASES))()
+        self._check(self.lib.srbe_get_phase_times(self.h, _ptr(ms), cnt))
+        return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
 
     def counters(self):
         a, b = _i64(), _i64()
