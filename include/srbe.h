@@ -162,6 +162,26 @@ int srbe_get_counters(const srbe_ctx *ctx, int64_t *kernel_launches, int64_t *mo
 int srbe_set_profiling(srbe_ctx *ctx, int on);
 int srbe_get_phase_times(srbe_ctx *ctx, double *ms, int64_t *count);
 
+/* Structure factor without any device allocation (no counterpart in the paper; an interface
+ * for callers that cannot allocate device memory, e.g. an MD engine that hands out every byte of
+ * GPU memory from its own pool, or code that must not allocate while its pipeline runs).
+ * Computes S(k) = sum_j w_j exp(i k . r_j) (Eq. 15 form) in FP64 for
+ *   box      host [3]: periodic lengths (nm), k = 2 pi m / L componentwise
+ *   r_dev    device [n][3] positions, w_dev device [n] weights (charges), n >= 0
+ *   m_dev    device [K][3] integer modes, 0 <= K <= 8192
+ *   S_dev    device [K][2] output (re, im), overwritten
+ *   stream   cudaStream_t as void* (NULL: legacy default stream); the call is asynchronous
+ * Partial sums go to one fixed 2 MiB array (131072 double2) compiled into the library, next to a
+ * 16 KiB sin/cos table; every GPU that loads the library holds both until the process exits.
+ * The first call on each device does its set-up (looks up the arrays' device addresses and
+ * copies the table in, with that device current), so make that first call before any stream
+ * capture.  Every call shares the array and leaves its partials there; each partial is written
+ * before it is read, so nothing has to be cleared, but calls that overlap on the GPU race on it.
+ * Allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ * Errors: SRBE_EINVAL (bad box, n < 0, K outside [0, 8192], null pointers), SRBE_ECUDA. */
+int srbe_structure_factor_noalloc(const double box[3], int64_t n, const double *r_dev, const double *w_dev, int K,
+                                  const int32_t *m_dev, double *S_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

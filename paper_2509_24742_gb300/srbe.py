@@ -60,6 +60,7 @@ EXPORTS = {
     "srbe_get_counters": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _int),
     "srbe_set_profiling": ([_vp, _int], _int),
     "srbe_get_phase_times": ([_vp, _dp, ctypes.POINTER(_i64)], _int),
+    "srbe_structure_factor_noalloc": ([_dp, _i64, _vp, _vp, _int, _vp, _vp, _vp], _int),
 }
 PHASES = ("upload", "cells", "S1", "rhs", "solve", "S2", "forces", "integrate", "energy")
 
@@ -247,6 +248,17 @@ class Context:
         a, b = _i64(), _i64()
         self._check(self.lib.srbe_get_counters(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+
+def structure_factor_noalloc(box, n, r_ptr, w_ptr, K, m_ptr, S_ptr, stream_ptr=None):
+    """S(k) for caller-owned device buffers (r [n][3], w [n], m [K][3] int32, S [K][2]) without
+    any device allocation by the library; see include/srbe.h for the limits."""
+    L = load()
+    b = _d(box, 3)
+    code = L.srbe_structure_factor_noalloc(_ptr(b), int(n), _vp(r_ptr), _vp(w_ptr), int(K), _vp(m_ptr),
+                                           _vp(S_ptr), _vp(stream_ptr) if stream_ptr else None)
+    if code != SRBE_OK:
+        raise SrbeError(code, "srbe_structure_factor_noalloc failed")
 
 
 def from_slab(slab, precision=FP64, alpha_A=0.0, md=False):
