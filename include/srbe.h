@@ -143,6 +143,13 @@ int srbe_forces(srbe_ctx *ctx, double *F, double *Q, double *psi_bar, double *en
  * sites stay fixed, ions wrap in x and y.  State stays on the device. */
 int srbe_step(srbe_ctx *ctx, int nsteps, uint64_t seed0);
 
+/* Relaxes the ions before MD by nsteps of displacement-capped steepest descent on the full
+ * force of srbe_forces (Coulomb with the CP charges, LJ, bonds): r_i += F_i min(a, dmax / |F_i|)
+ * with a in nm^2 mol/kJ and dmax in nm; the modes of iteration t are drawn with
+ * srbe_sample_k(seed, t).  No counterpart in the paper (the synthetic workloads start from a
+ * random packing); needs srbe_set_md.  Velocities are kept. */
+int srbe_minimize(srbe_ctx *ctx, int nsteps, double a, double dmax, uint64_t seed);
+
 /* Device-resident variants: same as the host calls, with device pointers on the context's
  * stream and no host copies.  F_dev [n_ion*3], Q_dev [n_ele] may be NULL. */
 int srbe_set_positions_dev(srbe_ctx *ctx, int64_t n_ion, const double *r_dev, const double *q_dev);

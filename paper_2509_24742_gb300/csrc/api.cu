@@ -227,6 +227,15 @@ __global__ void k_deinterleave(int64_t n, const double *__restrict__ r, double L
   z[i] = r[3 * i + 2];
 }
 
+__global__ void k_site_turns(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                             const double *__restrict__ z, double3 invL, uint64_t *__restrict__ u) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  u[i] = to_turns64(x[i], invL.x);
+  u[n + i] = to_turns64(y[i], invL.y);
+  u[2 * n + i] = to_turns64(z[i], invL.z);
+}
+
 __global__ void k_interleave(int64_t n, const double *__restrict__ F, double *__restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -325,7 +334,9 @@ void reserve(srbe_ctx *c) {
   c->partial.ensure((size_t)std::max<int64_t>(nch, 1) * K);
   c->mpart.ensure((size_t)std::max<int64_t>(nch, 1));
   c->coef.ensure((size_t)K);
-  const size_t nblk = blocks_for(std::max<int64_t>(c->ni, 1), 128);
+  c->coef32.ensure((size_t)K);
+  c->Q32.ensure((size_t)std::max<int64_t>(c->ne, 1));
+  const size_t nblk = blocks_for(std::max<int64_t>(c->ni, 1), kWarpsPerBlock);
   const size_t neb = blocks_for(std::max<int64_t>(c->ne, 1), 128);
   c->epart.ensure(nblk * 4 + 4 + neb + 8);
   c->scal.ensure(kScalCount);
@@ -614,7 +625,14 @@ int srbe_set_electrode(srbe_ctx *c, int64_t n_ele, const double *R, const int8_t
     const double pad = 0.5 * (c->L[2] - (zmax - zmin));
     choose_grid(c, c->ecells.g, zmin - pad, zmax + pad);
     c->icells.g = c->ecells.g;
+    build_run_table(c);
     build_cells(c, c->ecells, n_ele, c->ex.p, c->ey.p, c->ez.p, nullptr, nullptr, nullptr, false);
+    c->eu.ensure(3 * (size_t)n_ele);
+    k_site_turns<<<blocks_for(n_ele, 256), 256, 0, c->stream>>>(n_ele, c->ex.p, c->ey.p, c->ez.p,
+                                                               make_double3(1.0 / c->L[0], 1.0 / c->L[1],
+                                                                            1.0 / c->L[2]),
+                                                               c->eu.p);
+    SRBE_CUDA(cudaGetLastError());
     build_A_and_inverse(c);
     c->have_ele = true;
     extra(c)->forces_valid = false;
@@ -758,6 +776,9 @@ int srbe_set_md(srbe_ctx *c, const double *mass, const double *v, int ntype, con
       SRBE_CUDA(cudaMemcpy(c->mol.p, mol, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
     }
     SRBE_CUDA(cudaMemcpy(c->lj.p, lj.data(), sizeof(double) * lj.size(), cudaMemcpyHostToDevice));
+    std::vector<float> lj32(lj.begin(), lj.end());
+    c->lj32.ensure(lj32.size() / 2);
+    SRBE_CUDA(cudaMemcpy(c->lj32.p, lj32.data(), sizeof(float) * lj32.size(), cudaMemcpyHostToDevice));
     SRBE_CUDA(cudaMemcpy(c->bond_start.p, start.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
     if (nb > 0) {
       SRBE_CUDA(cudaMemcpy(c->bond_j.p, bj.data(), sizeof(int32_t) * 2 * nb, cudaMemcpyHostToDevice));
@@ -901,6 +922,21 @@ int srbe_get_phase_times(srbe_ctx *c, double *ms, int64_t *count) {
       if (ms) ms[p] = e->ms[p];
       if (count) count[p] = e->count[p];
     }
+  });
+}
+
+int srbe_minimize(srbe_ctx *c, int nsteps, double a, double dmax, uint64_t seed) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(nsteps >= 0 && a > 0 && dmax > 0 && std::isfinite(a) && std::isfinite(dmax), SRBE_EINVAL,
+                 "bad minimisation parameters");
+    SRBE_REQUIRE(c->have_ele && c->have_pos && c->have_md, SRBE_ESTATE, "electrode, positions and MD terms needed");
+    for (int t = 0; t < nsteps; ++t) {
+      sample_into(c, seed, (uint64_t)t);
+      forces_pass(c, false);
+      steepest_descent_move(c, a, dmax);
+    }
+    extra(c)->forces_valid = false;
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
   });
 }
 

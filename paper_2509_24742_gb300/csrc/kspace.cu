@@ -12,7 +12,8 @@
 
 namespace srbe {
 
-constexpr int kSfThreads = 128;
+constexpr int kSfThreads = 128;              // 4 warps; a block covers 32 modes x a particle chunk
+constexpr int kSfMaxChunks = 512;
 
 // FP32 Kahan-compensated accumulator (the mixed form's "compensated sums").
 struct KahanF {
@@ -26,20 +27,21 @@ struct KahanF {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// partial[c][k] = sum over the particles of chunk c of w_j exp(i k . r_j).  Lane = mode (32 per
+// block in y), the four warps take every fourth particle of each staged batch of 128, and the
+// four warp sums are added in warp order.  Blocks with blockIdx.y == 0 also sum w z per chunk.
 template <bool F32>
 __global__ void __launch_bounds__(kSfThreads)
 k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                const double *__restrict__ w, int K, const int4 *__restrict__ modes, double3 invL,
-               const double2 *__restrict__ gtab, int64_t chunk, double2 *__restrict__ partial,
+               const double2 *__restrict__ tab, int64_t chunk, double2 *__restrict__ partial,
                double *__restrict__ mpart) {
-  __shared__ double2 tab[F32 ? 1 : kTab];
-  __shared__ uint64_t sux[kSfThreads], suy[kSfThreads], suz[kSfThreads];
+  __shared__ uint64_t su[3][kSfThreads];
   __shared__ double sw[kSfThreads];
-  __shared__ double red[kSfThreads];
-  const int t = threadIdx.x;
-  if (!F32)
-    for (int i = t; i < kTab; i += kSfThreads) tab[i] = gtab[i];
-  const int kidx = blockIdx.y * kSfThreads + t;
+  __shared__ double2 red[4][32];
+  __shared__ double mred[kSfThreads];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int kidx = blockIdx.y * 32 + lane;
   const int4 m = kidx < K ? modes[kidx] : make_int4(0, 0, 0, 0);
   const int64_t i0 = (int64_t)blockIdx.x * chunk;
   const int64_t i1 = min(n, i0 + chunk);
@@ -49,32 +51,30 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
     __syncthreads();
     const int64_t i = base + t;
     if (i < i1) {
-      sux[t] = to_turns64(x[i], invL.x);
-      suy[t] = to_turns64(y[i], invL.y);
-      suz[t] = to_turns64(z[i], invL.z);
+      su[0][t] = to_turns64(x[i], invL.x);
+      su[1][t] = to_turns64(y[i], invL.y);
+      su[2][t] = to_turns64(z[i], invL.z);
       sw[t] = w[i];
       if (blockIdx.y == 0) mz = fma(w[i], z[i], mz);
     }
     __syncthreads();
     const int cnt = (int)min((int64_t)kSfThreads, i1 - base);
-    if (kidx < K) {
-      if (!F32) {
-        for (int j = 0; j < cnt; ++j) {
-          double c, s;
-          sincos_turns(phase64(m, sux[j], suy[j], suz[j]), tab, c, s);
-          are = fma(sw[j], c, are);
-          aim = fma(sw[j], s, aim);
-        }
-      } else {
-        for (int j = 0; j < cnt; ++j) {
-          const uint32_t th = (uint32_t)m.x * (uint32_t)(sux[j] >> 32) + (uint32_t)m.y * (uint32_t)(suy[j] >> 32) +
-                              (uint32_t)m.z * (uint32_t)(suz[j] >> 32);
-          float c, s;
-          sincos_turns32(th, c, s);
-          const float wf = (float)sw[j];
-          fre.add(wf * c);
-          fim.add(wf * s);
-        }
+    if (!F32) {
+      for (int j = warp; j < cnt; j += 4) {
+        double c, s;
+        sincos_turns(phase64(m, su[0][j], su[1][j], su[2][j]), tab, c, s);
+        are = fma(sw[j], c, are);
+        aim = fma(sw[j], s, aim);
+      }
+    } else {
+      for (int j = warp; j < cnt; j += 4) {
+        const uint32_t th = (uint32_t)m.x * (uint32_t)(su[0][j] >> 32) + (uint32_t)m.y * (uint32_t)(su[1][j] >> 32) +
+                            (uint32_t)m.z * (uint32_t)(su[2][j] >> 32);
+        float c, s;
+        sincos_turns32(th, c, s);
+        const float wf = (float)sw[j];
+        fre.add(wf * c);
+        fim.add(wf * s);
       }
     }
   }
@@ -82,66 +82,87 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
     are = fre.value();
     aim = fim.value();
   }
-  if (kidx < K) partial[(int64_t)blockIdx.x * K + kidx] = make_double2(are, aim);
+  red[warp][lane] = make_double2(are, aim);
+  __syncthreads();
+  if (warp == 0 && kidx < K) {
+    double2 a = red[0][lane];
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      a.x += red[q][lane].x;
+      a.y += red[q][lane].y;
+    }
+    partial[(int64_t)blockIdx.x * K + kidx] = a;
+  }
   if (blockIdx.y == 0) {
     // fixed-order block reduction of sum w z
-    red[t] = mz;
+    mred[t] = mz;
     __syncthreads();
     for (int s = kSfThreads / 2; s > 0; s >>= 1) {
-      if (t < s) red[t] += red[t + s];
+      if (t < s) mred[t] += mred[t + s];
       __syncthreads();
     }
-    if (t == 0) mpart[blockIdx.x] = red[0];
+    if (t == 0) mpart[blockIdx.x] = mred[0];
   }
 }
 
-// S[k] = sum over chunks (in order) of the partials (+ S_add[k]); thread K sums the dipole
-// partials into scal[mslot].
+// S[k] = sum over chunks of the partials (+ S_add[k]): one warp per mode, lanes take chunks
+// lane, lane + 32, ..., then a butterfly sum (every lane ends with the same value).  Warp K sums
+// the dipole partials into scal[mslot].
 __global__ void k_sfac_reduce(int K, int nchunk, const double2 *__restrict__ partial, const double *__restrict__ mpart,
                               double2 *__restrict__ S, const double2 *__restrict__ S_add, double *__restrict__ scal,
                               int mslot) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (k > K) return;
+  double re = 0.0, im = 0.0;
   if (k < K) {
-    double re = 0.0, im = 0.0;
-    for (int c = 0; c < nchunk; ++c) {
+    for (int c = lane; c < nchunk; c += 32) {
       const double2 p = partial[(int64_t)c * K + k];
       re += p.x;
       im += p.y;
     }
-    if (S_add) {
-      re += S_add[k].x;
-      im += S_add[k].y;
+  } else {
+    for (int c = lane; c < nchunk; c += 32) re += mpart[c];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) {
+    if (k < K) {
+      if (S_add) {
+        re += S_add[k].x;
+        im += S_add[k].y;
+      }
+      S[k] = make_double2(re, im);
+    } else {
+      scal[mslot] = re;
     }
-    S[k] = make_double2(re, im);
-  } else if (k == K) {
-    double m = 0.0;
-    for (int c = 0; c < nchunk; ++c) m += mpart[c];
-    scal[mslot] = m;
   }
 }
 
-// chunking of the particle sum: about four waves of blocks over the 152 SMs, chunks of whole
-// 128-particle batches
+// chunking of the particle sum: whole 128-particle batches, at most kSfMaxChunks chunks
 int64_t sfac_chunks(int64_t n, int K, int64_t *chunk) {
-  const int ktiles = std::max(1, (K + kSfThreads - 1) / kSfThreads);
+  (void)K;
   if (n <= 0) {
     *chunk = kSfThreads;
     return 0;
   }
-  int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (4 * 152 + ktiles - 1) / ktiles));
-  int64_t ch = (n + nchunk - 1) / nchunk;
-  ch = ((ch + kSfThreads - 1) / kSfThreads) * kSfThreads;
-  *chunk = ch;
-  return (n + ch - 1) / ch;
+  const int64_t batches = (n + kSfThreads - 1) / kSfThreads;
+  const int64_t per = (batches + kSfMaxChunks - 1) / kSfMaxChunks;
+  *chunk = per * kSfThreads;
+  return (n + *chunk - 1) / *chunk;
 }
 
 void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *w,
                       double2 *S, const double2 *S_add, int mslot) {
   const int K = c->K;
-  const int ktiles = std::max(1, (K + kSfThreads - 1) / kSfThreads);
+  const int ktiles = std::max(1, (K + 31) / 32);
   int64_t chunk;
   const int64_t nchunk = sfac_chunks(n, K, &chunk);
-  SRBE_REQUIRE(c->partial.cap >= (size_t)std::max<int64_t>(nchunk * K, 1) && c->mpart.cap >= (size_t)std::max<int64_t>(nchunk, 1),
+  SRBE_REQUIRE(c->partial.cap >= (size_t)std::max<int64_t>(nchunk * K, 1) &&
+                   c->mpart.cap >= (size_t)std::max<int64_t>(nchunk, 1),
                SRBE_ESTATE, "scratch buffers not reserved for this size");
   const double3 invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
   if (nchunk > 0) {
@@ -155,8 +176,8 @@ void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, 
     c->launches++;
     c->mode_evals += n * (int64_t)K;
   }
-  k_sfac_reduce<<<blocks_for(K + 1, 128), 128, 0, c->stream>>>(K, (int)nchunk, c->partial.p, c->mpart.p, S, S_add,
-                                                               c->scal.p, mslot);
+  k_sfac_reduce<<<blocks_for((int64_t)(K + 1) * 32, 256), 256, 0, c->stream>>>(K, (int)nchunk, c->partial.p,
+                                                                               c->mpart.p, S, S_add, c->scal.p, mslot);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }

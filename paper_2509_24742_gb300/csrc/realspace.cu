@@ -14,8 +14,6 @@ namespace srbe {
 
 constexpr double kKe = 138.935458;            // kJ mol^-1 nm e^-2
 constexpr double kTwoOverSqrtPi = 1.1283791670955126;
-constexpr int kGatherThreads = 128;
-constexpr int kModeTile = 256;
 
 struct GridDev {
   int nc[3];
@@ -49,6 +47,40 @@ void choose_grid(const srbe_ctx *c, CellGrid &g, double zlo, double zhi) {
   g.cs[2] = h / g.nc[2];
   g.span[2] = (int)std::ceil(c->rc / g.cs[2] - 1e-12);
   g.z0 = zlo;
+}
+
+static int host_floor_div(int a, int n) { return a >= 0 ? a / n : -((-a + n - 1) / n); }
+
+void build_run_table(srbe_ctx *c) {
+  const CellGrid &g = c->ecells.g;
+  std::vector<int4> runs;
+  std::vector<int32_t> first(g.ncell() + 1, 0);
+  for (int cz = 0; cz < g.nc[2]; ++cz)
+    for (int cy = 0; cy < g.nc[1]; ++cy)
+      for (int cx = 0; cx < g.nc[0]; ++cx) {
+        const int cell = (cz * g.nc[1] + cy) * g.nc[0] + cx;
+        first[cell] = (int32_t)runs.size();
+        for (int zc = std::max(0, cz - g.span[2]); zc <= std::min(g.nc[2] - 1, cz + g.span[2]); ++zc)
+          for (int oy = -g.span[1]; oy <= g.span[1]; ++oy) {
+            const int yy = cy + oy, iy = host_floor_div(yy, g.nc[1]);
+            const int rowbase = (zc * g.nc[1] + (yy - iy * g.nc[1])) * g.nc[0];
+            int ox = -g.span[0];
+            while (ox <= g.span[0]) {
+              const int xx = cx + ox, ix = host_floor_div(xx, g.nc[0]), ccx = xx - ix * g.nc[0];
+              const int run = std::min(g.span[0] - ox + 1, g.nc[0] - ccx);
+              runs.push_back(make_int4(rowbase + ccx, run, (ix + 512) | ((iy + 512) << 10), 0));
+              ox += run;
+            }
+          }
+      }
+  first[g.ncell()] = (int32_t)runs.size();
+  c->runtab.runs.ensure(runs.size());
+  c->runtab.first.ensure(first.size());
+  SRBE_CUDA(cudaMemcpyAsync(c->runtab.runs.p, runs.data(), sizeof(int4) * runs.size(), cudaMemcpyHostToDevice,
+                            c->stream));
+  SRBE_CUDA(cudaMemcpyAsync(c->runtab.first.p, first.data(), sizeof(int32_t) * first.size(),
+                            cudaMemcpyHostToDevice, c->stream));
+  SRBE_CUDA(cudaStreamSynchronize(c->stream));
 }
 
 __device__ __forceinline__ int cell_coord(double v, double inv, int n) {
@@ -100,19 +132,35 @@ __global__ void k_scatter(int64_t n, const int32_t *__restrict__ cell, const int
   if (i < n) order[start[cell[i]] + rank[i]] = (int32_t)i;
 }
 
-// insertion sort of each cell's entries by particle index (cells hold tens of particles)
+// sorts each cell's entries by particle index: one warp per cell; cells of up to 32 entries are
+// ranked with shuffles, larger ones fall back to an insertion sort by lane 0
 __global__ void k_sort_cells(int ncell, const int32_t *__restrict__ start, int32_t *__restrict__ order) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (c >= ncell) return;
-  const int b = start[c], e = start[c + 1];
-  for (int i = b + 1; i < e; ++i) {
-    int32_t v = order[i];
-    int j = i - 1;
-    while (j >= b && order[j] > v) {
-      order[j + 1] = order[j];
-      --j;
+  const int b = start[c], e = start[c + 1], n = e - b;
+  if (n <= 1) return;
+  if (n <= 32) {
+    const int32_t v = lane < n ? order[b + lane] : 0x7fffffff;
+    int rank = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int32_t w = __shfl_sync(0xffffffffu, v, l);
+      rank += (w < v) ? 1 : 0;
     }
-    order[j + 1] = v;
+    __syncwarp();
+    if (lane < n) order[b + rank] = v;
+    return;
+  }
+  if (lane == 0) {
+    for (int i = b + 1; i < e; ++i) {
+      int32_t v = order[i];
+      int j = i - 1;
+      while (j >= b && order[j] > v) {
+        order[j + 1] = order[j];
+        --j;
+      }
+      order[j + 1] = v;
+    }
   }
 }
 
@@ -121,17 +169,19 @@ __global__ void k_gather_sorted(int64_t n, const int32_t *__restrict__ order, co
                                 const double *__restrict__ w, const int32_t *__restrict__ typ,
                                 const int32_t *__restrict__ mol, double *__restrict__ xs, double *__restrict__ ys,
                                 double *__restrict__ zs, double *__restrict__ ws, int32_t *__restrict__ ts,
-                                int32_t *__restrict__ ms, float *__restrict__ xf, float *__restrict__ yf,
-                                float *__restrict__ zf) {
+                                int32_t *__restrict__ ms, float4 *__restrict__ pf, uint64_t *__restrict__ us,
+                                int32_t *__restrict__ inv, double3 invL) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int32_t i = order[p];
+  inv[i] = (int32_t)p;
+  us[p] = to_turns64(x[i], invL.x);
+  us[n + p] = to_turns64(y[i], invL.y);
+  us[2 * n + p] = to_turns64(z[i], invL.z);
   xs[p] = x[i];
   ys[p] = y[i];
   zs[p] = z[i];
-  xf[p] = (float)x[i];
-  yf[p] = (float)y[i];
-  zf[p] = (float)z[i];
+  pf[p] = make_float4((float)x[i], (float)y[i], (float)z[i], w ? (float)w[i] : 0.f);
   if (w) ws[p] = w[i];
   if (typ) ts[p] = typ[i];
   if (mol) ms[p] = mol[i];
@@ -151,9 +201,9 @@ void build_cells(srbe_ctx *c, Cells &cl, int64_t n, const double *x, const doubl
   cl.ws.ensure(nn);
   cl.ts.ensure(nn);
   cl.ms.ensure(nn);
-  cl.xf.ensure(nn);
-  cl.yf.ensure(nn);
-  cl.zf.ensure(nn);
+  cl.pf.ensure(nn);
+  cl.us.ensure(3 * nn);
+  cl.inv.ensure(nn);
   SRBE_CUDA(cudaMemsetAsync(cl.start.p, 0, sizeof(int32_t) * ((size_t)ncell + 1), c->stream));
   const GridDev g = to_dev(cl.g);
   if (n > 0) {
@@ -164,10 +214,11 @@ void build_cells(srbe_ctx *c, Cells &cl, int64_t n, const double *x, const doubl
   c->launches++;
   if (n > 0) {
     k_scatter<<<blocks_for(n, 256), 256, 0, c->stream>>>(n, cl.cell.p, cl.rank.p, cl.start.p, cl.order.p);
-    k_sort_cells<<<blocks_for(ncell, 128), 128, 0, c->stream>>>(ncell, cl.start.p, cl.order.p);
+    k_sort_cells<<<blocks_for((int64_t)ncell * 32, 256), 256, 0, c->stream>>>(ncell, cl.start.p, cl.order.p);
     k_gather_sorted<<<blocks_for(n, 256), 256, 0, c->stream>>>(n, cl.order.p, x, y, z, w, typ, mol, cl.xs.p, cl.ys.p,
-                                                              cl.zs.p, cl.ws.p, cl.ts.p, cl.ms.p, cl.xf.p, cl.yf.p,
-                                                              cl.zf.p);
+                                                              cl.zs.p, cl.ws.p, cl.ts.p, cl.ms.p, cl.pf.p, cl.us.p,
+                                                              cl.inv.p, make_double3(1.0 / c->L[0], 1.0 / c->L[1],
+                                                                           1.0 / c->L[2]));
     c->launches += 3;
   }
   SRBE_CUDA(cudaGetLastError());
@@ -228,10 +279,15 @@ struct CellsDev {
   const int32_t *start, *order;
   const double *xs, *ys, *zs, *ws;
   const int32_t *ts, *ms;
-  const float *xf, *yf, *zf;
+  const float4 *pf;
+  const uint64_t *us;
+  const int32_t *inv;
+  const int4 *runs;
+  const int32_t *run_first;
+  int64_t n;
 };
 
-static CellsDev cells_dev(const Cells &cl) {
+static CellsDev cells_dev(const Cells &cl, const RunTable &rt) {
   CellsDev d;
   d.g = to_dev(cl.g);
   d.start = cl.start.p;
@@ -242,14 +298,20 @@ static CellsDev cells_dev(const Cells &cl) {
   d.ws = cl.ws.p;
   d.ts = cl.ts.p;
   d.ms = cl.ms.p;
-  d.xf = cl.xf.p;
-  d.yf = cl.yf.p;
-  d.zf = cl.zf.p;
+  d.pf = cl.pf.p;
+  d.us = cl.us.p;
+  d.inv = cl.inv.p;
+  d.runs = rt.runs.p;
+  d.run_first = rt.first.p;
+  d.n = 0;
   return d;
 }
 
-// Visits every (neighbour, image) within the stencil of a point: fn(p, sx, sy, ix, iy) with p the
-// sorted index, (sx, sy) the image shift to add to the neighbour and (ix, iy) the image index.
+// Visits every (neighbour, image) within the stencil of a point, serially: fn(p, sx, sy, ix, iy)
+// with p the sorted index, (sx, sy) the image shift to add to the neighbour and (ix, iy) the image
+// index.  Used by the energy diagnostics; the hot gathers split the stencil over a warp.
+__device__ __forceinline__ int floor_div(int a, int n) { return a >= 0 ? a / n : -((-a + n - 1) / n); }
+
 template <class Fn>
 __device__ __forceinline__ void for_stencil(const CellsDev &C, double x, double y, double z, double Lx, double Ly,
                                             Fn &&fn) {
@@ -258,16 +320,16 @@ __device__ __forceinline__ void for_stencil(const CellsDev &C, double x, double 
   const int cy = cell_coord(y, g.inv[1], g.nc[1]);
   const int cz = cell_coord(z - g.z0, g.inv[2], g.nc[2]);
   const int z_lo = max(0, cz - g.span[2]), z_hi = min(g.nc[2] - 1, cz + g.span[2]);
-  for (int dz = z_lo; dz <= z_hi; ++dz) {
+  for (int zc = z_lo; zc <= z_hi; ++zc) {
     for (int oy = -g.span[1]; oy <= g.span[1]; ++oy) {
       const int yy = cy + oy;
-      const int iy = (yy >= 0) ? yy / g.nc[1] : -((-yy + g.nc[1] - 1) / g.nc[1]);
+      const int iy = floor_div(yy, g.nc[1]);
       const int ccy = yy - iy * g.nc[1];
       for (int ox = -g.span[0]; ox <= g.span[0]; ++ox) {
         const int xx = cx + ox;
-        const int ix = (xx >= 0) ? xx / g.nc[0] : -((-xx + g.nc[0] - 1) / g.nc[0]);
+        const int ix = floor_div(xx, g.nc[0]);
         const int ccx = xx - ix * g.nc[0];
-        const int cell = (dz * g.nc[1] + ccy) * g.nc[0] + ccx;
+        const int cell = (zc * g.nc[1] + ccy) * g.nc[0] + ccx;
         const int b = C.start[cell], e = C.start[cell + 1];
         for (int p = b; p < e; ++p) fn(p, ix * Lx, iy * Ly, ix, iy);
       }
@@ -275,110 +337,296 @@ __device__ __forceinline__ void for_stencil(const CellsDev &C, double x, double 
   }
 }
 
+// Butterfly sum over a warp.  Each step adds two lanes' values, and a + b == b + a exactly, so
+// every lane ends with the same, run-to-run reproducible, value.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct KahanF32 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c, t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+  __device__ __forceinline__ float valuef() const { return s - c; }
+};
+
+// FP32 pre-check margin: positions below 64 nm carry at most ~4e-6 nm of rounding in FP32
+constexpr float kPrecheckMargin = 1e-3f;
+
+struct MdDev {
+  int ntype;                        // 0 = no LJ / bonds
+  const double2 *lj;                // (sigma^2, eps) per type pair
+  const float2 *lj32;               // the same in FP32 (mixed form)
+  const int32_t *bond_start, *bond_j;
+  const double *bond_r0;
+  double kb;
+};
+
+// Per-ion constants and accumulators of the real-space pair sums.  Candidate neighbours that pass
+// the cutoff test are first compacted into a per-warp queue (index, image) in shared memory, so
+// that the pair arithmetic always runs on 32 pairs at once instead of on the ~20% of lanes whose
+// candidate falls inside rc.
+struct PairSite {
+  double X, Y, Z, qi, Lx, Ly, alpha, eta, rc2;
+  float Xf, Yf, Zf, qf, Lxf, Lyf, af, etaf;
+  int ti, mi;
+  int64_t p;
+};
+
+struct PairAcc {
+  KahanF32 c0, c1, c2, l0, l1, l2;   // FP32 form: Coulomb (Gaussian units) and LJ
+  float eii = 0.f, eie = 0.f, elj = 0.f;
+  double r[3] = {0, 0, 0}, l[3] = {0, 0, 0};   // FP64 form
+  double dii = 0, die = 0, dlj = 0;
+};
+
+__device__ __forceinline__ int pack_image(int ix, int iy) { return (ix + 512) | ((iy + 512) << 10); }
+__device__ __forceinline__ int image_x(int v) { return (v & 1023) - 512; }
+__device__ __forceinline__ int image_y(int v) { return ((v >> 10) & 1023) - 512; }
+
+template <bool F32>
+__device__ __forceinline__ void pair_ion_ion(const PairSite &S, const CellsDev &ions, const MdDev &md, int2 e,
+                                             PairAcc &A) {
+  const int pp = e.x, ix = image_x(e.y), iy = image_y(e.y);
+  const bool lj = md.ntype && ions.ms[pp] != S.mi;
+  if (F32) {
+    const float4 o = ions.pf[pp];
+    const float dx = S.Xf - (o.x + (float)ix * S.Lxf), dy = S.Yf - (o.y + (float)iy * S.Lyf), dz = S.Zf - o.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    float phi, md2;
+    pair_ii_f(r2, S.af, phi, md2);
+    const float qq = S.qf * o.w, s = qq * md2;
+    A.c0.add(s * dx);
+    A.c1.add(s * dy);
+    A.c2.add(s * dz);
+    A.eii += 0.5f * qq * phi;
+    if (lj) {
+      const float2 sg = md.lj32[S.ti * md.ntype + ions.ts[pp]];
+      const float sr2 = sg.x / r2, sr6 = sr2 * sr2 * sr2;
+      const float fs = 24.f * sg.y * (2.f * sr6 * sr6 - sr6) / r2;
+      A.l0.add(fs * dx);
+      A.l1.add(fs * dy);
+      A.l2.add(fs * dz);
+      A.elj += 2.f * sg.y * (sr6 * sr6 - sr6);
+    }
+  } else {
+    const double dx = S.X - (ions.xs[pp] + ix * S.Lx), dy = S.Y - (ions.ys[pp] + iy * S.Ly), dz = S.Z - ions.zs[pp];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= S.rc2) return;
+    double phi, md2;
+    pair_ii(r2, S.alpha, phi, md2);
+    const double qq = S.qi * ions.ws[pp], s = qq * md2;
+    A.r[0] = fma(s, dx, A.r[0]);
+    A.r[1] = fma(s, dy, A.r[1]);
+    A.r[2] = fma(s, dz, A.r[2]);
+    A.dii = fma(0.5 * qq, phi, A.dii);
+    if (lj) {
+      const double2 sg = md.lj[S.ti * md.ntype + ions.ts[pp]];
+      const double sr2 = sg.x / r2, sr6 = sr2 * sr2 * sr2;
+      const double fs = 24.0 * sg.y * (2.0 * sr6 * sr6 - sr6) / r2;
+      A.l[0] = fma(fs, dx, A.l[0]);
+      A.l[1] = fma(fs, dy, A.l[1]);
+      A.l[2] = fma(fs, dz, A.l[2]);
+      A.dlj += 0.5 * 4.0 * sg.y * (sr6 * sr6 - sr6);
+    }
+  }
+}
+
+template <bool F32>
+__device__ __forceinline__ void pair_ion_ele(const PairSite &S, const CellsDev &eles, const MdDev &md,
+                                             const double *__restrict__ Q, const float *__restrict__ Q32, int2 e,
+                                             PairAcc &A) {
+  const int pe = e.x, ix = image_x(e.y), iy = image_y(e.y);
+  if (F32) {
+    const float4 o = eles.pf[pe];
+    const float dx = S.Xf - (o.x + (float)ix * S.Lxf), dy = S.Yf - (o.y + (float)iy * S.Lyf), dz = S.Zf - o.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float Qj = Q32[eles.order[pe]];
+    float phi, md2;
+    pair_ie_f(r2, S.af, S.etaf, phi, md2);
+    const float s = S.qf * Qj * md2;
+    A.c0.add(s * dx);
+    A.c1.add(s * dy);
+    A.c2.add(s * dz);
+    A.eie += S.qf * Qj * phi;
+    if (md.ntype) {
+      const float2 sg = md.lj32[S.ti * md.ntype + (md.ntype - 1)];
+      const float sr2 = sg.x / r2, sr6 = sr2 * sr2 * sr2;
+      const float fs = 24.f * sg.y * (2.f * sr6 * sr6 - sr6) / r2;
+      A.l0.add(fs * dx);
+      A.l1.add(fs * dy);
+      A.l2.add(fs * dz);
+      A.elj += 4.f * sg.y * (sr6 * sr6 - sr6);
+    }
+  } else {
+    const double dx = S.X - (eles.xs[pe] + ix * S.Lx), dy = S.Y - (eles.ys[pe] + iy * S.Ly), dz = S.Z - eles.zs[pe];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= S.rc2 || r2 == 0.0) return;
+    const double Qj = Q[eles.order[pe]];
+    double phi, md2;
+    pair_ie(r2, S.alpha, S.eta, phi, md2);
+    const double s = S.qi * Qj * md2;
+    A.r[0] = fma(s, dx, A.r[0]);
+    A.r[1] = fma(s, dy, A.r[1]);
+    A.r[2] = fma(s, dz, A.r[2]);
+    A.die = fma(S.qi * Qj, phi, A.die);
+    if (md.ntype) {
+      const double2 sg = md.lj[S.ti * md.ntype + (md.ntype - 1)];
+      const double sr2 = sg.x / r2, sr6 = sr2 * sr2 * sr2;
+      const double fs = 24.0 * sg.y * (2.0 * sr6 * sr6 - sr6) / r2;
+      A.l[0] = fma(fs, dx, A.l[0]);
+      A.l[1] = fma(fs, dy, A.l[1]);
+      A.l[2] = fma(fs, dz, A.l[2]);
+      A.dlj += 4.0 * sg.y * (sr6 * sr6 - sr6);
+    }
+  }
+}
+
+// Walks the stencil of S over the cell list C and compacts candidates with squared distance below
+// cut2 (FP32 test) into the warp queue q; calls pair(entry) for every full batch of 32 and once
+// more for the rest.  All lanes of the warp take part; skip_self drops the zero image of S.p.
+template <class Pair>
+__device__ __forceinline__ void compacted_pairs(const PairSite &S, const CellsDev &C, bool skip_self, float cut2,
+                                                int2 *q, int lane, Pair &&pair) {
+  const GridDev &g = C.g;
+  const int cell = (cell_coord(S.Z - g.z0, g.inv[2], g.nc[2]) * g.nc[1] + cell_coord(S.Y, g.inv[1], g.nc[1])) *
+                       g.nc[0] + cell_coord(S.X, g.inv[0], g.nc[0]);
+  int qn = 0;
+  const unsigned below = (1u << lane) - 1u;
+  const int r1 = C.run_first[cell + 1];
+  for (int r = C.run_first[cell]; r < r1; ++r) {
+    const int4 R = C.runs[r];
+    const int b0 = C.start[R.x], b1 = C.start[R.x + R.y];
+    if (b0 == b1) continue;
+    const int ix = image_x(R.z), iy = image_y(R.z);
+    const float sxf = (float)ix * S.Lxf, syf = (float)iy * S.Lyf;
+    const bool zero_image = skip_self && ix == 0 && iy == 0;
+    const int img = R.z;
+    for (int base = b0; base < b1; base += 32) {
+      const int pp = base + lane;
+      bool in = false;
+      if (pp < b1 && !(zero_image && pp == S.p)) {
+        const float4 o = C.pf[pp];
+        const float dx = S.Xf - (o.x + sxf), dy = S.Yf - (o.y + syf), dz = S.Zf - o.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        in = r2 < cut2 && r2 > 0.f;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (in) q[qn + __popc(m & below)] = make_int2(pp, img);
+      qn += __popc(m);
+      if (qn >= 32) {
+        __syncwarp();
+        pair(q[lane]);
+        __syncwarp();
+        if (lane < qn - 32) q[lane] = q[lane + 32];
+        __syncwarp();
+        qn -= 32;
+      }
+    }
+  }
+  __syncwarp();
+  if (lane < qn) pair(q[lane]);
+  __syncwarp();
+}
+
 // ------------------------------------------------------------------------------------------------
-// electrode right-hand side
+// electrode right-hand side: one warp per electrode site, lanes split the modes and the stencil
 // ------------------------------------------------------------------------------------------------
 // coefS[k] = (c_k Re S1(k), c_k Im S1(k));  b_F,j = - sum_k Re(exp(-i k.R_j) c_k S1) (Eq. 24)
 template <bool F32>
 __global__ void __launch_bounds__(kGatherThreads)
 k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restrict__ ey,
-                const double *__restrict__ ez, int K, const int4 *__restrict__ modes,
-                const double2 *__restrict__ coefS, const double2 *__restrict__ gtab, double3 invL, CellsDev ions,
+                const double *__restrict__ ez, const uint64_t *__restrict__ eu, int K, const int4 *__restrict__ modes,
+                const double2 *__restrict__ coefS, const float2 *__restrict__ coefS32,
+                const double2 *__restrict__ tab, double3 invL, CellsDev ions,
                 double Lx, double Ly, double alpha, double eta, double rc, double slab, const double *__restrict__ scal,
                 double *__restrict__ b) {
-  __shared__ double2 tab[F32 ? 1 : kTab];
-  __shared__ int4 sm[kModeTile];
-  __shared__ double2 sc[kModeTile];
-  const int t = threadIdx.x;
-  if (!F32)
-    for (int i = t; i < kTab; i += kGatherThreads) tab[i] = gtab[i];
-  const int64_t j = (int64_t)blockIdx.x * kGatherThreads + t;
-  const bool live = j < ne;
-  double X = 0, Y = 0, Z = 0;
-  uint64_t ux = 0, uy = 0, uz = 0;
-  if (live) {
-    X = ex[j];
-    Y = ey[j];
-    Z = ez[j];
-    ux = to_turns64(X, invL.x);
-    uy = to_turns64(Y, invL.y);
-    uz = to_turns64(Z, invL.z);
-  }
+  __shared__ int2 wq[kWarpsPerBlock][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t j = ((int64_t)blockIdx.x * kGatherThreads + threadIdx.x) >> 5;
+  if (j >= ne) return;                        // whole warps leave together; no block barrier below
+  const double X = ex[j], Y = ey[j], Z = ez[j];
+  const uint64_t ux = eu[j], uy = eu[ne + j], uz = eu[2 * ne + j];
   double acc = 0.0;
-  float facc = 0.f, fcmp = 0.f;
-  for (int k0 = 0; k0 < K; k0 += kModeTile) {
-    __syncthreads();
-    for (int k = t; k < kModeTile && k0 + k < K; k += kGatherThreads) {
-      sm[k] = modes[k0 + k];
-      sc[k] = coefS[k0 + k];
+  KahanF32 fk;
+  if (!F32) {
+    for (int k = lane; k < K; k += 32) {
+      double cs, sn;
+      sincos_turns(phase64(__ldg(&modes[k]), ux, uy, uz), tab, cs, sn);
+      const double2 cf = __ldg(&coefS[k]);
+      acc = fma(-cf.x, cs, acc);
+      acc = fma(-cf.y, sn, acc);
     }
-    __syncthreads();
-    const int cnt = min(kModeTile, K - k0);
-    if (live) {
-      if (!F32) {
-        for (int k = 0; k < cnt; ++k) {
-          double cs, sn;
-          sincos_turns(phase64(sm[k], ux, uy, uz), tab, cs, sn);
-          acc = fma(-sc[k].x, cs, acc);
-          acc = fma(-sc[k].y, sn, acc);
-        }
-      } else {
-        const uint32_t vx = (uint32_t)(ux >> 32), vy = (uint32_t)(uy >> 32), vz = (uint32_t)(uz >> 32);
-        for (int k = 0; k < cnt; ++k) {
-          const int4 m = sm[k];
-          float cs, sn;
-          sincos_turns32((uint32_t)m.x * vx + (uint32_t)m.y * vy + (uint32_t)m.z * vz, cs, sn);
-          const float term = -(float)sc[k].x * cs - (float)sc[k].y * sn;
-          const float yv = term - fcmp, tv = facc + yv;
-          fcmp = (tv - facc) - yv;
-          facc = tv;
-        }
-      }
+  } else {
+    const uint32_t vx = (uint32_t)(ux >> 32), vy = (uint32_t)(uy >> 32), vz = (uint32_t)(uz >> 32);
+    for (int k = lane; k < K; k += 32) {
+      const int4 m = __ldg(&modes[k]);
+      float cs, sn;
+      sincos_turns32((uint32_t)m.x * vx + (uint32_t)m.y * vy + (uint32_t)m.z * vz, cs, sn);
+      const float2 cf = __ldg(&coefS32[k]);
+      fk.add(-cf.x * cs - cf.y * sn);
     }
   }
-  if (F32) acc = (double)facc - (double)fcmp;
-  if (!live) return;
-  // near part of Eq. 19: - sum_i q_i [erfc(alpha d) - erfc(d/eta)] / d over images within rc
-  const double rc2 = rc * rc;
-  if (!F32) {
-    double near = 0.0;
-    for_stencil(ions, X, Y, Z, Lx, Ly, [&](int p, double sx, double sy, int, int) {
-      const double dx = X - (ions.xs[p] + sx), dy = Y - (ions.ys[p] + sy), dz = Z - ions.zs[p];
+  // near part of Eq. 19: - sum_i q_i [erfc(alpha d) - erfc(d/eta)] / d over images within rc,
+  // candidates compacted through the warp queue
+  PairSite S;
+  S.X = X; S.Y = Y; S.Z = Z; S.qi = 0.0; S.Lx = Lx; S.Ly = Ly; S.alpha = alpha; S.eta = eta; S.rc2 = rc * rc;
+  S.Xf = (float)X; S.Yf = (float)Y; S.Zf = (float)Z; S.qf = 0.f;
+  S.Lxf = (float)Lx; S.Lyf = (float)Ly; S.af = (float)alpha; S.etaf = (float)eta;
+  S.ti = 0; S.mi = -1; S.p = -1;
+  const float rcf = (float)rc;
+  const float cut2 = F32 ? rcf * rcf : (rcf + kPrecheckMargin) * (rcf + kPrecheckMargin);
+  KahanF32 fn;
+  double near = 0.0;
+  compacted_pairs(S, ions, false, cut2, wq[warp], lane, [&](int2 e) {
+    const int pp = e.x, ix = image_x(e.y), iy = image_y(e.y);
+    if (F32) {
+      const float4 o = ions.pf[pp];
+      const float dx = S.Xf - (o.x + (float)ix * S.Lxf), dy = S.Yf - (o.y + (float)iy * S.Lyf), dz = S.Zf - o.z;
+      float phi, md;
+      pair_ie_f(dx * dx + dy * dy + dz * dz, S.af, S.etaf, phi, md);
+      fn.add(-o.w * phi);
+    } else {
+      const double dx = X - (ions.xs[pp] + ix * Lx), dy = Y - (ions.ys[pp] + iy * Ly), dz = Z - ions.zs[pp];
       const double r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < rc2 && r2 > 0.0) {
+      if (r2 < S.rc2 && r2 > 0.0) {
         double phi, md;
         pair_ie(r2, alpha, eta, phi, md);
-        near = fma(-ions.ws[p], phi, near);
+        near = fma(-ions.ws[pp], phi, near);
       }
-    });
-    acc += near;
+    }
+  });
+  if (F32) {
+    // FP32 to the end of the warp sum: on this GPU every FP64 warp instruction is costly
+    const float accf = warp_sum_f(fk.valuef() + fn.valuef());
+    if (lane == 0) b[j] = fma(-slab * Z, scal[kScalMion], (double)accf);
   } else {
-    const float Xf = (float)X, Yf = (float)Y, Zf = (float)Z, rc2f = (float)rc2;
-    float ns = 0.f, nc = 0.f;
-    for_stencil(ions, X, Y, Z, Lx, Ly, [&](int p, double sx, double sy, int, int) {
-      const float dx = Xf - (ions.xf[p] + (float)sx), dy = Yf - (ions.yf[p] + (float)sy), dz = Zf - ions.zf[p];
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < rc2f && r2 > 0.f) {
-        float phi, md;
-        pair_ie_f(r2, (float)alpha, (float)eta, phi, md);
-        const float yv = -(float)ions.ws[p] * phi - nc, tv = ns + yv;
-        nc = (tv - ns) - yv;
-        ns = tv;
-      }
-    });
-    acc += (double)ns - (double)nc;
+    acc = warp_sum(acc + near);
+    // slab part (FP64 in every form): -(4 pi / V) Z_j sum_i q_i z_i
+    if (lane == 0) b[j] = fma(-slab * Z, scal[kScalMion], acc);
   }
-  // slab part (FP64 in every form): -(4 pi / V) Z_j sum_i q_i z_i
-  acc = fma(-slab * Z, scal[kScalMion], acc);
-  b[j] = acc;
 }
 
 __global__ void k_coef(int K, const double *__restrict__ c, const double2 *__restrict__ S, double2 *__restrict__ out,
-                       int swap) {
+                       float2 *__restrict__ out32, int swap) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < K) {
     const double2 s = S[k];
-    out[k] = swap ? make_double2(c[k] * s.y, c[k] * s.x) : make_double2(c[k] * s.x, c[k] * s.y);
+    const double2 v = swap ? make_double2(c[k] * s.y, c[k] * s.x) : make_double2(c[k] * s.x, c[k] * s.y);
+    out[k] = v;
+    out32[k] = make_float2((float)v.x, (float)v.y);
   }
 }
 
@@ -386,275 +634,194 @@ void electrode_rhs(srbe_ctx *c) {
   const int K = c->K;
   double2 *coef = c->coef.p;
   if (K > 0) {
-    k_coef<<<blocks_for(K, 128), 128, 0, c->stream>>>(K, c->dc.p, c->S1.p, coef, 0);
+    k_coef<<<blocks_for(K, 128), 128, 0, c->stream>>>(K, c->dc.p, c->S1.p, coef, c->coef32.p, 0);
     c->launches++;
   }
   const double3 invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
   const double slab = 4.0 * kPi / c->V;
-  const CellsDev ions = cells_dev(c->icells);
+  const CellsDev ions = cells_dev(c->icells, c->runtab);
+  const unsigned nb = blocks_for(c->ne, kWarpsPerBlock);
   if (c->precision == SRBE_MIXED)
-    k_electrode_rhs<true><<<blocks_for(c->ne, kGatherThreads), kGatherThreads, 0, c->stream>>>(
-        c->ne, c->ex.p, c->ey.p, c->ez.p, K, c->dm.p, coef, c->tab.p, invL, ions, c->L[0], c->L[1], c->alpha,
-        c->eta, c->rc, slab, c->scal.p, c->bvec.p);
+    k_electrode_rhs<true><<<nb, kGatherThreads, 0, c->stream>>>(c->ne, c->ex.p, c->ey.p, c->ez.p, c->eu.p, K, c->dm.p,
+                                                               coef,
+                                                               c->coef32.p, c->tab.p, invL, ions, c->L[0], c->L[1], c->alpha,
+                                                               c->eta, c->rc, slab, c->scal.p, c->bvec.p);
   else
-    k_electrode_rhs<false><<<blocks_for(c->ne, kGatherThreads), kGatherThreads, 0, c->stream>>>(
-        c->ne, c->ex.p, c->ey.p, c->ez.p, K, c->dm.p, coef, c->tab.p, invL, ions, c->L[0], c->L[1], c->alpha,
-        c->eta, c->rc, slab, c->scal.p, c->bvec.p);
+    k_electrode_rhs<false><<<nb, kGatherThreads, 0, c->stream>>>(c->ne, c->ex.p, c->ey.p, c->ez.p, c->eu.p, K, c->dm.p,
+                                                               coef,
+                                                                c->coef32.p, c->tab.p, invL, ions, c->L[0], c->L[1], c->alpha,
+                                                                c->eta, c->rc, slab, c->scal.p, c->bvec.p);
   c->launches++;
   c->mode_evals += c->ne * (int64_t)K;
   SRBE_CUDA(cudaGetLastError());
 }
 
 // ------------------------------------------------------------------------------------------------
-// ion forces
+// ion forces: one warp per ion, lanes split the modes and the stencil cells
 // ------------------------------------------------------------------------------------------------
-struct MdDev {
-  int ntype;                        // 0 = no LJ / bonds
-  const double2 *lj;                // (sigma^2, eps) per type pair
-  const int32_t *bond_start, *bond_j;
-  const double *bond_r0;
-  double kb;
-};
 
 // coefF[k] = (c_k Im S(k), c_k Re S(k)) with S = S1 + S2;
 // F_i = - q_i sum_k c_k k Im(S exp(-i k . r_i)) = - q_i sum_k k (cIm cos - cRe sin)   (Eq. 25)
 template <bool F32>
 __global__ void __launch_bounds__(kGatherThreads)
-k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, const double *__restrict__ Q, int K,
-             const int4 *__restrict__ modes, const double2 *__restrict__ coefF, const double2 *__restrict__ gtab,
-             double3 invL, double Lx, double Ly, double alpha, double eta, double rc, double slab,
+k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, const double *__restrict__ Q, const float *__restrict__ Q32,
+             int K, const int4 *__restrict__ modes, const double2 *__restrict__ coefF,
+             const float2 *__restrict__ coefF32, const double2 *__restrict__ tab,
+             double3 invL, float3 kvf, double Lx, double Ly, double alpha, double eta, double rc, double slab,
              const double *__restrict__ scal, MdDev md, const double *__restrict__ x_orig,
              const double *__restrict__ y_orig, const double *__restrict__ z_orig, double *__restrict__ F,
              double *__restrict__ epart) {
-  __shared__ double2 tab[F32 ? 1 : kTab];
-  __shared__ int4 sm[kModeTile];
-  __shared__ double2 sc[kModeTile];
-  __shared__ double red[4][kGatherThreads];
-  const int t = threadIdx.x;
-  if (!F32)
-    for (int i = t; i < kTab; i += kGatherThreads) tab[i] = gtab[i];
-  const int64_t p = (int64_t)blockIdx.x * kGatherThreads + t;
-  const bool live = p < ni;
-  int32_t i = 0;
-  double X = 0, Y = 0, Z = 0, qi = 0;
-  int ti = 0, mi = -1;
-  uint64_t ux = 0, uy = 0, uz = 0;
-  if (live) {
-    i = ions.order[p];
-    X = ions.xs[p];
-    Y = ions.ys[p];
-    Z = ions.zs[p];
-    qi = ions.ws[p];
-    ti = ions.ts ? ions.ts[p] : 0;
-    mi = ions.ms ? ions.ms[p] : -1;
-    ux = to_turns64(X, invL.x);
-    uy = to_turns64(Y, invL.y);
-    uz = to_turns64(Z, invL.z);
-  }
-  // ---- k-space gather
-  double fk[3] = {0, 0, 0};
-  float ff[3] = {0, 0, 0}, fc[3] = {0, 0, 0};
-  const double tpx = 2.0 * kPi * invL.x, tpy = 2.0 * kPi * invL.y, tpz = 2.0 * kPi * invL.z;
-  for (int k0 = 0; k0 < K; k0 += kModeTile) {
-    __syncthreads();
-    for (int k = t; k < kModeTile && k0 + k < K; k += kGatherThreads) {
-      sm[k] = modes[k0 + k];
-      sc[k] = coefF[k0 + k];
+  __shared__ double red[kWarpsPerBlock][4];
+  __shared__ int2 wq[kWarpsPerBlock][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  double e_ii = 0, e_ie = 0, e_lj = 0, e_b = 0;
+  if (p < ni) {
+    const int32_t i = ions.order[p];
+    const double X = ions.xs[p], Y = ions.ys[p], Z = ions.zs[p], qi = ions.ws[p];
+    const int ti = ions.ts ? ions.ts[p] : 0;
+    const int mi = ions.ms ? ions.ms[p] : -1;
+    const uint64_t ux = ions.us[p], uy = ions.us[ni + p], uz = ions.us[2 * ni + p];
+    const double tpx = 2.0 * kPi * invL.x, tpy = 2.0 * kPi * invL.y, tpz = 2.0 * kPi * invL.z;
+    // ---- k-space gather
+    double fk[3] = {0, 0, 0};
+    KahanF32 ak0, ak1, ak2;
+    if (!F32) {
+      for (int k = lane; k < K; k += 32) {
+        const int4 m = __ldg(&modes[k]);
+        double cs, sn;
+        sincos_turns(phase64(m, ux, uy, uz), tab, cs, sn);
+        const double2 cf = __ldg(&coefF[k]);
+        const double im = fma(cf.x, cs, -cf.y * sn);
+        fk[0] = fma(tpx * m.x, im, fk[0]);
+        fk[1] = fma(tpy * m.y, im, fk[1]);
+        fk[2] = fma(tpz * m.z, im, fk[2]);
+      }
+    } else {
+      const uint32_t vx = (uint32_t)(ux >> 32), vy = (uint32_t)(uy >> 32), vz = (uint32_t)(uz >> 32);
+      for (int k = lane; k < K; k += 32) {
+        const int4 m = __ldg(&modes[k]);
+        float cs, sn;
+        sincos_turns32((uint32_t)m.x * vx + (uint32_t)m.y * vy + (uint32_t)m.z * vz, cs, sn);
+        const float2 cf = __ldg(&coefF32[k]);
+        const float im = cf.x * cs - cf.y * sn;
+        ak0.add(kvf.x * (float)m.x * im);
+        ak1.add(kvf.y * (float)m.y * im);
+        ak2.add(kvf.z * (float)m.z * im);
+      }
     }
-    __syncthreads();
-    const int cnt = min(kModeTile, K - k0);
-    if (live) {
-      if (!F32) {
-        for (int k = 0; k < cnt; ++k) {
-          const int4 m = sm[k];
-          double cs, sn;
-          sincos_turns(phase64(m, ux, uy, uz), tab, cs, sn);
-          const double im = fma(sc[k].x, cs, -sc[k].y * sn);
-          fk[0] = fma(tpx * m.x, im, fk[0]);
-          fk[1] = fma(tpy * m.y, im, fk[1]);
-          fk[2] = fma(tpz * m.z, im, fk[2]);
-        }
-      } else {
-        const uint32_t vx = (uint32_t)(ux >> 32), vy = (uint32_t)(uy >> 32), vz = (uint32_t)(uz >> 32);
-        const float kx = (float)tpx, ky = (float)tpy, kz = (float)tpz;
-        for (int k = 0; k < cnt; ++k) {
-          const int4 m = sm[k];
-          float cs, sn;
-          sincos_turns32((uint32_t)m.x * vx + (uint32_t)m.y * vy + (uint32_t)m.z * vz, cs, sn);
-          const float im = (float)sc[k].x * cs - (float)sc[k].y * sn;
-          const float v[3] = {kx * (float)m.x * im, ky * (float)m.y * im, kz * (float)m.z * im};
+    // ---- real space: Coulomb of Eq. 13 (Gaussian units) and LJ (kJ/mol/nm), compacted pairs
+    PairSite S;
+    S.X = X; S.Y = Y; S.Z = Z; S.qi = qi; S.Lx = Lx; S.Ly = Ly; S.alpha = alpha; S.eta = eta; S.rc2 = rc * rc;
+    const float4 self = ions.pf[p];
+    S.Xf = self.x; S.Yf = self.y; S.Zf = self.z; S.qf = self.w;
+    S.Lxf = (float)Lx; S.Lyf = (float)Ly; S.af = (float)alpha; S.etaf = (float)eta;
+    S.ti = ti; S.mi = mi; S.p = p;
+    const float rcf = (float)rc;
+    const float cut2 = F32 ? rcf * rcf : (rcf + kPrecheckMargin) * (rcf + kPrecheckMargin);
+    PairAcc A;
+    int2 *q = wq[warp];
+    compacted_pairs(S, ions, true, cut2, q, lane, [&](int2 e) { pair_ion_ion<F32>(S, ions, md, e, A); });
+    compacted_pairs(S, eles, false, cut2, q, lane, [&](int2 e) { pair_ion_ele<F32>(S, eles, md, Q, Q32, e, A); });
+    const float Xf = S.Xf, Yf = S.Yf, Zf = S.Zf, qf = S.qf;
+    double rr[3] = {A.r[0], A.r[1], A.r[2]}, ll[3] = {A.l[0], A.l[1], A.l[2]};
+    e_ii = A.dii;
+    e_ie = A.die;
+    e_lj = A.dlj;
+    float eii = A.eii, eie = A.eie, elj = A.elj;
+    KahanF32 &ka0 = A.c0, &ka1 = A.c1, &ka2 = A.c2, &ka3 = A.l0, &ka4 = A.l1, &ka5 = A.l2;
+    if (F32) {
+      // FP32 to the end: sums, warp reductions, bonds and the force assembly; only M_z (an FP64
+      // reduction over all charges) enters from FP64
+      float v[9] = {ak0.valuef(), ak1.valuef(), ak2.valuef(), ka0.valuef(), ka1.valuef(), ka2.valuef(),
+                    ka3.valuef(), ka4.valuef(), ka5.valuef()};
 #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const float yv = v[d] - fc[d], tv = ff[d] + yv;
-            fc[d] = (tv - ff[d]) - yv;
-            ff[d] = tv;
+      for (int d = 0; d < 9; ++d) v[d] = warp_sum_f(v[d]);
+      if (epart) {
+        eii = warp_sum_f(eii);
+        eie = warp_sum_f(eie);
+        elj = warp_sum_f(elj);
+      }
+      if (lane == 0) {
+        const float Mz = (float)(scal[kScalMion] + scal[kScalMele]);
+        float Fx = -qf * v[0], Fy = -qf * v[1], Fz = -qf * v[2] - (float)slab * qf * Mz;
+        float bx = 0.f, by = 0.f, bz = 0.f, eb = 0.f;
+        if (md.ntype && md.bond_start) {
+          const float Lxf = (float)Lx, Lyf = (float)Ly, kbf = (float)md.kb;
+          for (int b = md.bond_start[i]; b < md.bond_start[i + 1]; ++b) {
+            const float4 o = ions.pf[ions.inv[md.bond_j[b]]];
+            float dx = Xf - o.x, dy = Yf - o.y, dz = Zf - o.z;
+            dx -= Lxf * floorf(dx / Lxf + 0.5f);
+            dy -= Lyf * floorf(dy / Lyf + 0.5f);
+            const float len = sqrtf(dx * dx + dy * dy + dz * dz);
+            const float ext = len - (float)md.bond_r0[b];
+            const float f = -kbf * ext / len;
+            bx += f * dx;
+            by += f * dy;
+            bz += f * dz;
+            eb += 0.25f * kbf * ext * ext;   // each bond is visited from both ends
           }
         }
+        const float ke = (float)kKe;
+        F[i] = (double)(ke * (Fx + v[3]) + v[6] + bx);
+        F[ni + i] = (double)(ke * (Fy + v[4]) + v[7] + by);
+        F[2 * ni + i] = (double)(ke * (Fz + v[5]) + v[8] + bz);
+        e_ii = eii;
+        e_ie = eie;
+        e_lj = elj;
+        e_b = eb;
       }
-    }
-  }
-  if (!live) {
-    // keep the block-wide reduction below well formed
-    for (int e = 0; e < 4; ++e) red[e][t] = 0.0;
-  }
-  double e_ii = 0, e_ie = 0, e_lj = 0, e_b = 0;
-  if (live) {
-    if (F32)
-      for (int d = 0; d < 3; ++d) fk[d] = (double)ff[d] - (double)fc[d];
-    double Fx = -qi * fk[0], Fy = -qi * fk[1], Fz = -qi * fk[2];
-    // slab force, FP64 in every form: M_z = sum q_i z_i + sum Q_j Z_j
-    Fz = fma(-slab * qi, scal[kScalMion] + scal[kScalMele], Fz);
-    // ---- real space
-    const double rc2 = rc * rc;
-    double rx = 0, ry = 0, rz = 0;      // Coulomb (Gaussian units)
-    double lx = 0, ly = 0, lz = 0;      // LJ (kJ/mol/nm)
-    if (!F32) {
-      for_stencil(ions, X, Y, Z, Lx, Ly, [&](int pp, double sx, double sy, int ix, int iy) {
-        if (pp == p && ix == 0 && iy == 0) return;
-        const double dx = X - (ions.xs[pp] + sx), dy = Y - (ions.ys[pp] + sy), dz = Z - ions.zs[pp];
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= rc2) return;
-        double phi, md2;
-        pair_ii(r2, alpha, phi, md2);
-        const double s = qi * ions.ws[pp] * md2;
-        rx = fma(s, dx, rx);
-        ry = fma(s, dy, ry);
-        rz = fma(s, dz, rz);
-        e_ii = fma(0.5 * qi * ions.ws[pp], phi, e_ii);
-        if (md.ntype && ions.ms[pp] != mi) {
-          const double2 sg = md.lj[ti * md.ntype + ions.ts[pp]];
-          const double sr2 = sg.x / r2, sr6 = sr2 * sr2 * sr2;
-          const double fs = 24.0 * sg.y * (2.0 * sr6 * sr6 - sr6) / r2;
-          lx = fma(fs, dx, lx);
-          ly = fma(fs, dy, ly);
-          lz = fma(fs, dz, lz);
-          e_lj += 0.5 * 4.0 * sg.y * (sr6 * sr6 - sr6);
-        }
-      });
-      for_stencil(eles, X, Y, Z, Lx, Ly, [&](int pe, double sx, double sy, int, int) {
-        const double dx = X - (eles.xs[pe] + sx), dy = Y - (eles.ys[pe] + sy), dz = Z - eles.zs[pe];
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= rc2 || r2 == 0.0) return;
-        const double Qj = Q[eles.order[pe]];
-        double phi, md2;
-        pair_ie(r2, alpha, eta, phi, md2);
-        const double s = qi * Qj * md2;
-        rx = fma(s, dx, rx);
-        ry = fma(s, dy, ry);
-        rz = fma(s, dz, rz);
-        e_ie = fma(qi * Qj, phi, e_ie);
-        if (md.ntype) {
-          const double2 sg = md.lj[ti * md.ntype + (md.ntype - 1)];
-          const double sr2 = sg.x / r2, sr6 = sr2 * sr2 * sr2;
-          const double fs = 24.0 * sg.y * (2.0 * sr6 * sr6 - sr6) / r2;
-          lx = fma(fs, dx, lx);
-          ly = fma(fs, dy, ly);
-          lz = fma(fs, dz, lz);
-          e_lj += 4.0 * sg.y * (sr6 * sr6 - sr6);
-        }
-      });
     } else {
-      const float Xf = (float)X, Yf = (float)Y, Zf = (float)Z, rc2f = (float)rc2;
-      const float af = (float)alpha, etaf = (float)eta, qf = (float)qi;
-      float a[6] = {0, 0, 0, 0, 0, 0}, cmp[6] = {0, 0, 0, 0, 0, 0};
-      auto kadd = [&](int d, float v) {
-        const float yv = v - cmp[d], tv = a[d] + yv;
-        cmp[d] = (tv - a[d]) - yv;
-        a[d] = tv;
-      };
-      float eii = 0.f, eie = 0.f, elj = 0.f;
-      for_stencil(ions, X, Y, Z, Lx, Ly, [&](int pp, double sx, double sy, int ix, int iy) {
-        if (pp == p && ix == 0 && iy == 0) return;
-        const float dx = Xf - (ions.xf[pp] + (float)sx), dy = Yf - (ions.yf[pp] + (float)sy), dz = Zf - ions.zf[pp];
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= rc2f) return;
-        float phi, md2;
-        pair_ii_f(r2, af, phi, md2);
-        const float qq = qf * (float)ions.ws[pp];
-        const float s = qq * md2;
-        kadd(0, s * dx);
-        kadd(1, s * dy);
-        kadd(2, s * dz);
-        eii += 0.5f * qq * phi;
-        if (md.ntype && ions.ms[pp] != mi) {
-          const double2 sg = md.lj[ti * md.ntype + ions.ts[pp]];
-          const float sr2 = (float)sg.x / r2, sr6 = sr2 * sr2 * sr2;
-          const float fs = 24.f * (float)sg.y * (2.f * sr6 * sr6 - sr6) / r2;
-          kadd(3, fs * dx);
-          kadd(4, fs * dy);
-          kadd(5, fs * dz);
-          elj += 2.f * (float)sg.y * (sr6 * sr6 - sr6);
+      for (int d = 0; d < 3; ++d) {
+        fk[d] = warp_sum(fk[d]);
+        rr[d] = warp_sum(rr[d]);
+        ll[d] = warp_sum(ll[d]);
+      }
+      if (epart) {
+        e_ii = warp_sum(e_ii);
+        e_ie = warp_sum(e_ie);
+        e_lj = warp_sum(e_lj);
+      }
+      if (lane == 0) {
+        double Fx = -qi * fk[0], Fy = -qi * fk[1], Fz = -qi * fk[2];
+        // slab force: M_z = sum q_i z_i + sum Q_j Z_j
+        Fz = fma(-slab * qi, scal[kScalMion] + scal[kScalMele], Fz);
+        double bx = 0, by = 0, bz = 0;
+        if (md.ntype && md.bond_start) {
+          const double xo = x_orig[i], yo = y_orig[i], zo = z_orig[i];
+          for (int b = md.bond_start[i]; b < md.bond_start[i + 1]; ++b) {
+            const int j2 = md.bond_j[b];
+            double dx = xo - x_orig[j2], dy = yo - y_orig[j2], dz = zo - z_orig[j2];
+            dx -= Lx * floor(dx / Lx + 0.5);
+            dy -= Ly * floor(dy / Ly + 0.5);
+            const double len = sqrt(dx * dx + dy * dy + dz * dz);
+            const double ext = len - md.bond_r0[b];
+            const double f = -md.kb * ext / len;
+            bx = fma(f, dx, bx);
+            by = fma(f, dy, by);
+            bz = fma(f, dz, bz);
+            e_b += 0.25 * md.kb * ext * ext;   // each bond is visited from both ends
+          }
         }
-      });
-      for_stencil(eles, X, Y, Z, Lx, Ly, [&](int pe, double sx, double sy, int, int) {
-        const float dx = Xf - (eles.xf[pe] + (float)sx), dy = Yf - (eles.yf[pe] + (float)sy), dz = Zf - eles.zf[pe];
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= rc2f || r2 == 0.f) return;
-        const float Qj = (float)Q[eles.order[pe]];
-        float phi, md2;
-        pair_ie_f(r2, af, etaf, phi, md2);
-        const float s = qf * Qj * md2;
-        kadd(0, s * dx);
-        kadd(1, s * dy);
-        kadd(2, s * dz);
-        eie += qf * Qj * phi;
-        if (md.ntype) {
-          const double2 sg = md.lj[ti * md.ntype + (md.ntype - 1)];
-          const float sr2 = (float)sg.x / r2, sr6 = sr2 * sr2 * sr2;
-          const float fs = 24.f * (float)sg.y * (2.f * sr6 * sr6 - sr6) / r2;
-          kadd(3, fs * dx);
-          kadd(4, fs * dy);
-          kadd(5, fs * dz);
-          elj += 4.f * (float)sg.y * (sr6 * sr6 - sr6);
-        }
-      });
-      rx = (double)a[0] - cmp[0];
-      ry = (double)a[1] - cmp[1];
-      rz = (double)a[2] - cmp[2];
-      lx = (double)a[3] - cmp[3];
-      ly = (double)a[4] - cmp[4];
-      lz = (double)a[5] - cmp[5];
-      e_ii = eii;
-      e_ie = eie;
-      e_lj = elj;
-    }
-    // ---- bonds (FP64; a handful per site)
-    double bx = 0, by = 0, bz = 0;
-    if (md.ntype && md.bond_start) {
-      const double xo = x_orig[i], yo = y_orig[i], zo = z_orig[i];
-      for (int b = md.bond_start[i]; b < md.bond_start[i + 1]; ++b) {
-        const int j2 = md.bond_j[b];
-        double dx = xo - x_orig[j2], dy = yo - y_orig[j2], dz = zo - z_orig[j2];
-        dx -= Lx * floor(dx / Lx + 0.5);
-        dy -= Ly * floor(dy / Ly + 0.5);
-        const double len = sqrt(dx * dx + dy * dy + dz * dz);
-        const double ext = len - md.bond_r0[b];
-        const double f = -md.kb * ext / len;
-        bx = fma(f, dx, bx);
-        by = fma(f, dy, by);
-        bz = fma(f, dz, bz);
-        e_b += 0.25 * md.kb * ext * ext;   // each bond is visited from both ends
+        F[i] = kKe * (Fx + rr[0]) + ll[0] + bx;
+        F[ni + i] = kKe * (Fy + rr[1]) + ll[1] + by;
+        F[2 * ni + i] = kKe * (Fz + rr[2]) + ll[2] + bz;
       }
     }
-    Fx = kKe * (Fx + rx) + lx + bx;
-    Fy = kKe * (Fy + ry) + ly + by;
-    Fz = kKe * (Fz + rz) + lz + bz;
-    F[i] = Fx;
-    F[ni + i] = Fy;
-    F[2 * ni + i] = Fz;
-    red[0][t] = e_ii;
-    red[1][t] = e_ie;
-    red[2][t] = e_lj;
-    red[3][t] = e_b;
   }
   if (epart) {
-    __syncthreads();
-    for (int s = kGatherThreads / 2; s > 0; s >>= 1) {
-      if (t < s)
-        for (int e = 0; e < 4; ++e) red[e][t] += red[e][t + s];
-      __syncthreads();
+    if (lane == 0) {
+      red[warp][0] = e_ii;
+      red[warp][1] = e_ie;
+      red[warp][2] = e_lj;
+      red[warp][3] = e_b;
     }
-    if (t < 4) epart[(int64_t)blockIdx.x * 4 + t] = red[t][0];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      double s = 0.0;
+      for (int w = 0; w < kWarpsPerBlock; ++w) s += red[w][threadIdx.x];
+      epart[(int64_t)blockIdx.x * 4 + threadIdx.x] = s;
+    }
   }
 }
 
@@ -700,23 +867,26 @@ void ion_forces(srbe_ctx *c, bool energies) {
   const int K = c->K;
   double2 *coef = c->coef.p;
   if (K > 0) {
-    k_coef<<<blocks_for(K, 128), 128, 0, c->stream>>>(K, c->dc.p, c->S2.p, coef, 1);
+    k_coef<<<blocks_for(K, 128), 128, 0, c->stream>>>(K, c->dc.p, c->S2.p, coef, c->coef32.p, 1);
     c->launches++;
   }
   MdDev md{};
   if (c->have_md) {
     md.ntype = c->ntype;
     md.lj = (const double2 *)c->lj.p;
+    md.lj32 = c->lj32.p;
     md.bond_start = c->bond_start.p;
     md.bond_j = c->bond_j.p;
     md.bond_r0 = c->bond_r0.p;
     md.kb = c->kb;
   }
   const double3 invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
+  const float3 kvf = make_float3((float)(2.0 * kPi / c->L[0]), (float)(2.0 * kPi / c->L[1]),
+                                 (float)(2.0 * kPi / c->L[2]));
   const double slab = 4.0 * kPi / c->V;
-  const unsigned nblk = blocks_for(std::max<int64_t>(c->ni, 1), kGatherThreads);
+  const unsigned nblk = blocks_for(std::max<int64_t>(c->ni, 1), kWarpsPerBlock);
   double *ep = energies ? c->epart.p : nullptr;
-  CellsDev ions = cells_dev(c->icells), eles = cells_dev(c->ecells);
+  CellsDev ions = cells_dev(c->icells, c->runtab), eles = cells_dev(c->ecells, c->runtab);
   if (!c->have_md) {
     ions.ts = nullptr;
     ions.ms = nullptr;
@@ -724,11 +894,11 @@ void ion_forces(srbe_ctx *c, bool energies) {
   if (c->ni > 0) {
     if (c->precision == SRBE_MIXED)
       k_ion_forces<true><<<nblk, kGatherThreads, 0, c->stream>>>(
-          c->ni, ions, eles, c->Q.p, K, c->dm.p, coef, c->tab.p, invL, c->L[0], c->L[1], c->alpha, c->eta, c->rc,
+          c->ni, ions, eles, c->Q.p, c->Q32.p, K, c->dm.p, coef, c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta, c->rc,
           slab, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep);
     else
       k_ion_forces<false><<<nblk, kGatherThreads, 0, c->stream>>>(
-          c->ni, ions, eles, c->Q.p, K, c->dm.p, coef, c->tab.p, invL, c->L[0], c->L[1], c->alpha, c->eta, c->rc,
+          c->ni, ions, eles, c->Q.p, c->Q32.p, K, c->dm.p, coef, c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta, c->rc,
           slab, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep);
     c->launches++;
     c->mode_evals += c->ni * (int64_t)K;
@@ -772,6 +942,32 @@ __global__ void k_kick_drift(int64_t n, double *__restrict__ x, double *__restri
     y[i] = Y;
     z[i] = fma(dt, c, z[i]);
   }
+}
+
+// capped steepest descent: r += F min(a, dmax / |F|), x and y wrapped into [0, L)
+__global__ void k_sd_move(int64_t n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
+                          const double *__restrict__ F, double a, double dmax, double Lx, double Ly) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double fx = F[i], fy = F[n + i], fz = F[2 * n + i];
+  const double fn = sqrt(fx * fx + fy * fy + fz * fz);
+  const double s = fn > 0.0 ? fmin(a, dmax / fn) : 0.0;
+  double X = fma(s, fx, x[i]), Y = fma(s, fy, y[i]);
+  X -= Lx * floor(X / Lx);
+  Y -= Ly * floor(Y / Ly);
+  if (X >= Lx) X -= Lx;
+  if (Y >= Ly) Y -= Ly;
+  x[i] = X;
+  y[i] = Y;
+  z[i] = fma(s, fz, z[i]);
+}
+
+void steepest_descent_move(srbe_ctx *c, double a, double dmax) {
+  if (c->ni == 0) return;
+  k_sd_move<<<blocks_for(c->ni, 256), 256, 0, c->stream>>>(c->ni, c->x.p, c->y.p, c->z.p, c->F.p, a, dmax, c->L[0],
+                                                          c->L[1]);
+  c->launches++;
+  SRBE_CUDA(cudaGetLastError());
 }
 
 void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift) {

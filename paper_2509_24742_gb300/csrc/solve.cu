@@ -148,7 +148,8 @@ __global__ void k_gj_update(int64_t ne, int64_t p, double *__restrict__ A, const
 template <class T>
 __global__ void k_gemv_rows(int64_t nrow, int64_t ncol, const T *__restrict__ M, const double *__restrict__ v,
                             double dpsi, const double *__restrict__ add, double *__restrict__ y,
-                            const double *__restrict__ wrow, double wd, double s_e, double *__restrict__ scal) {
+                            const double *__restrict__ wrow, double wd, double s_e, double *__restrict__ scal,
+                            float *__restrict__ y32 = nullptr) {
   const int lane = threadIdx.x & 31;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (row > nrow || (row == nrow && !wrow)) return;
@@ -162,7 +163,11 @@ __global__ void k_gemv_rows(int64_t nrow, int64_t ncol, const T *__restrict__ M,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) {
-    if (row < nrow) y[row] = add ? fma(dpsi, add[row], acc) : acc;
+    if (row < nrow) {
+      const double r = add ? fma(dpsi, add[row], acc) : acc;
+      y[row] = r;
+      if (y32) y32[row] = (float)r;
+    }
     else scal[kScalPsi] = -(acc + dpsi * wd) / s_e;
   }
 }
@@ -310,7 +315,7 @@ void charge_update(srbe_ctx *c) {
   const int64_t ne = c->ne;
   const unsigned nb = blocks_for((ne + 1) * 32, 256);
   k_gemv_rows<double><<<nb, 256, 0, c->stream>>>(ne, ne, c->Bmat.p, c->bvec.p, c->dpsi, c->qd.p, c->Q.p, c->we.p,
-                                                 c->wd, c->s_e, c->scal.p);
+                                                 c->wd, c->s_e, c->scal.p, c->Q32.p);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }

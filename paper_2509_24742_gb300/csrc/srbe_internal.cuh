@@ -17,6 +17,8 @@ namespace srbe {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kTabBits = 10;                  // sin/cos table of 1024 entries per turn
 constexpr int kTab = 1 << kTabBits;
+constexpr int kGatherThreads = 256;           // gather kernels: one warp per particle
+constexpr int kWarpsPerBlock = kGatherThreads / 32;
 
 // ------------------------------------------------------------------------------------------------
 // error plumbing
@@ -78,12 +80,21 @@ struct CellGrid {
   int ncell() const { return nc[0] * nc[1] * nc[2]; }
 };
 
+// Stencil of every cell as runs of consecutive cells of one x-row sharing an image shift:
+// (first cell, number of cells, packed image (ix + 512) | (iy + 512) << 10, 0), per-cell offsets.
+struct RunTable {
+  DevBuf<int4> runs;
+  DevBuf<int32_t> first;
+};
+
 struct Cells {
   CellGrid g;
   DevBuf<int32_t> cell, rank, start, order;   // order: sorted position -> original index
+  DevBuf<int32_t> inv;                        // original index -> sorted position
   DevBuf<double> xs, ys, zs, ws;              // positions / charges in sorted order
   DevBuf<int32_t> ts, ms;                     // type, molecule in sorted order
-  DevBuf<float> xf, yf, zf;                   // FP32 copies for the cheap distance pre-check
+  DevBuf<float4> pf;                          // FP32 (x, y, z, w) in sorted order for the pre-check
+  DevBuf<uint64_t> us;                        // fixed-point phase coordinates [3][n] in sorted order
 };
 
 struct HostExt;   // host-only per-context state (sampler, staging), defined in api.cu
@@ -116,6 +127,7 @@ struct srbe_ctx {
   // electrode (fixed sites)
   int64_t ne = 0;
   srbe::DevBuf<double> ex, ey, ez, ed;         // positions and d (-1/2 | +1/2)
+  srbe::DevBuf<uint64_t> eu;                   // fixed-point phase coordinates [3][ne], site order
   srbe::DevBuf<double> Bmat;                   // projected inverse J A^-1, ne x ne row-major
   srbe::DevBuf<float> Bmat32;                  // its FP32 copy (mixed form)
   srbe::DevBuf<double> Amat;                   // A itself (kept for the refinement residual)
@@ -125,6 +137,7 @@ struct srbe_ctx {
   std::vector<double> hR;                      // host copy of R
   std::vector<int8_t> hside;
   srbe::Cells ecells;
+  srbe::RunTable runtab;                       // stencil runs of the shared ion / electrode grid
 
   // electrolyte
   int64_t ni = 0;
@@ -161,6 +174,9 @@ struct srbe_ctx {
   srbe::DevBuf<double2> partial;               // structure-factor partials [chunks][K]
   srbe::DevBuf<double> mpart;                  // dipole partials [chunks]
   srbe::DevBuf<double2> coef;                  // per-mode c_k S(k) coefficients [K]
+  srbe::DevBuf<float2> coef32;                 // their FP32 copy (mixed form)
+  srbe::DevBuf<float> Q32;                     // FP32 copy of the charges (mixed form)
+  srbe::DevBuf<float2> lj32;                   // FP32 (sigma^2, eps) table (mixed form)
   srbe::DevBuf<double> scal;                   // device scalars (see kScal* indices)
   srbe::DevBuf<double> epart;                  // per-block energy partials
   srbe::DevBuf<int> flag;                      // device error flag
@@ -221,7 +237,7 @@ __device__ __forceinline__ void sincos_turns(uint64_t th, const double2 *__restr
   const double x2 = x * x;
   const double sx = fma(x * x2, fma(x2, 1.0 / 120.0, -1.0 / 6.0), x);
   const double cm1 = x2 * fma(x2, 1.0 / 24.0, -0.5);
-  const double2 T = tab[idx];
+  const double2 T = __ldg(&tab[idx]);
   c = fma(T.x, cm1, fma(-T.y, sx, T.x));
   s = fma(T.y, cm1, fma(T.x, sx, T.y));
 }
@@ -241,12 +257,14 @@ void upload_table(srbe_ctx *c);
 void build_cells(srbe_ctx *c, Cells &cl, int64_t n, const double *x, const double *y, const double *z,
                  const double *w, const int32_t *typ, const int32_t *mol, bool is_ion);
 void choose_grid(const srbe_ctx *c, CellGrid &g, double zlo, double zhi);
+void build_run_table(srbe_ctx *c);
 void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *w,
                       double2 *S, const double2 *S_add, int mslot);
 void electrode_rhs(srbe_ctx *c);
 void charge_update(srbe_ctx *c);
 void ion_forces(srbe_ctx *c, bool energies);
 void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift);
+void steepest_descent_move(srbe_ctx *c, double a, double dmax);
 void build_A_and_inverse(srbe_ctx *c);
 void energy_scalars(srbe_ctx *c);
 enum Phase { kPhUpload = 0, kPhCells, kPhS1, kPhRhs, kPhSolve, kPhS2, kPhForces, kPhIntegrate, kPhEnergy, kPhCount };

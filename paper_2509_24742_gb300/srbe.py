@@ -61,6 +61,7 @@ EXPORTS = {
     "srbe_set_profiling": ([_vp, _int], _int),
     "srbe_get_phase_times": ([_vp, _dp, ctypes.POINTER(_i64)], _int),
     "srbe_structure_factor_noalloc": ([_dp, _i64, _vp, _vp, _int, _vp, _vp, _vp], _int),
+    "srbe_minimize": ([_vp, _int, _dbl, _dbl, _u64], _int),
 }
 PHASES = ("upload", "cells", "S1", "rhs", "solve", "S2", "forces", "integrate", "energy")
 
@@ -230,6 +231,9 @@ class Context:
 
     def forces_dev(self, F_ptr=None, Q_ptr=None):
         self._check(self.lib.srbe_forces_dev(self.h, _vp(F_ptr) if F_ptr else None, _vp(Q_ptr) if Q_ptr else None))
+
+    def minimize(self, nsteps, a=2e-5, dmax=0.01, seed=9):
+        self._check(self.lib.srbe_minimize(self.h, int(nsteps), float(a), float(dmax), int(seed)))
 
     def step(self, nsteps, seed0):
         self._check(self.lib.srbe_step(self.h, int(nsteps), int(seed0)))

@@ -212,7 +212,9 @@ def make_slab(name, box, nx, ny, n_pairs, cation_sites, *, alpha, eta_inv, rc, P
     # electrode diameter is kept, and the 0.3 nm wall gap stays outside sigma_ion-electrode
     sig = np.array([0.50, 0.40, 0.35, 0.45, 0.337])
     sig[:4] = sig[:4] * min(1.0, d_min / sig[:4].max())
-    eps = np.array([0.5, 0.5, 0.5, 0.5, 0.23])
+    # eps 2 kJ/mol (ions) and 1 kJ/mol (electrode): with the scaled-down diameters a weaker
+    # repulsion lets opposite charges collapse and the dense packing heat to thousands of K
+    eps = np.array([2.0, 2.0, 2.0, 2.0, 1.0])
     bonds, r0 = np.zeros((0, 2), np.int32), np.zeros(0)
     if cation_sites == 3:
         b = []
