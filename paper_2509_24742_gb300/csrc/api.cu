@@ -340,6 +340,42 @@ void reserve(srbe_ctx *c) {
   const size_t neb = blocks_for(std::max<int64_t>(c->ne, 1), 128);
   c->epart.ensure(nblk * 4 + 4 + neb + 8);
   c->scal.ensure(kScalCount);
+  // ion cell list and Verlet lists
+  Cells &cl = c->icells;
+  const size_t nn = (size_t)std::max<int64_t>(c->ni, 1), ne = (size_t)std::max<int64_t>(c->ne, 1);
+  cl.cell.ensure(nn);
+  cl.rank.ensure(nn);
+  cl.order.ensure(nn);
+  cl.inv.ensure(nn);
+  cl.start.ensure((size_t)cl.g.ncell() + 1);
+  cl.xs.ensure(nn);
+  cl.ys.ensure(nn);
+  cl.zs.ensure(nn);
+  cl.ws.ensure(nn);
+  cl.ts.ensure(nn);
+  cl.ms.ensure(nn);
+  cl.pf.ensure(nn);
+  cl.us.ensure(3 * nn);
+  NbrLists &nb = c->nbr;
+  if (nb.cap == 0) {
+    // twice the expected neighbour count at rc + skin for the mean ion density between the walls
+    const double h = std::max(1.0, c->wall_span);
+    const double rho = (double)std::max<int64_t>(c->ni, 1) / (c->L[0] * c->L[1] * h);
+    const double r = c->rc + nb.skin;
+    const double expect = rho * 4.0 / 3.0 * kPi * r * r * r;
+    nb.cap = (int)std::min<double>(1 << 20, 32 * std::ceil(std::max(128.0, 2.0 * expect + 64.0) / 32.0));
+  }
+  nb.ii.ensure(nn * nb.cap);
+  nb.ie.ensure(nn * nb.cap);
+  nb.ei.ensure(ne * nb.cap);
+  nb.ii_n.ensure(nn);
+  nb.ie_n.ensure(nn);
+  nb.ei_n.ensure(ne);
+  nb.xb.ensure(nn);
+  nb.yb.ensure(nn);
+  nb.pfb.ensure(nn);
+  nb.cell_s.ensure(nn);
+  nb.flag.ensure(2);
 }
 
 }  // namespace srbe
@@ -415,11 +451,10 @@ void require_state(srbe_ctx *c, bool pos) {
 void charges_pass(srbe_ctx *c) {
   reserve(c);
   phase_begin(c, kPhCells);
-  build_cells(c, c->icells, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->have_md ? c->itype.p : nullptr,
-              c->have_md ? c->mol.p : nullptr, true);
+  neighbor_update(c);
   phase_end(c, kPhCells);
   phase_begin(c, kPhS1);
-  structure_factor(c, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->S1.p, nullptr, kScalMion);
+  structure_factor(c, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->S1.p, nullptr, kScalMion, 0);
   phase_end(c, kPhS1);
   phase_begin(c, kPhRhs);
   electrode_rhs(c);
@@ -432,7 +467,7 @@ void charges_pass(srbe_ctx *c) {
 void forces_pass(srbe_ctx *c, bool energies) {
   charges_pass(c);
   phase_begin(c, kPhS2);
-  structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele);
+  structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele, 1);
   phase_end(c, kPhS2);
   phase_begin(c, kPhForces);
   ion_forces(c, energies);
@@ -623,6 +658,7 @@ int srbe_set_electrode(srbe_ctx *c, int64_t n_ele, const double *R, const int8_t
     // one cell grid for ions and electrode sites: the whole periodic length in z, centred on the walls
     const double zmin = *std::min_element(z.begin(), z.end()), zmax = *std::max_element(z.begin(), z.end());
     const double pad = 0.5 * (c->L[2] - (zmax - zmin));
+    c->wall_span = zmax - zmin;
     choose_grid(c, c->ecells.g, zmin - pad, zmax + pad);
     c->icells.g = c->ecells.g;
     build_run_table(c);
@@ -645,6 +681,7 @@ int srbe_set_positions(srbe_ctx *c, int64_t n_ion, const double *r, const double
     SRBE_REQUIRE(n_ion < (1ll << 31), SRBE_EINVAL, "too many ions");
     SRBE_REQUIRE(finite_all(r, 3 * n_ion) && finite_all(q, n_ion), SRBE_EINVAL, "non-finite ion position or charge");
     if (c->have_md && n_ion != c->ni) c->have_md = false;
+    if (n_ion != c->ni) c->nbr.cap = 0;
     c->ni = n_ion;
     const size_t n = (size_t)std::max<int64_t>(n_ion, 1);
     c->x.ensure(n);
@@ -652,6 +689,7 @@ int srbe_set_positions(srbe_ctx *c, int64_t n_ion, const double *r, const double
     c->z.ensure(n);
     c->q.ensure(n);
     c->F.ensure(3 * n);
+    neighbor_force_rebuild(c);
     Extra *e = extra(c);
     if (n_ion > 0) {
       double *aos = e->aos.ensure(3 * n);
@@ -671,7 +709,9 @@ int srbe_set_positions_dev(srbe_ctx *c, int64_t n_ion, const double *r_dev, cons
   return guarded(c, [&] {
     SRBE_REQUIRE(n_ion >= 0 && (n_ion == 0 || (r_dev && q_dev)), SRBE_EINVAL, "null positions or charges");
     if (c->have_md && n_ion != c->ni) c->have_md = false;
+    if (n_ion != c->ni) c->nbr.cap = 0;
     c->ni = n_ion;
+    neighbor_force_rebuild(c);
     const size_t n = (size_t)std::max<int64_t>(n_ion, 1);
     c->x.ensure(n);
     c->y.ensure(n);
@@ -788,6 +828,7 @@ int srbe_set_md(srbe_ctx *c, const double *mass, const double *v, int ntype, con
     c->kb = kb;
     c->dt = dt;
     c->have_md = true;
+    neighbor_force_rebuild(c);
     extra(c)->forces_valid = false;
   });
 }

@@ -110,7 +110,8 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
 // the dipole partials into scal[mslot].
 __global__ void k_sfac_reduce(int K, int nchunk, const double2 *__restrict__ partial, const double *__restrict__ mpart,
                               double2 *__restrict__ S, const double2 *__restrict__ S_add, double *__restrict__ scal,
-                              int mslot) {
+                              int mslot, const double *__restrict__ cw, double2 *__restrict__ coef,
+                              float2 *__restrict__ coef32, int swap) {
   const int lane = threadIdx.x & 31;
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (k > K) return;
@@ -136,6 +137,13 @@ __global__ void k_sfac_reduce(int K, int nchunk, const double2 *__restrict__ par
         im += S_add[k].y;
       }
       S[k] = make_double2(re, im);
+      if (coef) {
+        // per-mode coefficients of the gathers: (c Re S, c Im S) for b, (c Im S, c Re S) for forces
+        const double c = cw[k];
+        const double2 v = swap ? make_double2(c * im, c * re) : make_double2(c * re, c * im);
+        coef[k] = v;
+        coef32[k] = make_float2((float)v.x, (float)v.y);
+      }
     } else {
       scal[mslot] = re;
     }
@@ -156,7 +164,7 @@ int64_t sfac_chunks(int64_t n, int K, int64_t *chunk) {
 }
 
 void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *w,
-                      double2 *S, const double2 *S_add, int mslot) {
+                      double2 *S, const double2 *S_add, int mslot, int coef_mode) {
   const int K = c->K;
   const int ktiles = std::max(1, (K + 31) / 32);
   int64_t chunk;
@@ -176,8 +184,9 @@ void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, 
     c->launches++;
     c->mode_evals += n * (int64_t)K;
   }
-  k_sfac_reduce<<<blocks_for((int64_t)(K + 1) * 32, 256), 256, 0, c->stream>>>(K, (int)nchunk, c->partial.p,
-                                                                               c->mpart.p, S, S_add, c->scal.p, mslot);
+  k_sfac_reduce<<<blocks_for((int64_t)(K + 1) * 32, 256), 256, 0, c->stream>>>(
+      K, (int)nchunk, c->partial.p, c->mpart.p, S, S_add, c->scal.p, mslot, c->dc.p,
+      coef_mode >= 0 ? c->coef.p : nullptr, c->coef32.p, coef_mode > 0 ? 1 : 0);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }

@@ -8,7 +8,11 @@
 //  * the velocity-Verlet kick/drift.
 // One thread per particle; stencil cells are visited in a fixed order and cells are sorted by
 // particle index, so every sum has a fixed order and results are bitwise reproducible.
+#include <cooperative_groups.h>
+
 #include "srbe_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace srbe {
 
@@ -35,17 +39,22 @@ static GridDev to_dev(const CellGrid &g) {
   return d;
 }
 
+// Cells of at least (rc + skin) / 2, so that the stencil of a cell covers rc + skin from any point
+// in it: Verlet lists built at rc + skin then hold every pair within rc until an ion has moved
+// skin / 2.
 void choose_grid(const srbe_ctx *c, CellGrid &g, double zlo, double zhi) {
-  const double target = 0.5 * c->rc;
+  const double reach = c->rc + c->nbr.skin;
+  const double target = 0.5 * reach;
   for (int d = 0; d < 2; ++d) {
     g.nc[d] = std::max(1, (int)std::floor(c->L[d] / target));
     g.cs[d] = c->L[d] / g.nc[d];
-    g.span[d] = (int)std::ceil(c->rc / g.cs[d] - 1e-12);
+    g.span[d] = (int)std::ceil(reach / g.cs[d] - 1e-12);
+    SRBE_REQUIRE(g.span[d] <= 7 * g.nc[d], SRBE_EINVAL, "cutoff too long for the periodic box (more than 7 images)");
   }
   const double h = std::max(zhi - zlo, 1e-9);
   g.nc[2] = std::max(1, (int)std::floor(h / target));
   g.cs[2] = h / g.nc[2];
-  g.span[2] = (int)std::ceil(c->rc / g.cs[2] - 1e-12);
+  g.span[2] = (int)std::ceil(reach / g.cs[2] - 1e-12);
   g.z0 = zlo;
 }
 
@@ -251,27 +260,36 @@ __device__ __forceinline__ void pair_ie(double r2, double alpha, double eta, dou
   mdphi_r = f / r2;
 }
 
+// erfc(x) for x >= 0 from Abramowitz & Stegun 7.1.26 (Hastings' rational approximation,
+// |error| <= 1.5e-7 absolute), written against exp(-x^2) so that the force term shares it.
+__device__ __forceinline__ float erfc_as(float x, float ex2) {
+  const float t = __frcp_rn(fmaf(0.3275911f, x, 1.0f));
+  const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f),
+                                      -0.284496736f), 0.254829592f);
+  return poly * ex2;
+}
+
 __device__ __forceinline__ void pair_ii_f(float r2, float alpha, float &phi, float &mdphi_r) {
-  const float r = sqrtf(r2);
-  const float ec = erfcf(alpha * r);
+  const float rinv = rsqrtf(r2);
+  const float r = r2 * rinv;
   const float ex = __expf(-alpha * alpha * r2);
-  phi = ec / r;
-  mdphi_r = (phi + (float)kTwoOverSqrtPi * alpha * ex) / r2;
+  phi = erfc_as(alpha * r, ex) * rinv;
+  mdphi_r = (phi + (float)kTwoOverSqrtPi * alpha * ex) * (rinv * rinv);
 }
 
 __device__ __forceinline__ void pair_ie_f(float r2, float alpha, float eta, float &phi, float &mdphi_r) {
-  const float r = sqrtf(r2);
-  const float ec = erfcf(alpha * r);
+  const float rinv = rsqrtf(r2);
+  const float r = r2 * rinv;
   const float ex = __expf(-alpha * alpha * r2);
-  float p = ec / r, f = p + (float)kTwoOverSqrtPi * alpha * ex;
+  float p = erfc_as(alpha * r, ex) * rinv, f = p + (float)kTwoOverSqrtPi * alpha * ex;
   if (r < 4.5f * eta) {
     const float eg = erfcf(r / eta);
     const float exg = __expf(-r2 / (eta * eta));
-    p -= eg / r;
-    f -= eg / r + (float)kTwoOverSqrtPi / eta * exg;
+    p -= eg * rinv;
+    f -= eg * rinv + (float)kTwoOverSqrtPi / eta * exg;
   }
   phi = p;
-  mdphi_r = f / r2;
+  mdphi_r = f * (rinv * rinv);
 }
 
 struct CellsDev {
@@ -414,8 +432,8 @@ __device__ __forceinline__ void pair_ion_ion(const PairSite &S, const CellsDev &
     A.eii += 0.5f * qq * phi;
     if (lj) {
       const float2 sg = md.lj32[S.ti * md.ntype + ions.ts[pp]];
-      const float sr2 = sg.x / r2, sr6 = sr2 * sr2 * sr2;
-      const float fs = 24.f * sg.y * (2.f * sr6 * sr6 - sr6) / r2;
+      const float ir2 = __frcp_rn(r2), sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
+      const float fs = 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
       A.l0.add(fs * dx);
       A.l1.add(fs * dy);
       A.l2.add(fs * dz);
@@ -463,8 +481,8 @@ __device__ __forceinline__ void pair_ion_ele(const PairSite &S, const CellsDev &
     A.eie += S.qf * Qj * phi;
     if (md.ntype) {
       const float2 sg = md.lj32[S.ti * md.ntype + (md.ntype - 1)];
-      const float sr2 = sg.x / r2, sr6 = sr2 * sr2 * sr2;
-      const float fs = 24.f * sg.y * (2.f * sr6 * sr6 - sr6) / r2;
+      const float ir2 = __frcp_rn(r2), sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
+      const float fs = 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
       A.l0.add(fs * dx);
       A.l1.add(fs * dy);
       A.l2.add(fs * dz);
@@ -498,11 +516,8 @@ __device__ __forceinline__ void pair_ion_ele(const PairSite &S, const CellsDev &
 // cut2 (FP32 test) into the warp queue q; calls pair(entry) for every full batch of 32 and once
 // more for the rest.  All lanes of the warp take part; skip_self drops the zero image of S.p.
 template <class Pair>
-__device__ __forceinline__ void compacted_pairs(const PairSite &S, const CellsDev &C, bool skip_self, float cut2,
-                                                int2 *q, int lane, Pair &&pair) {
-  const GridDev &g = C.g;
-  const int cell = (cell_coord(S.Z - g.z0, g.inv[2], g.nc[2]) * g.nc[1] + cell_coord(S.Y, g.inv[1], g.nc[1])) *
-                       g.nc[0] + cell_coord(S.X, g.inv[0], g.nc[0]);
+__device__ __forceinline__ void compacted_pairs(const PairSite &S, const CellsDev &C, int cell, bool skip_self,
+                                                float cut2, int2 *q, int lane, Pair &&pair) {
   int qn = 0;
   const unsigned below = (1u << lane) - 1u;
   const int r1 = C.run_first[cell + 1];
@@ -541,6 +556,57 @@ __device__ __forceinline__ void compacted_pairs(const PairSite &S, const CellsDe
   __syncwarp();
 }
 
+// The same compaction over a Verlet list: entries pack a sorted index (bits 0-23) and the image
+// shifts ix + 8, iy + 8 (bits 24-27, 28-31); consecutive lanes read consecutive entries.
+__device__ __forceinline__ int list_index(int32_t e) { return e & 0xffffff; }
+__device__ __forceinline__ int list_ix(int32_t e) { return ((e >> 24) & 15) - 8; }
+__device__ __forceinline__ int list_iy(int32_t e) { return ((unsigned)e >> 28) - 8; }
+__device__ __forceinline__ int32_t list_entry(int idx, int ix, int iy) {
+  return (int32_t)((unsigned)idx | ((unsigned)(ix + 8) << 24) | ((unsigned)(iy + 8) << 28));
+}
+
+template <class Pair>
+__device__ __forceinline__ void compacted_list(const PairSite &S, const CellsDev &C, const int32_t *__restrict__ list,
+                                               int count, float cut2, int2 *q, int lane, Pair &&pair) {
+  int qn = 0;
+  const unsigned below = (1u << lane) - 1u;
+  for (int base = 0; base < count; base += 32) {
+    const int k = base + lane;
+    bool in = false;
+    int pp = 0, img = 0;
+    if (k < count) {
+      const int32_t e = list[k];
+      pp = list_index(e);
+      const int ix = list_ix(e), iy = list_iy(e);
+      const float4 o = C.pf[pp];
+      const float dx = S.Xf - (o.x + (float)ix * S.Lxf), dy = S.Yf - (o.y + (float)iy * S.Lyf), dz = S.Zf - o.z;
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      in = r2 < cut2 && r2 > 0.f;
+      img = pack_image(ix, iy);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) q[qn + __popc(m & below)] = make_int2(pp, img);
+    qn += __popc(m);
+    if (qn >= 32) {
+      __syncwarp();
+      pair(q[lane]);
+      __syncwarp();
+      if (lane < qn - 32) q[lane] = q[lane + 32];
+      __syncwarp();
+      qn -= 32;
+    }
+  }
+  __syncwarp();
+  if (lane < qn) pair(q[lane]);
+  __syncwarp();
+}
+
+// Verlet-list view handed to the gathers
+struct ListsDev {
+  const int32_t *ii, *ie, *ei, *ii_n, *ie_n, *ei_n, *cell_s, *ecell;
+  int cap;
+};
+
 // ------------------------------------------------------------------------------------------------
 // electrode right-hand side: one warp per electrode site, lanes split the modes and the stencil
 // ------------------------------------------------------------------------------------------------
@@ -550,9 +616,9 @@ __global__ void __launch_bounds__(kGatherThreads)
 k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restrict__ ey,
                 const double *__restrict__ ez, const uint64_t *__restrict__ eu, int K, const int4 *__restrict__ modes,
                 const double2 *__restrict__ coefS, const float2 *__restrict__ coefS32,
-                const double2 *__restrict__ tab, double3 invL, CellsDev ions,
+                const double2 *__restrict__ tab, double3 invL, CellsDev ions, ListsDev nl,
                 double Lx, double Ly, double alpha, double eta, double rc, double slab, const double *__restrict__ scal,
-                double *__restrict__ b) {
+                double *__restrict__ b, float2 *__restrict__ bsplit) {
   __shared__ int2 wq[kWarpsPerBlock][64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t j = ((int64_t)blockIdx.x * kGatherThreads + threadIdx.x) >> 5;
@@ -590,7 +656,7 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
   const float cut2 = F32 ? rcf * rcf : (rcf + kPrecheckMargin) * (rcf + kPrecheckMargin);
   KahanF32 fn;
   double near = 0.0;
-  compacted_pairs(S, ions, false, cut2, wq[warp], lane, [&](int2 e) {
+  auto near_pair = [&](int2 e) {
     const int pp = e.x, ix = image_x(e.y), iy = image_y(e.y);
     if (F32) {
       const float4 o = ions.pf[pp];
@@ -607,11 +673,19 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
         near = fma(-ions.ws[pp], phi, near);
       }
     }
-  });
+  };
+  const int nei = nl.ei_n[j];
+  if (nei <= nl.cap) compacted_list(S, ions, nl.ei + j * nl.cap, nei, cut2, wq[warp], lane, near_pair);
+  else compacted_pairs(S, ions, nl.ecell[j], false, cut2, wq[warp], lane, near_pair);
   if (F32) {
     // FP32 to the end of the warp sum: on this GPU every FP64 warp instruction is costly
     const float accf = warp_sum_f(fk.valuef() + fn.valuef());
-    if (lane == 0) b[j] = fma(-slab * Z, scal[kScalMion], (double)accf);
+    if (lane == 0) {
+      const double bj = fma(-slab * Z, scal[kScalMion], (double)accf);
+      const float hi = (float)bj;
+      b[j] = bj;
+      bsplit[j] = make_float2(hi, (float)(bj - (double)hi));
+    }
   } else {
     acc = warp_sum(acc + near);
     // slab part (FP64 in every form): -(4 pi / V) Z_j sum_i q_i z_i
@@ -619,24 +693,314 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
   }
 }
 
-__global__ void k_coef(int K, const double *__restrict__ c, const double2 *__restrict__ S, double2 *__restrict__ out,
-                       float2 *__restrict__ out32, int swap) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < K) {
-    const double2 s = S[k];
-    const double2 v = swap ? make_double2(c[k] * s.y, c[k] * s.x) : make_double2(c[k] * s.x, c[k] * s.y);
-    out[k] = v;
-    out32[k] = make_float2((float)v.x, (float)v.y);
+static ListsDev lists_dev(const srbe_ctx *c) {
+  ListsDev d;
+  d.ii = c->nbr.ii.p;
+  d.ie = c->nbr.ie.p;
+  d.ei = c->nbr.ei.p;
+  d.ii_n = c->nbr.ii_n.p;
+  d.ie_n = c->nbr.ie_n.p;
+  d.ei_n = c->nbr.ei_n.p;
+  d.cell_s = c->nbr.cell_s.p;
+  d.ecell = c->ecells.cell.p;
+  d.cap = c->nbr.cap;
+  return d;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Verlet lists of the ions: one cooperative launch per step.
+//   phase 0  refresh the sorted copies in the order of the last build, x and y unwrapped next to
+//            the build positions (so the stored image shifts stay valid), and flag a rebuild when
+//            an ion has moved more than skin / 2;
+//   grid sync; if no rebuild: done;
+//   phases 1-6  rebuild the cell list (zero, count, scan, scatter, per-cell sort, gather + snapshot);
+//   phases 7-8  rebuild the ion-ion / ion-electrode lists (warp per ion) and the electrode-ion
+//               lists (warp per electrode site) at rc + skin.
+// The barriers are cooperative-groups grid syncs over a co-resident grid.
+// ------------------------------------------------------------------------------------------------
+struct NbrKernelArgs {
+  int64_t n, ne;
+  int ncell, cap;
+  const double *x, *y, *z, *w;
+  const int32_t *typ, *mol;
+  int32_t *cell, *rank, *start, *order, *inv, *ts, *ms, *cell_s;
+  double *xs, *ys, *zs, *ws, *xb, *yb;
+  float4 *pf, *pfb;
+  uint64_t *us;
+  int32_t *ii, *ie, *ei, *ii_n, *ie_n, *ei_n;
+  GridDev g;
+  const int4 *runs;
+  const int32_t *run_first;
+  CellsDev eles;
+  const int32_t *ecell;
+  const double *ex, *ey, *ez;
+  double Lx, Ly;
+  double3 invL;
+  float cut2, half_skin2;
+  int *flag;
+};
+
+__device__ __forceinline__ void warp_append(int32_t *list, int cap, int &count, bool in, int32_t entry, int lane) {
+  const unsigned m = __ballot_sync(0xffffffffu, in);
+  const int pos = count + __popc(m & ((1u << lane) - 1u));
+  if (in && pos < cap) list[pos] = entry;
+  count += __popc(m);
+}
+
+// appends every particle of the runs of `cell` within sqrt(cut2) of (X, Y, Z) to list
+__device__ __forceinline__ int build_list(const NbrKernelArgs &a, const int4 *runs, const int32_t *run_first, int cell,
+                                          const int32_t *start, const float4 *pf, float X, float Y, float Z,
+                                          int64_t self, int32_t *list, int lane) {
+  int count = 0;
+  const float Lxf = (float)a.Lx, Lyf = (float)a.Ly;
+  for (int r = run_first[cell]; r < run_first[cell + 1]; ++r) {
+    const int4 R = runs[r];
+    const int b0 = start[R.x], b1 = start[R.x + R.y];
+    if (b0 == b1) continue;
+    const int ix = image_x(R.z), iy = image_y(R.z);
+    const float sx = (float)ix * Lxf, sy = (float)iy * Lyf;
+    const bool zero_image = ix == 0 && iy == 0;
+    for (int base = b0; base < b1; base += 32) {
+      const int pp = base + lane;
+      bool in = false;
+      if (pp < b1 && !(zero_image && pp == self)) {
+        const float4 o = pf[pp];
+        const float dx = X - (o.x + sx), dy = Y - (o.y + sy), dz = Z - o.z;
+        in = dx * dx + dy * dy + dz * dz < a.cut2;
+      }
+      warp_append(list, a.cap, count, in, list_entry(pp, ix, iy), lane);
+    }
   }
+  return count;
+}
+
+__global__ void __launch_bounds__(256) k_neighbor_update(NbrKernelArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ int32_t part[256];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid, gsize = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gwarp = gtid >> 5, nwarps = gsize >> 5;
+  const int forced = __ldcg(&a.flag[1]);
+  // ---- phase 0: refresh + displacement test
+  if (!forced) {
+    for (int64_t p = gtid; p < a.n; p += gsize) {
+      const int32_t i = a.order[p];
+      double dx = a.x[i] - a.xb[p], dy = a.y[i] - a.yb[p];
+      dx -= a.Lx * floor(dx / a.Lx + 0.5);
+      dy -= a.Ly * floor(dy / a.Ly + 0.5);
+      const double X = a.xb[p] + dx, Y = a.yb[p] + dy, Z = a.z[i];
+      a.xs[p] = X;
+      a.ys[p] = Y;
+      a.zs[p] = Z;
+      const float4 b = a.pfb[p];
+      a.pf[p] = make_float4((float)X, (float)Y, (float)Z, b.w);
+      a.us[p] = to_turns64(X, a.invL.x);
+      a.us[a.n + p] = to_turns64(Y, a.invL.y);
+      a.us[2 * a.n + p] = to_turns64(Z, a.invL.z);
+      const float ex = (float)X - b.x, ey = (float)Y - b.y, ez = (float)Z - b.z;
+      if (ex * ex + ey * ey + ez * ez > a.half_skin2) atomicOr(&a.flag[0], 1);
+    }
+  } else if (gtid == 0) {
+    atomicOr(&a.flag[0], 1);
+  }
+  grid.sync();
+  // one L2 read of the flag per block (a grid-wide atomic read serialises), uniform over the grid
+  __shared__ int s_rebuild;
+  if (tid == 0) s_rebuild = __ldcg(&a.flag[0]);
+  __syncthreads();
+  if (!s_rebuild) return;
+  // ---- phase 1: zero the cell counts
+  for (int64_t c = gtid; c <= a.ncell; c += gsize) a.start[c] = 0;
+  grid.sync();
+  // ---- phase 2: count
+  for (int64_t i = gtid; i < a.n; i += gsize) {
+    const int cx = cell_coord(a.x[i], a.g.inv[0], a.g.nc[0]);
+    const int cy = cell_coord(a.y[i], a.g.inv[1], a.g.nc[1]);
+    const int cz = cell_coord(a.z[i] - a.g.z0, a.g.inv[2], a.g.nc[2]);
+    const int c = (cz * a.g.nc[1] + cy) * a.g.nc[0] + cx;
+    a.cell[i] = c;
+    a.rank[i] = atomicAdd(&a.start[c], 1);
+  }
+  grid.sync();
+  // ---- phase 3: exclusive scan (block 0)
+  if (blockIdx.x == 0) {
+    const int per = (a.ncell + 255) / 256;
+    const int b = tid * per, e = min(a.ncell, b + per);
+    int32_t s = 0;
+    for (int i = b; i < e; ++i) s += a.start[i];
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+      const int32_t v = tid >= off ? part[tid - off] : 0;
+      __syncthreads();
+      part[tid] += v;
+      __syncthreads();
+    }
+    int32_t run = part[tid] - s;
+    for (int i = b; i < e; ++i) {
+      const int32_t v = a.start[i];
+      a.start[i] = run;
+      run += v;
+    }
+    if (tid == 255) a.start[a.ncell] = part[255];
+  }
+  grid.sync();
+  // ---- phase 4: scatter
+  for (int64_t i = gtid; i < a.n; i += gsize) a.order[a.start[a.cell[i]] + a.rank[i]] = (int32_t)i;
+  grid.sync();
+  // ---- phase 5: sort each cell by particle index (warp per cell)
+  for (int64_t c = gwarp; c < a.ncell; c += nwarps) {
+    const int b = a.start[c], e = a.start[c + 1], m = e - b;
+    if (m <= 1) continue;
+    if (m <= 32) {
+      const int32_t v = lane < m ? a.order[b + lane] : 0x7fffffff;
+      int rank = 0;
+      for (int l = 0; l < 32; ++l) rank += (__shfl_sync(0xffffffffu, v, l) < v) ? 1 : 0;
+      __syncwarp();
+      if (lane < m) a.order[b + rank] = v;
+    } else if (lane == 0) {
+      for (int i = b + 1; i < e; ++i) {
+        const int32_t v = a.order[i];
+        int j = i - 1;
+        while (j >= b && a.order[j] > v) {
+          a.order[j + 1] = a.order[j];
+          --j;
+        }
+        a.order[j + 1] = v;
+      }
+    }
+    __syncwarp();
+  }
+  grid.sync();
+  // ---- phase 6: gather into sorted order and snapshot the build positions
+  for (int64_t p = gtid; p < a.n; p += gsize) {
+    const int32_t i = a.order[p];
+    a.inv[i] = (int32_t)p;
+    const double X = a.x[i], Y = a.y[i], Z = a.z[i];
+    a.xs[p] = X;
+    a.ys[p] = Y;
+    a.zs[p] = Z;
+    a.xb[p] = X;
+    a.yb[p] = Y;
+    a.ws[p] = a.w[i];
+    if (a.typ) a.ts[p] = a.typ[i];
+    if (a.mol) a.ms[p] = a.mol[i];
+    const float4 f = make_float4((float)X, (float)Y, (float)Z, (float)a.w[i]);
+    a.pf[p] = f;
+    a.pfb[p] = f;
+    a.us[p] = to_turns64(X, a.invL.x);
+    a.us[a.n + p] = to_turns64(Y, a.invL.y);
+    a.us[2 * a.n + p] = to_turns64(Z, a.invL.z);
+    a.cell_s[p] = a.cell[i];
+  }
+  grid.sync();
+  // ---- phase 7: ion lists (warp per ion)
+  for (int64_t p = gwarp; p < a.n; p += nwarps) {
+    const float4 me = a.pf[p];
+    const int cell = a.cell_s[p];
+    const int nii = build_list(a, a.runs, a.run_first, cell, a.start, a.pf, me.x, me.y, me.z, p,
+                               a.ii + p * a.cap, lane);
+    const int nie = build_list(a, a.runs, a.run_first, cell, a.eles.start, a.eles.pf, me.x, me.y, me.z, -1,
+                               a.ie + p * a.cap, lane);
+    if (lane == 0) {
+      a.ii_n[p] = nii;
+      a.ie_n[p] = nie;
+    }
+  }
+  // ---- phase 8: electrode-ion lists (warp per electrode site)
+  for (int64_t j = gwarp; j < a.ne; j += nwarps) {
+    const int nei = build_list(a, a.runs, a.run_first, a.ecell[j], a.start, a.pf, (float)a.ex[j], (float)a.ey[j],
+                               (float)a.ez[j], -1, a.ei + j * a.cap, lane);
+    if (lane == 0) a.ei_n[j] = nei;
+  }
+  grid.sync();
+  if (gtid == 0) {
+    a.flag[0] = 0;
+    a.flag[1] = 0;
+  }
+}
+
+void neighbor_force_rebuild(srbe_ctx *c) {
+  int *f = c->nbr.flag.ensure(2);
+  const int one[2] = {1, 1};
+  SRBE_CUDA(cudaMemcpyAsync(f, one, sizeof(one), cudaMemcpyHostToDevice, c->stream));
+  SRBE_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void neighbor_update(srbe_ctx *c) {
+  Cells &cl = c->icells;
+  NbrLists &nb = c->nbr;
+  const int64_t n = c->ni;
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  const int ncell = cl.g.ncell();
+  SRBE_REQUIRE(nb.cap > 0 && nb.ii.cap >= nn * (size_t)nb.cap, SRBE_ESTATE, "neighbor lists not reserved");
+  NbrKernelArgs a;
+  a.n = n;
+  a.ne = c->ne;
+  a.ncell = ncell;
+  a.cap = nb.cap;
+  a.x = c->x.p;
+  a.y = c->y.p;
+  a.z = c->z.p;
+  a.w = c->q.p;
+  a.typ = c->have_md ? c->itype.p : nullptr;
+  a.mol = c->have_md ? c->mol.p : nullptr;
+  a.cell = cl.cell.p;
+  a.rank = cl.rank.p;
+  a.start = cl.start.p;
+  a.order = cl.order.p;
+  a.inv = cl.inv.p;
+  a.ts = cl.ts.p;
+  a.ms = cl.ms.p;
+  a.cell_s = nb.cell_s.p;
+  a.xs = cl.xs.p;
+  a.ys = cl.ys.p;
+  a.zs = cl.zs.p;
+  a.ws = cl.ws.p;
+  a.xb = nb.xb.p;
+  a.yb = nb.yb.p;
+  a.pf = cl.pf.p;
+  a.pfb = nb.pfb.p;
+  a.us = cl.us.p;
+  a.ii = nb.ii.p;
+  a.ie = nb.ie.p;
+  a.ei = nb.ei.p;
+  a.ii_n = nb.ii_n.p;
+  a.ie_n = nb.ie_n.p;
+  a.ei_n = nb.ei_n.p;
+  a.g = to_dev(cl.g);
+  a.runs = c->runtab.runs.p;
+  a.run_first = c->runtab.first.p;
+  a.eles = cells_dev(c->ecells, c->runtab);
+  a.ecell = c->ecells.cell.p;
+  a.ex = c->ex.p;
+  a.ey = c->ey.p;
+  a.ez = c->ez.p;
+  a.Lx = c->L[0];
+  a.Ly = c->L[1];
+  a.invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
+  const float reach = (float)(c->rc + nb.skin) + (c->precision == SRBE_MIXED ? 0.f : kPrecheckMargin);
+  a.cut2 = reach * reach;
+  a.half_skin2 = (float)(0.25 * nb.skin * nb.skin);
+  a.flag = nb.flag.p;
+  static int blocks_per_sm = 0, nsm = 0;
+  if (!blocks_per_sm) {
+    int dev = 0;
+    SRBE_CUDA(cudaGetDevice(&dev));
+    SRBE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SRBE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_neighbor_update, 256, 0));
+    SRBE_REQUIRE(blocks_per_sm > 0, SRBE_ECUDA, "neighbor-update kernel cannot be resident");
+  }
+  const int want = (int)std::max<int64_t>(1, std::min<int64_t>((std::max<int64_t>(n, c->ne) * 32 + 255) / 256,
+                                                                 (int64_t)blocks_per_sm * nsm));
+  void *args[] = {&a};
+  SRBE_CUDA(cudaLaunchCooperativeKernel((const void *)k_neighbor_update, dim3(want), dim3(256), args, 0, c->stream));
+  c->launches++;
 }
 
 void electrode_rhs(srbe_ctx *c) {
   const int K = c->K;
-  double2 *coef = c->coef.p;
-  if (K > 0) {
-    k_coef<<<blocks_for(K, 128), 128, 0, c->stream>>>(K, c->dc.p, c->S1.p, coef, c->coef32.p, 0);
-    c->launches++;
-  }
+  double2 *coef = c->coef.p;   // written by the S1 reduction
   const double3 invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
   const double slab = 4.0 * kPi / c->V;
   const CellsDev ions = cells_dev(c->icells, c->runtab);
@@ -644,13 +1008,13 @@ void electrode_rhs(srbe_ctx *c) {
   if (c->precision == SRBE_MIXED)
     k_electrode_rhs<true><<<nb, kGatherThreads, 0, c->stream>>>(c->ne, c->ex.p, c->ey.p, c->ez.p, c->eu.p, K, c->dm.p,
                                                                coef,
-                                                               c->coef32.p, c->tab.p, invL, ions, c->L[0], c->L[1], c->alpha,
-                                                               c->eta, c->rc, slab, c->scal.p, c->bvec.p);
+                                                               c->coef32.p, c->tab.p, invL, ions, lists_dev(c), c->L[0], c->L[1], c->alpha,
+                                                               c->eta, c->rc, slab, c->scal.p, c->bvec.p, c->bsplit.p);
   else
     k_electrode_rhs<false><<<nb, kGatherThreads, 0, c->stream>>>(c->ne, c->ex.p, c->ey.p, c->ez.p, c->eu.p, K, c->dm.p,
                                                                coef,
-                                                                c->coef32.p, c->tab.p, invL, ions, c->L[0], c->L[1], c->alpha,
-                                                                c->eta, c->rc, slab, c->scal.p, c->bvec.p);
+                                                                c->coef32.p, c->tab.p, invL, ions, lists_dev(c), c->L[0], c->L[1], c->alpha,
+                                                                c->eta, c->rc, slab, c->scal.p, c->bvec.p, c->bsplit.p);
   c->launches++;
   c->mode_evals += c->ne * (int64_t)K;
   SRBE_CUDA(cudaGetLastError());
@@ -664,7 +1028,8 @@ void electrode_rhs(srbe_ctx *c) {
 // F_i = - q_i sum_k c_k k Im(S exp(-i k . r_i)) = - q_i sum_k k (cIm cos - cRe sin)   (Eq. 25)
 template <bool F32>
 __global__ void __launch_bounds__(kGatherThreads)
-k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, const double *__restrict__ Q, const float *__restrict__ Q32,
+k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double *__restrict__ Q,
+             const float *__restrict__ Q32,
              int K, const int4 *__restrict__ modes, const double2 *__restrict__ coefF,
              const float2 *__restrict__ coefF32, const double2 *__restrict__ tab,
              double3 invL, float3 kvf, double Lx, double Ly, double alpha, double eta, double rc, double slab,
@@ -721,8 +1086,20 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, const double *__restrict_
     const float cut2 = F32 ? rcf * rcf : (rcf + kPrecheckMargin) * (rcf + kPrecheckMargin);
     PairAcc A;
     int2 *q = wq[warp];
-    compacted_pairs(S, ions, true, cut2, q, lane, [&](int2 e) { pair_ion_ion<F32>(S, ions, md, e, A); });
-    compacted_pairs(S, eles, false, cut2, q, lane, [&](int2 e) { pair_ion_ele<F32>(S, eles, md, Q, Q32, e, A); });
+    // Verlet lists; a particle whose list overflowed walks the stencil of its build cell instead
+    const int nii = nl.ii_n[p], nie = nl.ie_n[p];
+    if (nii <= nl.cap)
+      compacted_list(S, ions, nl.ii + p * nl.cap, nii, cut2, q, lane,
+                     [&](int2 e) { pair_ion_ion<F32>(S, ions, md, e, A); });
+    else
+      compacted_pairs(S, ions, nl.cell_s[p], true, cut2, q, lane,
+                      [&](int2 e) { pair_ion_ion<F32>(S, ions, md, e, A); });
+    if (nie <= nl.cap)
+      compacted_list(S, eles, nl.ie + p * nl.cap, nie, cut2, q, lane,
+                     [&](int2 e) { pair_ion_ele<F32>(S, eles, md, Q, Q32, e, A); });
+    else
+      compacted_pairs(S, eles, nl.cell_s[p], false, cut2, q, lane,
+                      [&](int2 e) { pair_ion_ele<F32>(S, eles, md, Q, Q32, e, A); });
     const float Xf = S.Xf, Yf = S.Yf, Zf = S.Zf, qf = S.qf;
     double rr[3] = {A.r[0], A.r[1], A.r[2]}, ll[3] = {A.l[0], A.l[1], A.l[2]};
     e_ii = A.dii;
@@ -865,11 +1242,7 @@ __global__ void k_sum_partials(int nblk, int width, const double *__restrict__ p
 
 void ion_forces(srbe_ctx *c, bool energies) {
   const int K = c->K;
-  double2 *coef = c->coef.p;
-  if (K > 0) {
-    k_coef<<<blocks_for(K, 128), 128, 0, c->stream>>>(K, c->dc.p, c->S2.p, coef, c->coef32.p, 1);
-    c->launches++;
-  }
+  double2 *coef = c->coef.p;   // written by the S2 reduction (S = S1 + S2)
   MdDev md{};
   if (c->have_md) {
     md.ntype = c->ntype;
@@ -894,11 +1267,11 @@ void ion_forces(srbe_ctx *c, bool energies) {
   if (c->ni > 0) {
     if (c->precision == SRBE_MIXED)
       k_ion_forces<true><<<nblk, kGatherThreads, 0, c->stream>>>(
-          c->ni, ions, eles, c->Q.p, c->Q32.p, K, c->dm.p, coef, c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta, c->rc,
+          c->ni, ions, eles, lists_dev(c), c->Q.p, c->Q32.p, K, c->dm.p, coef, c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta, c->rc,
           slab, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep);
     else
       k_ion_forces<false><<<nblk, kGatherThreads, 0, c->stream>>>(
-          c->ni, ions, eles, c->Q.p, c->Q32.p, K, c->dm.p, coef, c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta, c->rc,
+          c->ni, ions, eles, lists_dev(c), c->Q.p, c->Q32.p, K, c->dm.p, coef, c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta, c->rc,
           slab, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep);
     c->launches++;
     c->mode_evals += c->ni * (int64_t)K;

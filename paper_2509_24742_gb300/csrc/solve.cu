@@ -172,6 +172,136 @@ __global__ void k_gemv_rows(int64_t nrow, int64_t ncol, const T *__restrict__ M,
   }
 }
 
+// Charge update Q = B b + dpsi q_d and psi_bar = -(w_e . b + dpsi w_e . d) / s_e (Eqs. 9-10), one
+// warp per row (row n: the w_e row).  FP64 form: double2 loads, four in flight per lane.
+__global__ void __launch_bounds__(256)
+k_charges_fp64(int64_t n, const double *__restrict__ B, const double *__restrict__ b, double dpsi,
+               const double *__restrict__ qd, const double *__restrict__ we, double wd, double s_e,
+               double *__restrict__ Q, float *__restrict__ Q32, double *__restrict__ scal) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row > n) return;
+  const double *r = row < n ? B + row * n : we;
+  double a0 = 0.0, a1 = 0.0;
+  int64_t j = 0;
+  if ((n & 1) == 0) {
+    const double2 *r2 = reinterpret_cast<const double2 *>(r);
+    const double2 *b2 = reinterpret_cast<const double2 *>(b);
+    const int64_t h = n >> 1;
+    int64_t k = lane;
+    for (; k + 96 < h; k += 128) {
+      const double2 m0 = __ldcs(r2 + k), m1 = __ldcs(r2 + k + 32), m2 = __ldcs(r2 + k + 64),
+                    m3 = __ldcs(r2 + k + 96);
+      const double2 v0 = __ldg(b2 + k), v1 = __ldg(b2 + k + 32), v2 = __ldg(b2 + k + 64), v3 = __ldg(b2 + k + 96);
+      a0 = fma(m0.x, v0.x, a0);
+      a1 = fma(m0.y, v0.y, a1);
+      a0 = fma(m1.x, v1.x, a0);
+      a1 = fma(m1.y, v1.y, a1);
+      a0 = fma(m2.x, v2.x, a0);
+      a1 = fma(m2.y, v2.y, a1);
+      a0 = fma(m3.x, v3.x, a0);
+      a1 = fma(m3.y, v3.y, a1);
+    }
+    for (; k < h; k += 32) {
+      const double2 m0 = __ldcs(r2 + k), v0 = __ldg(b2 + k);
+      a0 = fma(m0.x, v0.x, a0);
+      a1 = fma(m0.y, v0.y, a1);
+    }
+    j = n;
+  }
+  for (int64_t jj = j + lane; jj < n; jj += 32) a0 = fma(r[jj], __ldg(b + jj), a0);
+  double acc = a0 + a1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    if (row < n) {
+      const double q = fma(dpsi, qd[row], acc);
+      Q[row] = q;
+      Q32[row] = (float)q;
+    } else {
+      scal[kScalPsi] = -(acc + dpsi * wd) / s_e;
+    }
+  }
+}
+
+// Double-float arithmetic (pairs of FP32 with error-free transformations): products by FMA,
+// sums by Knuth's TwoSum; about 2^-48 relative accuracy with only FP32 instructions.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, float b) {
+  const float s = a.hi + b, bb = s - a.hi, err = (a.hi - (s - bb)) + (b - bb);
+  return DF{s, a.lo + err};
+}
+__device__ __forceinline__ DF df_add_df(DF a, DF b) {
+  const float s = a.hi + b.hi, bb = s - a.hi, err = (a.hi - (s - bb)) + (b.hi - bb);
+  const float lo = err + a.lo + b.lo;
+  const float h = s + lo;
+  return DF{h, lo - (h - s)};
+}
+
+// Mixed form of the same update: B and b as (hi, lo) FP32 pairs; every term is the exact product
+// hi*hi (FMA remainder) plus the cross terms, accumulated as a double-float.  Only the final
+// combination with dpsi q_d and psi_bar run in FP64 (one lane per row).
+__global__ void __launch_bounds__(256)
+k_charges_split(int64_t n, const float2 *__restrict__ B, const float2 *__restrict__ b, double dpsi,
+                const double *__restrict__ qd, const float2 *__restrict__ we, double wd, double s_e,
+                double *__restrict__ Q, float *__restrict__ Q32, double *__restrict__ scal) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row > n) return;
+  const float2 *r = row < n ? B + row * n : we;
+  DF acc{0.f, 0.f};
+  float lo = 0.f;
+  int64_t k = lane;
+  for (; k + 96 < n; k += 128) {
+    float2 m[4], v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      m[u] = __ldcs(r + k + 32 * u);
+      v[u] = __ldg(b + k + 32 * u);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float p = m[u].x * v[u].x;
+      const float e = fmaf(m[u].x, v[u].x, -p);
+      lo += e + fmaf(m[u].x, v[u].y, m[u].y * v[u].x);
+      acc = df_add(acc, p);
+    }
+  }
+  for (; k < n; k += 32) {
+    const float2 m0 = __ldcs(r + k), v0 = __ldg(b + k);
+    const float p = m0.x * v0.x;
+    const float e = fmaf(m0.x, v0.x, -p);
+    lo += e + fmaf(m0.x, v0.y, m0.y * v0.x);
+    acc = df_add(acc, p);
+  }
+  acc.lo += lo;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF other{__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)};
+    // order the operands by lane so that both partners compute the identical sum
+    acc = (lane & o) ? df_add_df(other, acc) : df_add_df(acc, other);
+  }
+  if (lane == 0) {
+    const double a = (double)acc.hi + (double)acc.lo;
+    if (row < n) {
+      const double q = fma(dpsi, qd[row], a);
+      Q[row] = q;
+      Q32[row] = (float)q;
+    } else {
+      scal[kScalPsi] = -(a + dpsi * wd) / s_e;
+    }
+  }
+}
+
+__global__ void k_split(int64_t n, const double *__restrict__ a, float2 *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float hi = (float)a[i];
+  out[i] = make_float2(hi, (float)(a[i] - (double)hi));
+}
+
 __global__ void k_rowsum(int64_t ne, const double *__restrict__ A, double *__restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -304,8 +434,10 @@ void build_A_and_inverse(srbe_ctx *c) {
   double *qd = c->qd.ensure(ne);
   k_gemv_rows<double><<<blocks_for(ne * 32, 256), 256, 0, c->stream>>>(ne, ne, A, c->ed.p, 0.0, nullptr, qd, nullptr,
                                                                       0.0, 1.0, nullptr);
-  float *B32 = c->Bmat32.ensure((size_t)ne * ne);
-  k_to_float<<<blocks_for(ne * ne, 256), 256, 0, c->stream>>>(ne * ne, A, B32);
+  float2 *Bs = c->Bsplit.ensure((size_t)ne * ne);
+  k_split<<<blocks_for(ne * ne, 256), 256, 0, c->stream>>>(ne * ne, A, Bs);
+  k_split<<<blocks_for(ne, 256), 256, 0, c->stream>>>(ne, we, c->wesplit.ensure(ne));
+  c->bsplit.ensure(ne);
   c->launches += 4;
   SRBE_CUDA(cudaGetLastError());
   SRBE_CUDA(cudaStreamSynchronize(c->stream));
@@ -314,8 +446,12 @@ void build_A_and_inverse(srbe_ctx *c) {
 void charge_update(srbe_ctx *c) {
   const int64_t ne = c->ne;
   const unsigned nb = blocks_for((ne + 1) * 32, 256);
-  k_gemv_rows<double><<<nb, 256, 0, c->stream>>>(ne, ne, c->Bmat.p, c->bvec.p, c->dpsi, c->qd.p, c->Q.p, c->we.p,
-                                                 c->wd, c->s_e, c->scal.p, c->Q32.p);
+  if (c->precision == SRBE_MIXED)
+    k_charges_split<<<nb, 256, 0, c->stream>>>(ne, c->Bsplit.p, c->bsplit.p, c->dpsi, c->qd.p, c->wesplit.p, c->wd,
+                                               c->s_e, c->Q.p, c->Q32.p, c->scal.p);
+  else
+    k_charges_fp64<<<nb, 256, 0, c->stream>>>(ne, c->Bmat.p, c->bvec.p, c->dpsi, c->qd.p, c->we.p, c->wd, c->s_e,
+                                              c->Q.p, c->Q32.p, c->scal.p);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }

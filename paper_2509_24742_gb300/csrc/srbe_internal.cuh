@@ -87,6 +87,20 @@ struct RunTable {
   DevBuf<int32_t> first;
 };
 
+// Verlet lists (rc + skin), rebuilt on the device when an ion has moved more than skin / 2 since
+// the last build.  Entries pack a sorted index (bits 0-23) and the image shifts (ix + 8, iy + 8) in
+// 4 bits each (bits 24-27, 28-31).
+struct NbrLists {
+  DevBuf<int32_t> ii, ie, ei;        // ion-ion [ni][cap], ion-electrode [ni][cap], electrode-ion [ne][cap]
+  DevBuf<int32_t> ii_n, ie_n, ei_n;  // entry counts (can exceed cap: the gathers then walk the stencil)
+  int cap = 0;
+  DevBuf<double> xb, yb;             // sorted x, y at the last build (unwrapping reference)
+  DevBuf<float4> pfb;                // sorted FP32 positions at the last build
+  DevBuf<int32_t> cell_s;            // cell of each sorted ion at the last build
+  DevBuf<int> flag;                  // [0] rebuild needed, [1] forced by the host
+  double skin = 0.1;
+};
+
 struct Cells {
   CellGrid g;
   DevBuf<int32_t> cell, rank, start, order;   // order: sorted position -> original index
@@ -129,15 +143,19 @@ struct srbe_ctx {
   srbe::DevBuf<double> ex, ey, ez, ed;         // positions and d (-1/2 | +1/2)
   srbe::DevBuf<uint64_t> eu;                   // fixed-point phase coordinates [3][ne], site order
   srbe::DevBuf<double> Bmat;                   // projected inverse J A^-1, ne x ne row-major
-  srbe::DevBuf<float> Bmat32;                  // its FP32 copy (mixed form)
+  srbe::DevBuf<float2> Bsplit;                 // its (hi, lo) FP32 split (mixed form)
   srbe::DevBuf<double> Amat;                   // A itself (kept for the refinement residual)
   srbe::DevBuf<double> we, qd;                 // A^-1 e and (J A^-1) d
   srbe::DevBuf<double> bvec, Q;                // per-step b and charges
+  srbe::DevBuf<float2> bsplit;                 // b as (hi, lo) FP32 pairs (mixed form)
+  srbe::DevBuf<float2> wesplit;                // A^-1 e as (hi, lo) FP32 pairs
   double s_e = 0, wd = 0;                      // e^T A^-1 e and (A^-1 e)^T d
   std::vector<double> hR;                      // host copy of R
+  double wall_span = 0;                        // z extent of the electrode sites
   std::vector<int8_t> hside;
   srbe::Cells ecells;
   srbe::RunTable runtab;                       // stencil runs of the shared ion / electrode grid
+  srbe::NbrLists nbr;                          // Verlet lists of the real-space sums
 
   // electrolyte
   int64_t ni = 0;
@@ -258,8 +276,12 @@ void build_cells(srbe_ctx *c, Cells &cl, int64_t n, const double *x, const doubl
                  const double *w, const int32_t *typ, const int32_t *mol, bool is_ion);
 void choose_grid(const srbe_ctx *c, CellGrid &g, double zlo, double zhi);
 void build_run_table(srbe_ctx *c);
+void neighbor_update(srbe_ctx *c);
+void neighbor_force_rebuild(srbe_ctx *c);
+// coef_mode: -1 none, 0 writes (c Re S, c Im S) for the electrode right-hand side, 1 writes
+// (c Im S, c Re S) for the ion forces, into ctx->coef / coef32
 void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *w,
-                      double2 *S, const double2 *S_add, int mslot);
+                      double2 *S, const double2 *S_add, int mslot, int coef_mode);
 void electrode_rhs(srbe_ctx *c);
 void charge_update(srbe_ctx *c);
 void ion_forces(srbe_ctx *c, bool energies);
