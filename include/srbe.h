@@ -169,6 +169,40 @@ int srbe_get_counters(const srbe_ctx *ctx, int64_t *kernel_launches, int64_t *mo
 int srbe_set_profiling(srbe_ctx *ctx, int on);
 int srbe_get_phase_times(srbe_ctx *ctx, double *ms, int64_t *count);
 
+/* ---- iterative charge solve and the learned warm start ------------------------------------------
+ * The per-step charge update can run preconditioned conjugate gradients on A y = dpsi d + b
+ * (Jacobi preconditioner, one cooperative launch, convergence tested on the device) instead of the
+ * direct projected inverse; Q and psi_bar then follow from Eqs. 9-10.  The starting guess is zero,
+ * the previous step's solution, or the prediction of a per-site MLP (the learned form; no
+ * counterpart in the paper).  tol is the relative residual ||dpsi d + b - A y|| / ||dpsi d + b||. */
+enum srbe_solver { SRBE_SOLVER_DIRECT = 0, SRBE_SOLVER_PCG = 1 };
+enum srbe_warm { SRBE_WARM_ZERO = 0, SRBE_WARM_PREVIOUS = 1, SRBE_WARM_MODEL = 2 };
+int srbe_set_solver(srbe_ctx *ctx, int kind, double tol, int maxit, int warm);
+/* Iterations and the recomputed relative residual of the last PCG solve. */
+int srbe_get_solver_stats(srbe_ctx *ctx, int *iterations, double *rel_residual);
+
+/* The MLP (80 -> 128 -> 128 -> 1, SiLU, FP32) predicts y = A^-1 (dpsi d + b) per electrode site from
+ * 80 descriptors: 32 Gaussian radial densities (centres 0.25..1.25 nm, width 0.035 nm) of the
+ * positive and of the negative ion charge within rc, and Re, Im of exp(-i k_z Z_j) S1(k_z) for the 8
+ * lowest k_z modes.  Parameters are one float vector (srbe_mlp_get_params gives its length):
+ * W1[128][80], b1, W2[128][128], b2, W3[128], b3, input mean[80], input spread[80], target mean,
+ * target spread; inputs and target are standardised by the last four. */
+int srbe_mlp_init(srbe_ctx *ctx, uint64_t seed);
+int srbe_mlp_get_params(srbe_ctx *ctx, float *params, int64_t *count);
+int srbe_mlp_set_params(srbe_ctx *ctx, const float *params, int64_t count);
+/* Descriptors [n_ele][80] of the current configuration; valid after a charge update or force call. */
+int srbe_descriptors(srbe_ctx *ctx, float *D);
+/* The unprojected solution y = Q - psi_bar A^-1 e [n_ele] of the last charge update (the target). */
+int srbe_solution(srbe_ctx *ctx, double *y);
+int srbe_mlp_predict(srbe_ctx *ctx, const float *D, int64_t n, float *out);
+/* Gradient of the mean squared standardised error over n rows (no update); grad has the length of
+ * the trainable part of the parameter vector (everything before the input mean). */
+int srbe_mlp_gradients(srbe_ctx *ctx, const float *D, const float *target, int64_t n, float *grad, double *loss);
+/* Sets the standardisation from the data, then epochs of shuffled minibatch AdamW (lr, decoupled
+ * weight decay); returns the mean loss of the last epoch. */
+int srbe_mlp_train(srbe_ctx *ctx, const float *D, const float *target, int64_t n, int epochs, int batch, float lr,
+                   float weight_decay, uint64_t seed, double *final_loss);
+
 /* Structure factor without any device allocation (no counterpart in the paper; an interface
  * for callers that cannot allocate device memory, e.g. an MD engine that hands out every byte of
  * GPU memory from its own pool, or code that must not allocate while its pipeline runs).

@@ -236,6 +236,13 @@ __global__ void k_site_turns(int64_t n, const double *__restrict__ x, const doub
   u[2 * n + i] = to_turns64(z[i], invL.z);
 }
 
+// y = Q - psi_bar A^-1 e (inverse of Q = y + psi_bar A^-1 e, Eq. 10)
+__global__ void k_unproject(int64_t n, const double *__restrict__ Q, const double *__restrict__ we,
+                            const double *__restrict__ scal, double *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = fma(-scal[kScalPsi], we[i], Q[i]);
+}
+
 __global__ void k_interleave(int64_t n, const double *__restrict__ F, double *__restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -978,6 +985,232 @@ int srbe_minimize(srbe_ctx *c, int nsteps, double a, double dmax, uint64_t seed)
     }
     extra(c)->forces_valid = false;
     SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+// ---- iterative solve and learned warm start ---------------------------------------------------
+int srbe_set_solver(srbe_ctx *c, int kind, double tol, int maxit, int warm) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(kind == SRBE_SOLVER_DIRECT || kind == SRBE_SOLVER_PCG, SRBE_EINVAL, "unknown solver");
+    SRBE_REQUIRE(warm >= SRBE_WARM_ZERO && warm <= SRBE_WARM_MODEL, SRBE_EINVAL, "unknown warm start");
+    SRBE_REQUIRE(tol > 0 && tol < 1 && maxit > 0, SRBE_EINVAL, "bad tolerance or iteration limit");
+    SRBE_REQUIRE(c->have_ele, SRBE_ESTATE, "srbe_set_electrode must come first");
+    c->pcg.on = kind == SRBE_SOLVER_PCG;
+    c->pcg.tol = tol;
+    c->pcg.maxit = maxit;
+    c->pcg.warm = warm;
+    if (c->pcg.on) pcg_prepare(c);
+  });
+}
+
+int srbe_get_solver_stats(srbe_ctx *c, int *iterations, double *rel_residual) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(c->pcg.on, SRBE_ESTATE, "the iterative solver is not selected");
+    int it = 0;
+    double r = 0.0;
+    SRBE_CUDA(cudaMemcpyAsync(&it, c->pcg.stats.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SRBE_CUDA(cudaMemcpyAsync(&r, c->pcg.res.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    if (iterations) *iterations = it;
+    if (rel_residual) *rel_residual = r;
+  });
+}
+
+namespace {
+void mlp_alloc(srbe_ctx *c) {
+  const size_t n = (size_t)mlp_param_count();
+  c->mlp.P.ensure(n);
+  c->mlp.m1.ensure(n);
+  c->mlp.m2.ensure(n);
+  c->mlp.grad.ensure(n);
+}
+void mlp_reset_moments(srbe_ctx *c) {
+  const size_t n = (size_t)mlp_param_count();
+  SRBE_CUDA(cudaMemsetAsync(c->mlp.m1.p, 0, sizeof(float) * n, c->stream));
+  SRBE_CUDA(cudaMemsetAsync(c->mlp.m2.p, 0, sizeof(float) * n, c->stream));
+  c->mlp.t = 0;
+}
+}  // namespace
+
+int srbe_mlp_init(srbe_ctx *c, uint64_t seed) {
+  return guarded(c, [&] {
+    const int n = mlp_param_count(), nin = mlp_input_width(), nh = 128;
+    std::vector<float> P(n, 0.f);
+    // Glorot-uniform weights from Philox4x64-10 words, zero biases, identity standardisation
+    uint64_t ctr = 0;
+    auto uniform = [&](double lim) {
+      const uint64_t c4[4] = {ctr++, 0, 0, 0x4d4c5000ull};
+      uint64_t w[4];
+      Philox4x64::block(c4, seed, 0x5352424500000003ull, w);
+      return (float)((2.0 * unit_open0(w[0]) - 1.0) * lim);
+    };
+    const double l1 = std::sqrt(6.0 / (nin + nh)), l2 = std::sqrt(6.0 / (nh + nh)), l3 = std::sqrt(6.0 / (nh + 1));
+    size_t o = 0;
+    for (int i = 0; i < nh * nin; ++i) P[o++] = uniform(l1);
+    o += nh;
+    for (int i = 0; i < nh * nh; ++i) P[o++] = uniform(l2);
+    o += nh;
+    for (int i = 0; i < nh; ++i) P[o++] = uniform(l3);
+    o += 1;
+    o += nin;                                   // input means 0
+    for (int i = 0; i < nin; ++i) P[o++] = 1.f;  // input spreads 1
+    P[o++] = 0.f;                               // target mean
+    P[o++] = 1.f;                               // target spread
+    mlp_alloc(c);
+    SRBE_CUDA(cudaMemcpyAsync(c->mlp.P.p, P.data(), sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
+    mlp_reset_moments(c);
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    c->mlp.ready = true;
+  });
+}
+
+int srbe_mlp_get_params(srbe_ctx *c, float *params, int64_t *count) {
+  return guarded(c, [&] {
+    if (count) *count = mlp_param_count();
+    if (!params) return;
+    SRBE_REQUIRE(c->mlp.ready, SRBE_ESTATE, "no MLP parameters");
+    SRBE_CUDA(cudaMemcpyAsync(params, c->mlp.P.p, sizeof(float) * mlp_param_count(), cudaMemcpyDeviceToHost,
+                              c->stream));
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+int srbe_mlp_set_params(srbe_ctx *c, const float *params, int64_t count) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(params && count == mlp_param_count(), SRBE_EINVAL, "parameter vector of the wrong length");
+    for (int64_t i = 0; i < count; ++i) SRBE_REQUIRE(std::isfinite(params[i]), SRBE_EINVAL, "non-finite parameter");
+    mlp_alloc(c);
+    SRBE_CUDA(cudaMemcpyAsync(c->mlp.P.p, params, sizeof(float) * count, cudaMemcpyHostToDevice, c->stream));
+    mlp_reset_moments(c);
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    c->mlp.ready = true;
+  });
+}
+
+int srbe_descriptors(srbe_ctx *c, float *D) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(D, SRBE_EINVAL, "null output");
+    SRBE_REQUIRE(c->have_ele && c->have_pos && c->nbr.cap > 0, SRBE_ESTATE,
+                 "descriptors need a charge update or force call first");
+    c->mlp.D.ensure((size_t)c->ne * mlp_input_width());
+    mlp_descriptors(c, c->mlp.D.p);
+    SRBE_CUDA(cudaMemcpyAsync(D, c->mlp.D.p, sizeof(float) * c->ne * mlp_input_width(), cudaMemcpyDeviceToHost,
+                              c->stream));
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+int srbe_solution(srbe_ctx *c, double *y) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(y, SRBE_EINVAL, "null output");
+    SRBE_REQUIRE(c->have_ele, SRBE_ESTATE, "no electrode");
+    k_unproject<<<blocks_for(c->ne, 256), 256, 0, c->stream>>>(c->ne, c->Q.p, c->we.p, c->scal.p,
+                                                              extra(c)->aos.ensure(std::max<int64_t>(c->ne, 1)));
+    c->launches++;
+    SRBE_CUDA(cudaGetLastError());
+    SRBE_CUDA(cudaMemcpyAsync(y, extra(c)->aos.p, sizeof(double) * c->ne, cudaMemcpyDeviceToHost, c->stream));
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+namespace {
+void upload_rows(srbe_ctx *c, const float *D, const float *T, int64_t n) {
+  const int w = mlp_input_width();
+  c->mlp.data_D.ensure((size_t)std::max<int64_t>(n, 1) * w);
+  SRBE_CUDA(cudaMemcpyAsync(c->mlp.data_D.p, D, sizeof(float) * n * w, cudaMemcpyHostToDevice, c->stream));
+  if (T) {
+    c->mlp.data_T.ensure((size_t)std::max<int64_t>(n, 1));
+    SRBE_CUDA(cudaMemcpyAsync(c->mlp.data_T.p, T, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
+  }
+}
+}  // namespace
+
+int srbe_mlp_predict(srbe_ctx *c, const float *D, int64_t n, float *out) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(D && out && n >= 0, SRBE_EINVAL, "bad arguments");
+    SRBE_REQUIRE(c->mlp.ready, SRBE_ESTATE, "no MLP parameters");
+    if (n == 0) return;
+    upload_rows(c, D, nullptr, n);
+    float *o = c->mlp.grad.ensure(std::max<size_t>((size_t)n, (size_t)mlp_param_count()));
+    mlp_forward(c, c->mlp.data_D.p, n, o, nullptr);
+    SRBE_CUDA(cudaMemcpyAsync(out, o, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+int srbe_mlp_gradients(srbe_ctx *c, const float *D, const float *target, int64_t n, float *grad, double *loss) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(D && target && grad && n > 0, SRBE_EINVAL, "bad arguments");
+    SRBE_REQUIRE(c->mlp.ready, SRBE_ESTATE, "no MLP parameters");
+    upload_rows(c, D, target, n);
+    const double l = mlp_grad_step(c, c->mlp.data_D.p, c->mlp.data_T.p, nullptr, n, c->mlp.grad.p, false, 0.f, 0.f);
+    int64_t ntrain = 0;
+    // the trainable part is everything before the input mean
+    ntrain = mlp_param_count() - 2 * mlp_input_width() - 2;
+    SRBE_CUDA(cudaMemcpyAsync(grad, c->mlp.grad.p, sizeof(float) * ntrain, cudaMemcpyDeviceToHost, c->stream));
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    if (loss) *loss = l;
+  });
+}
+
+int srbe_mlp_train(srbe_ctx *c, const float *D, const float *target, int64_t n, int epochs, int batch, float lr,
+                   float weight_decay, uint64_t seed, double *final_loss) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(D && target && n > 1 && epochs > 0 && batch > 0 && lr > 0, SRBE_EINVAL, "bad arguments");
+    SRBE_REQUIRE(c->mlp.ready, SRBE_ESTATE, "no MLP parameters (srbe_mlp_init)");
+    const int w = mlp_input_width(), np = mlp_param_count();
+    // standardisation from the data (mean and spread of every input column and of the target)
+    std::vector<float> P(np);
+    SRBE_CUDA(cudaMemcpy(P.data(), c->mlp.P.p, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    const int oXm = np - 2 * w - 2, oXs = oXm + w, oYm = oXs + w, oYs = oYm + 1;
+    for (int k = 0; k < w; ++k) {
+      double s = 0.0, s2 = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        const double v = D[i * w + k];
+        s += v;
+        s2 += v * v;
+      }
+      const double m = s / n, var = std::max(s2 / n - m * m, 0.0);
+      P[oXm + k] = (float)m;
+      P[oXs + k] = (float)std::max(std::sqrt(var), 1e-6);
+    }
+    double s = 0.0, s2 = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      s += target[i];
+      s2 += (double)target[i] * target[i];
+    }
+    const double m = s / n;
+    P[oYm] = (float)m;
+    P[oYs] = (float)std::max(std::sqrt(std::max(s2 / n - m * m, 0.0)), 1e-12);
+    SRBE_CUDA(cudaMemcpy(c->mlp.P.p, P.data(), sizeof(float) * np, cudaMemcpyHostToDevice));
+    mlp_reset_moments(c);
+    upload_rows(c, D, target, n);
+    c->mlp.rows.ensure((size_t)n);
+    std::vector<int32_t> perm(n);
+    double last = 0.0;
+    uint64_t ctr = 0;
+    for (int e = 0; e < epochs; ++e) {
+      for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+      for (int64_t i = n - 1; i > 0; --i) {   // Fisher-Yates with Philox draws
+        const uint64_t c4[4] = {ctr++, (uint64_t)e, 0, 0x53485546ull};
+        uint64_t wv[4];
+        Philox4x64::block(c4, seed, 0x5352424500000004ull, wv);
+        const int64_t j = (int64_t)(wv[0] % (uint64_t)(i + 1));
+        std::swap(perm[i], perm[j]);
+      }
+      SRBE_CUDA(cudaMemcpyAsync(c->mlp.rows.p, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
+      double tot = 0.0;
+      int64_t seen = 0;
+      for (int64_t b0 = 0; b0 < n; b0 += batch) {
+        const int64_t nb = std::min<int64_t>(batch, n - b0);
+        const double l = mlp_grad_step(c, c->mlp.data_D.p, c->mlp.data_T.p, c->mlp.rows.p + b0, nb, nullptr, true,
+                                       lr, weight_decay);
+        tot += l * nb;
+        seen += nb;
+      }
+      last = tot / seen;
+    }
+    if (final_loss) *final_loss = last;
   });
 }
 

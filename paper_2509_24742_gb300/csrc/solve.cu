@@ -12,7 +12,11 @@
 //
 // Per step (Eqs. 9-10):  Q = B b + dpsi q_d,  psi_bar = -(w_e^T b + dpsi w_e^T d) / s,
 // one dense FP64 matrix-vector product, one warp per row with a fixed-order shuffle reduction.
+#include <cooperative_groups.h>
+
 #include "srbe_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace srbe {
 
@@ -443,7 +447,211 @@ void build_A_and_inverse(srbe_ctx *c) {
   SRBE_CUDA(cudaStreamSynchronize(c->stream));
 }
 
+// ------------------------------------------------------------------------------------------------
+// Preconditioned conjugate gradients for A y = dpsi d + b (A symmetric positive definite, Eq. 18),
+// Jacobi preconditioner, in one cooperative launch: the matrix-vector products run one warp per
+// row, every dot product is a fixed-order two-level reduction (block partials, then each block sums
+// the partials in block order, so all blocks hold the same value without another barrier), and the
+// loop ends on the device when ||r|| <= tol ||v||.  Q and psi_bar follow from Eqs. 9-10:
+// psi_bar = -e^T y / (e^T A^-1 e), Q = y + psi_bar A^-1 e.
+// ------------------------------------------------------------------------------------------------
+struct PcgArgs {
+  int64_t n;
+  const double *A, *dinv, *b, *d, *we;
+  double dpsi, s_e, tol2;
+  int maxit;
+  double *y, *r, *z, *p, *Ap, *part;
+  double *Q, *scal;
+  float *Q32;
+  int *stats;        // [0] iterations
+  double *res;       // [0] final relative residual (recomputed)
+};
+
+__device__ double grid_dot_sum(const PcgArgs &a, double mine, int slot, cg::grid_group &grid) {
+  __shared__ double red[256];
+  const int t = threadIdx.x;
+  red[t] = mine;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (t < s) red[t] += red[t + s];
+    __syncthreads();
+  }
+  if (t == 0) a.part[slot * gridDim.x + blockIdx.x] = red[0];
+  grid.sync();
+  __shared__ double total;
+  if (t < 32) {
+    double acc = 0.0;
+    for (unsigned b = t; b < gridDim.x; b += 32) acc += __ldcg(&a.part[slot * gridDim.x + b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (t == 0) total = acc;
+  }
+  __syncthreads();
+  return total;
+}
+
+// out = v - A x (minus = true) or A x, rows grid-strided over warps
+__device__ void grid_gemv(const PcgArgs &a, const double *x, const double *v, double *out, bool minus) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = gw; row < a.n; row += nw) {
+    const double *Ar = a.A + row * a.n;
+    double acc = 0.0;
+    for (int64_t j = lane; j < a.n; j += 32) acc = fma(__ldcs(Ar + j), __ldcg(x + j), acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[row] = minus ? v[row] - acc : acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+  // v = dpsi d + b lives in p for the first product; r = v - A y
+  for (int64_t i = gt; i < a.n; i += gs) a.p[i] = fma(a.dpsi, a.d[i], a.b[i]);
+  grid.sync();
+  grid_gemv(a, a.y, a.p, a.r, true);
+  grid.sync();
+  double vv = 0.0, rz = 0.0, rr = 0.0;
+  for (int64_t i = gt; i < a.n; i += gs) {
+    const double v = a.p[i];
+    vv += v * v;
+  }
+  vv = grid_dot_sum(a, vv, 0, grid);
+  for (int64_t i = gt; i < a.n; i += gs) {
+    const double zi = a.dinv[i] * a.r[i];
+    a.z[i] = zi;
+    rz += a.r[i] * zi;
+    rr += a.r[i] * a.r[i];
+  }
+  rz = grid_dot_sum(a, rz, 1, grid);
+  rr = grid_dot_sum(a, rr, 2, grid);
+  for (int64_t i = gt; i < a.n; i += gs) a.p[i] = a.z[i];
+  grid.sync();
+  int it = 0;
+  while (it < a.maxit && rr > a.tol2 * vv) {
+    grid_gemv(a, a.p, nullptr, a.Ap, false);
+    grid.sync();
+    double pap = 0.0;
+    for (int64_t i = gt; i < a.n; i += gs) pap += a.p[i] * a.Ap[i];
+    pap = grid_dot_sum(a, pap, 3, grid);
+    const double alpha = rz / pap;
+    double rz1 = 0.0, rr1 = 0.0;
+    for (int64_t i = gt; i < a.n; i += gs) {
+      a.y[i] = fma(alpha, a.p[i], a.y[i]);
+      const double ri = fma(-alpha, a.Ap[i], a.r[i]);
+      a.r[i] = ri;
+      const double zi = a.dinv[i] * ri;
+      a.z[i] = zi;
+      rz1 += ri * zi;
+      rr1 += ri * ri;
+    }
+    rz1 = grid_dot_sum(a, rz1, 4 + (it & 1) * 2, grid);
+    rr1 = grid_dot_sum(a, rr1, 5 + (it & 1) * 2, grid);
+    const double beta = rz1 / rz;
+    rz = rz1;
+    rr = rr1;
+    for (int64_t i = gt; i < a.n; i += gs) a.p[i] = fma(beta, a.p[i], a.z[i]);
+    grid.sync();
+    ++it;
+  }
+  // true residual, neutrality projection and psi_bar (Eqs. 9-10)
+  for (int64_t i = gt; i < a.n; i += gs) a.z[i] = fma(a.dpsi, a.d[i], a.b[i]);
+  grid.sync();
+  grid_gemv(a, a.y, a.z, a.r, true);
+  grid.sync();
+  double r2 = 0.0, ey = 0.0;
+  for (int64_t i = gt; i < a.n; i += gs) {
+    r2 += a.r[i] * a.r[i];
+    ey += a.y[i];
+  }
+  r2 = grid_dot_sum(a, r2, 8, grid);
+  ey = grid_dot_sum(a, ey, 9, grid);
+  const double psi = -ey / a.s_e;
+  for (int64_t i = gt; i < a.n; i += gs) {
+    const double q = fma(psi, a.we[i], a.y[i]);
+    a.Q[i] = q;
+    a.Q32[i] = (float)q;
+  }
+  if (gt == 0) {
+    a.scal[kScalPsi] = psi;
+    a.stats[0] = it;
+    a.res[0] = sqrt(r2 / vv);
+  }
+}
+
+void charge_update_pcg(srbe_ctx *c) {
+  const int64_t n = c->ne;
+  static int blocks_per_sm = 0, nsm = 0;
+  if (!blocks_per_sm) {
+    int dev = 0;
+    SRBE_CUDA(cudaGetDevice(&dev));
+    SRBE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SRBE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pcg, 256, 0));
+    SRBE_REQUIRE(blocks_per_sm > 0, SRBE_ECUDA, "PCG kernel cannot be resident");
+  }
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n * 32 + 255) / 256, (int64_t)blocks_per_sm * nsm));
+  PcgArgs a;
+  a.n = n;
+  a.A = c->Amat.p;
+  a.dinv = c->pcg.dinv.p;
+  a.b = c->bvec.p;
+  a.d = c->ed.p;
+  a.we = c->we.p;
+  a.dpsi = c->dpsi;
+  a.s_e = c->s_e;
+  a.tol2 = c->pcg.tol * c->pcg.tol;
+  a.maxit = c->pcg.maxit;
+  a.y = c->pcg.y.p;
+  a.r = c->pcg.r.p;
+  a.z = c->pcg.z.p;
+  a.p = c->pcg.p.p;
+  a.Ap = c->pcg.Ap.p;
+  a.part = c->pcg.part.ensure((size_t)grid * 10);
+  a.Q = c->Q.p;
+  a.Q32 = c->Q32.p;
+  a.scal = c->scal.p;
+  a.stats = c->pcg.stats.p;
+  a.res = c->pcg.res.p;
+  void *args[] = {&a};
+  SRBE_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg, dim3(grid), dim3(256), args, 0, c->stream));
+  c->launches++;
+}
+
+__global__ void k_diag_inv(int64_t n, const double *__restrict__ A, double *__restrict__ dinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dinv[i] = 1.0 / A[i * n + i];
+}
+
+void pcg_prepare(srbe_ctx *c) {
+  const int64_t n = c->ne;
+  c->pcg.dinv.ensure(n);
+  c->pcg.y.ensure(n);
+  c->pcg.r.ensure(n);
+  c->pcg.z.ensure(n);
+  c->pcg.p.ensure(n);
+  c->pcg.Ap.ensure(n);
+  c->pcg.stats.ensure(4);
+  c->pcg.res.ensure(4);
+  k_diag_inv<<<blocks_for(n, 256), 256, 0, c->stream>>>(n, c->Amat.p, c->pcg.dinv.p);
+  SRBE_CUDA(cudaMemsetAsync(c->pcg.y.p, 0, sizeof(double) * n, c->stream));
+  SRBE_CUDA(cudaGetLastError());
+}
+
 void charge_update(srbe_ctx *c) {
+  if (c->pcg.on) {
+    if (c->pcg.warm == 0) {
+      SRBE_CUDA(cudaMemsetAsync(c->pcg.y.p, 0, sizeof(double) * c->ne, c->stream));
+    } else if (c->pcg.warm == 2) {
+      SRBE_REQUIRE(c->mlp.ready, SRBE_ESTATE, "learned warm start needs srbe_mlp_init or srbe_mlp_set_params");
+      c->mlp.D.ensure((size_t)c->ne * mlp_input_width());
+      mlp_descriptors(c, c->mlp.D.p);
+      mlp_forward(c, c->mlp.D.p, c->ne, nullptr, c->pcg.y.p);
+    }
+    charge_update_pcg(c);
+    return;
+  }
   const int64_t ne = c->ne;
   const unsigned nb = blocks_for((ne + 1) * 32, 256);
   if (c->precision == SRBE_MIXED)

@@ -101,6 +101,26 @@ struct NbrLists {
   double skin = 0.1;
 };
 
+// Iterative charge solve state (preconditioned CG on A y = dpsi d + b)
+struct PcgState {
+  bool on = false;
+  double tol = 1e-8;
+  int maxit = 1000;
+  int warm = 0;                      // 0 zero, 1 previous solution, 2 learned model
+  DevBuf<double> dinv, y, r, z, p, Ap, part, res;
+  DevBuf<int> stats;
+};
+
+// Learned warm start: MLP parameters, AdamW moments, scratch
+struct MlpState {
+  bool ready = false;
+  int t = 0;
+  DevBuf<float> P, m1, m2, gpart, grad, D, data_D, data_T;
+  DevBuf<double> lpart;
+  DevBuf<double2> Slow;
+  DevBuf<int32_t> rows;
+};
+
 struct Cells {
   CellGrid g;
   DevBuf<int32_t> cell, rank, start, order;   // order: sorted position -> original index
@@ -156,6 +176,8 @@ struct srbe_ctx {
   srbe::Cells ecells;
   srbe::RunTable runtab;                       // stencil runs of the shared ion / electrode grid
   srbe::NbrLists nbr;                          // Verlet lists of the real-space sums
+  srbe::PcgState pcg;                          // iterative charge solve
+  srbe::MlpState mlp;                          // learned warm start
 
   // electrolyte
   int64_t ni = 0;
@@ -284,6 +306,13 @@ void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, 
                       double2 *S, const double2 *S_add, int mslot, int coef_mode);
 void electrode_rhs(srbe_ctx *c);
 void charge_update(srbe_ctx *c);
+void pcg_prepare(srbe_ctx *c);
+int mlp_param_count();
+int mlp_input_width();
+void mlp_descriptors(srbe_ctx *c, float *D_dev);
+void mlp_forward(srbe_ctx *c, const float *D_dev, int64_t n, float *out_dev, double *out_y_dev);
+double mlp_grad_step(srbe_ctx *c, const float *D_dev, const float *T_dev, const int32_t *rows_dev, int64_t n,
+                     float *grad_dev, bool apply, float lr, float wd);
 void ion_forces(srbe_ctx *c, bool energies);
 void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift);
 void steepest_descent_move(srbe_ctx *c, double a, double dmax);

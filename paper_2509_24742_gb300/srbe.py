@@ -14,6 +14,9 @@ from . import build as _build
 
 SRBE_OK, SRBE_EINVAL, SRBE_ENOMEM, SRBE_ECUDA, SRBE_ESTATE, SRBE_ENOTCONV, SRBE_ETIMEOUT = range(7)
 FP64, MIXED = 0, 1
+DIRECT, PCG = 0, 1
+WARM_ZERO, WARM_PREVIOUS, WARM_MODEL = 0, 1, 2
+N_DESC = 80
 METROPOLIS, EXACT = 0, 1
 VOLT = 0.694461
 K_E = 138.935458
@@ -34,6 +37,7 @@ _lib = None
 _vp, _dp, _i64, _int, _u64, _dbl = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int, \
     ctypes.c_uint64, ctypes.c_double
 _ip = ctypes.POINTER(ctypes.c_int32)
+_fp = ctypes.POINTER(ctypes.c_float)
 _bp = ctypes.POINTER(ctypes.c_int8)
 
 EXPORTS = {
@@ -62,6 +66,17 @@ EXPORTS = {
     "srbe_get_phase_times": ([_vp, _dp, ctypes.POINTER(_i64)], _int),
     "srbe_structure_factor_noalloc": ([_dp, _i64, _vp, _vp, _int, _vp, _vp, _vp], _int),
     "srbe_minimize": ([_vp, _int, _dbl, _dbl, _u64], _int),
+    "srbe_set_solver": ([_vp, _int, _dbl, _int, _int], _int),
+    "srbe_get_solver_stats": ([_vp, ctypes.POINTER(_int), ctypes.POINTER(_dbl)], _int),
+    "srbe_mlp_init": ([_vp, _u64], _int),
+    "srbe_mlp_get_params": ([_vp, _fp, ctypes.POINTER(_i64)], _int),
+    "srbe_mlp_set_params": ([_vp, _fp, _i64], _int),
+    "srbe_descriptors": ([_vp, _fp], _int),
+    "srbe_solution": ([_vp, _dp], _int),
+    "srbe_mlp_predict": ([_vp, _fp, _i64, _fp], _int),
+    "srbe_mlp_gradients": ([_vp, _fp, _fp, _i64, _fp, ctypes.POINTER(_dbl)], _int),
+    "srbe_mlp_train": ([_vp, _fp, _fp, _i64, _int, _int, ctypes.c_float, ctypes.c_float, _u64,
+                        ctypes.POINTER(_dbl)], _int),
 }
 PHASES = ("upload", "cells", "S1", "rhs", "solve", "S2", "forces", "integrate", "energy")
 
@@ -247,6 +262,63 @@ class Context:
         cnt = (_i64 * len(PHASES))()
         self._check(self.lib.srbe_get_phase_times(self.h, _ptr(ms), cnt))
         return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+    # --- iterative solve and the learned warm start
+    def set_solver(self, kind=PCG, tol=1e-8, maxit=1000, warm=WARM_ZERO):
+        self._check(self.lib.srbe_set_solver(self.h, int(kind), float(tol), int(maxit), int(warm)))
+
+    def solver_stats(self):
+        it, res = _int(), _dbl()
+        self._check(self.lib.srbe_get_solver_stats(self.h, ctypes.byref(it), ctypes.byref(res)))
+        return it.value, res.value
+
+    def mlp_init(self, seed=0):
+        self._check(self.lib.srbe_mlp_init(self.h, int(seed)))
+
+    def mlp_params(self):
+        n = _i64()
+        self._check(self.lib.srbe_mlp_get_params(self.h, None, ctypes.byref(n)))
+        out = np.empty(n.value, np.float32)
+        self._check(self.lib.srbe_mlp_get_params(self.h, _ptr(out, _fp), ctypes.byref(n)))
+        return out
+
+    def mlp_set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self.lib.srbe_mlp_set_params(self.h, _ptr(p, _fp), p.size))
+
+    def descriptors(self):
+        D = np.empty((self.n_ele, N_DESC), np.float32)
+        self._check(self.lib.srbe_descriptors(self.h, _ptr(D, _fp)))
+        return D
+
+    def solution(self):
+        y = np.empty(self.n_ele)
+        self._check(self.lib.srbe_solution(self.h, _ptr(y)))
+        return y
+
+    def mlp_predict(self, D):
+        D = np.ascontiguousarray(D, dtype=np.float32).reshape(-1, N_DESC)
+        out = np.empty(D.shape[0], np.float32)
+        self._check(self.lib.srbe_mlp_predict(self.h, _ptr(D, _fp), D.shape[0], _ptr(out, _fp)))
+        return out
+
+    def mlp_gradients(self, D, T):
+        D = np.ascontiguousarray(D, dtype=np.float32).reshape(-1, N_DESC)
+        T = np.ascontiguousarray(T, dtype=np.float32).reshape(-1)
+        n = self.mlp_params().size - 2 * N_DESC - 2
+        g = np.empty(n, np.float32)
+        loss = _dbl()
+        self._check(self.lib.srbe_mlp_gradients(self.h, _ptr(D, _fp), _ptr(T, _fp), D.shape[0], _ptr(g, _fp),
+                                                ctypes.byref(loss)))
+        return g, loss.value
+
+    def mlp_train(self, D, T, epochs=10, batch=512, lr=1e-3, weight_decay=1e-4, seed=0):
+        D = np.ascontiguousarray(D, dtype=np.float32).reshape(-1, N_DESC)
+        T = np.ascontiguousarray(T, dtype=np.float32).reshape(-1)
+        loss = _dbl()
+        self._check(self.lib.srbe_mlp_train(self.h, _ptr(D, _fp), _ptr(T, _fp), D.shape[0], int(epochs), int(batch),
+                                            float(lr), float(weight_decay), int(seed), ctypes.byref(loss)))
+        return loss.value
 
     def counters(self):
         a, b = _i64(), _i64()
