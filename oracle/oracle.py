@@ -81,6 +81,7 @@ def lib():
         L.orc_sample_exact.restype = _i64
         L.orc_G_brute.argtypes = [_dp, _dbl, _int, _ip]
         L.orc_G_brute.restype = _dbl
+        L.orc_langevin_gauss.argtypes = [_u64, _u64, _i64, _dp]
         _lib = L
     return _lib
 
@@ -170,6 +171,26 @@ def sample_exact(L, alpha, M, P, seed, step, mmax=(0, 0, 0)):
     out = np.empty((P, 3), np.int32)
     lib().orc_sample_exact(_d(L), alpha, M, _i(mmax), P, seed, step, out)
     return out
+
+
+def langevin_gauss(seed, step, n):
+    """[n][3] standard normal numbers of the thermostat for step `step` (Philox4x64-10, Box-Muller)."""
+    g = np.empty((int(n), 3))
+    lib().orc_langevin_gauss(int(seed), int(step), int(n), g)
+    return g
+
+
+KB = 0.0083144626      # kJ mol^-1 K^-1
+
+
+def langevin_o(v, mass, gamma, T, dt, seed, step):
+    """Exact Ornstein-Uhlenbeck solution of the friction and noise terms of Eq. 39 over dt, with
+    gamma read as a collision rate (1/ps): v <- e^{-gamma dt} v + sqrt((1 - e^{-2 gamma dt}) kB T / m) g."""
+    if gamma <= 0.0:
+        return v
+    c1 = math.exp(-gamma * dt)
+    sig = np.sqrt((1.0 - c1 * c1) * KB * T / np.asarray(mass, float))
+    return c1 * v + sig[:, None] * langevin_gauss(seed, step, v.shape[0])
 
 
 def philox4x64(ctr, key):
@@ -342,10 +363,12 @@ class System:
         s2.r = np.ascontiguousarray(r, dtype=np.float64)
         return s2
 
-    def md_step(self, r, v, F, m, c):
-        """One velocity-Verlet step (the integrator of Algorithm 1's last line): half kick with F,
-        drift, new SRBE forces at the new positions with the step's mode list (m, c), half kick.
-        Electrode sites stay fixed; ions wrap in x and y.  Returns (r, v, evaluation)."""
+    def md_step(self, r, v, F, m, c, thermostat=None, step=0):
+        """One step of Algorithm 1's integrator: half kick with F, drift, new SRBE forces at the new
+        positions with the step's mode list (m, c), half kick (velocity Verlet); then, with
+        thermostat = (gamma, T, seed), the Langevin friction and noise of Eq. 39 over the whole step
+        (langevin_o with the noise of step `step`).  Electrode sites stay fixed; ions wrap in x and y.
+        Returns (r, v, evaluation)."""
         s = self.slab
         dt = s.dt
         v = v + 0.5 * dt * F / s.mass[:, None]
@@ -354,4 +377,7 @@ class System:
         r[:, 1] %= s.box[1]
         ev = evaluate(self.at(r), self.factor, m, c)
         v = v + 0.5 * dt * ev["F"] / s.mass[:, None]
+        if thermostat is not None:
+            gamma, T, seed = thermostat
+            v = langevin_o(v, s.mass, gamma, T, dt, seed, step)
         return r, v, ev

@@ -511,3 +511,25 @@ double orc_G_brute(const double L[3], double alpha, int M, const int32_t mmax[3]
       }
   return nval(&g);
 }
+
+/* ---------------------------------------------------------------------------
+ * Langevin thermostat noise (Eq. 39: the Wiener increments dW_i of every ion).
+ * Three independent standard normal numbers per ion i and step n: Philox4x64-10
+ * with key (seed, 0x4C414E47) and counter (n, i, 0, 0) gives four 64-bit words
+ * w0..w3; uniforms u_a = ((w_a >> 11) + 1/2) 2^-53 lie strictly inside (0, 1);
+ * Box-Muller: g_x = sqrt(-2 ln u0) cos(2 pi u1), g_y = sqrt(-2 ln u0) sin(2 pi u1),
+ * g_z = sqrt(-2 ln u2) cos(2 pi u3).  g is [n][3].
+ * ------------------------------------------------------------------------- */
+void orc_langevin_gauss(uint64_t seed, uint64_t step, int64_t n, double *g) {
+  const uint64_t key[2] = {seed, 0x4C414E47ull};
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t ctr[4] = {step, (uint64_t)i, 0, 0}, w[4];
+    orc_philox4x64(ctr, key, w);
+    double u[4];
+    for (int a = 0; a < 4; ++a) u[a] = ((double)(w[a] >> 11) + 0.5) * 0x1.0p-53;
+    const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
+    g[3 * i + 0] = r0 * cos(2.0 * M_PI * u[1]);
+    g[3 * i + 1] = r0 * sin(2.0 * M_PI * u[1]);
+    g[3 * i + 2] = r1 * cos(2.0 * M_PI * u[3]);
+  }
+}
