@@ -13,6 +13,12 @@ L2 is flushed (a 256 MB write) between timed steps; each step is timed with CUDA
 library's stream and the per-phase device times come from the library's own event tracing.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload batch64 [--replicas R] [--steps K] [--warmup W]
+
+The second form measures the batching form instead: R uneven replicas (default 64; 8k-57k
+particles, 1,536-6,144 electrode sites, 0-4 V, Lz/Lx 3-8, P 100-400, each with its own seed)
+stepped as one CUDA-graph launch per batch step, against the same replicas stepped one after
+another with the plain FP64 path.
 """
 from __future__ import annotations
 
@@ -113,12 +119,13 @@ def pair_counts(slab, r):
     from scipy.spatial import cKDTree
     Lx, Ly, _ = slab.box
     big = 1e4
+    def wrap(a, L):
+        a = np.mod(a, L)
+        return np.where(a >= L, a - L, a)      # mod of a tiny negative number can round to L
     rr = np.array(r, float)
-    rr[:, 0] %= Lx
-    rr[:, 1] %= Ly
+    rr[:, 0], rr[:, 1] = wrap(rr[:, 0], Lx), wrap(rr[:, 1], Ly)
     R = np.array(slab.R, float)
-    R[:, 0] %= Lx
-    R[:, 1] %= Ly
+    R[:, 0], R[:, 1] = wrap(R[:, 0], Lx), wrap(R[:, 1], Ly)
     zoff = 1e3      # keep z inside the non-wrapping box
     t = cKDTree(np.c_[rr[:, :2], rr[:, 2] + zoff], boxsize=[Lx, Ly, big])
     te = cKDTree(np.c_[R[:, :2], R[:, 2] + zoff], boxsize=[Lx, Ly, big])
@@ -207,10 +214,13 @@ def gpu_arm(args, rank, world):
     rms_q = float(np.sqrt(((Q32 - Q64) ** 2).mean() / (Q64 ** 2).mean()))
     head = "mixed" if rms_f <= 1e-3 else "fp64"
 
-    def timed(ctx, steps, warm):
+    def timed(ctx, steps, warm, traced=False):
+        """Device time of `steps` MD steps, each bracketed by CUDA events on the context's stream,
+        with an L2 flush between steps.  Untraced, srbe_step replays its captured CUDA graph;
+        traced, the ordinary launch path records an event pair around every phase."""
+        ctx.set_profiling(traced)
         ctx.step(warm, SEED)
         torch.cuda.synchronize()
-        ctx.set_profiling(True)
         l0, _ = ctx.counters()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if world > 1:
@@ -227,17 +237,21 @@ def gpu_arm(args, rank, world):
             torch.distributed.barrier()
         l1, _ = ctx.counters()
         ms = sum(a.elapsed_time(b) for a, b in ev)
-        phases = ctx.phase_times()
+        phases = ctx.phase_times() if traced else None
         ctx.set_profiling(False)
         return ms, phases, l1 - l0
 
     clocks = ClockSampler(local)
     clocks.start()
-    ms_head, ph_head, launches = timed(ctxs[head], args.steps, args.warmup)
+    ms_head, _, launches = timed(ctxs[head], args.steps, args.warmup)
     clk = clocks.stop()
+    graph_state = ctxs[head].graph_state()
+    # phase split of the same form: a traced pass (ordinary launches, event pair per phase) right after
+    n_trace = max(3, min(args.steps, 200))
+    ms_trace, ph_head, _ = timed(ctxs[head], n_trace, 3, traced=True)
     other = "fp64" if head == "mixed" else "mixed"
     n_other = max(3, min(args.steps, 50))
-    ms_other, ph_other, _ = timed(ctxs[other], n_other, max(3, min(args.warmup, 5)))
+    ms_other, ph_other, _ = timed(ctxs[other], n_other, max(3, min(args.warmup, 5)), traced=True)
 
     if world > 1:
         t = torch.tensor([ms_head], device="cuda", dtype=torch.float64)
@@ -246,7 +260,7 @@ def gpu_arm(args, rank, world):
     value = world * args.steps / (ms_head * 1e-3)
 
     # dominant phase and its roofline
-    per_step = {p: v[0] / args.steps for p, v in ph_head.items() if v[1]}
+    per_step = {p: v[0] / n_trace for p, v in ph_head.items() if v[1]}
     dom = max((p for p in per_step if p not in ("upload",)), key=lambda p: per_step[p])
     r_end = ctxs[head].get_positions()
     n_ii, n_ie = pair_counts(slab, r_end)
@@ -276,6 +290,11 @@ def gpu_arm(args, rank, world):
         "accuracy": {"rms_force_err_vs_fp64_gpu": rms_f, "rms_charge_err_vs_fp64_gpu": rms_q},
         "roofline": roof,
         "phases_ms_per_step": {p: round(v, 5) for p, v in per_step.items()},
+        "launch": {"timed_steps": "CUDA-graph replay, one graph launch per step" if graph_state[0] == 1
+                   else "ordinary launches", "kernels_per_step": graph_state[1] or None,
+                   "traced_pass": {"steps": n_trace, "steps_per_s": n_trace / (ms_trace * 1e-3),
+                                   "what": "ordinary launches with an event pair per phase; source of the "
+                                           "phase split and of the roofline's kernel duration"}},
         "other_form": {"form": other, "steps_per_s": n_other / (ms_other * 1e-3),
                        "phases_ms_per_step": {p: round(v[0] / n_other, 5) for p, v in ph_other.items() if v[1]}},
         "pairs_within_rc": {"ion_ion": n_ii, "ion_electrode": n_ie},
@@ -315,6 +334,90 @@ def e2e_arm(ctx, slab, stream, flush, steps):
     return {"value": steps / tot, "unit": UNIT, "h2d_bytes_per_step": int(rn.nbytes + qn.nbytes),
             "d2h_bytes_per_step": int(Fn.nbytes + Qn.nbytes),
             "what": "host-pointer force provider: srbe_set_positions + srbe_sample_k + srbe_forces per step"}
+
+
+# ---------------------------------------------------------------------------------------------- batching form
+def batch_arm(args):
+    """R uneven replicas: the mixed-precision batch (one graph launch per batch step, autotuned
+    stream width) against the plain FP64 path stepping the same replicas one by one.  The state of
+    the batch (22 GB of electrode matrices at R = 64) is far larger than L2, so no flush is needed."""
+    import torch
+    from paper_2509_24742_gb300 import srbe, workloads
+    torch.cuda.set_device(0)
+    t_setup = time.time()
+    slabs = workloads.batch_replicas(args.replicas)
+    seeds = np.arange(1, args.replicas + 1, dtype=np.uint64) * 7919
+    ctxs = []
+    for s in slabs:
+        c = srbe.from_slab(s, precision=srbe.MIXED, md=True)
+        c.minimize(50)
+        ctxs.append(c)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t_setup
+    n_part = np.array([s.n_ion + s.n_ele for s in slabs])
+    b = srbe.Batch(ctxs)
+    tune = b.autotune(3, seeds)
+    width = b.width()
+    bs = torch.cuda.ExternalStream(b.stream())
+
+    def run_batch(steps):
+        b.step(args.warmup, seeds)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(bs)
+        b.step(steps, seeds)
+        e1.record(bs)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_b = run_batch(args.steps)
+    clk = clocks.stop()
+    res = b.step(1, seeds, residuals=True)
+    launches = sum(c.counters()[0] for c in ctxs)
+
+    # the same replicas one after another, plain FP64 path (srbe_step, its own step graph)
+    for c in ctxs:
+        c.set_precision(srbe.FP64)
+    n_plain = max(3, min(args.steps, 20))
+    for c, sd in zip(ctxs, seeds):
+        c.step(3, int(sd))
+    torch.cuda.synchronize()
+    ms_p = 0.0
+    for c, sd in zip(ctxs, seeds):
+        t0 = time.perf_counter()
+        c.step(n_plain, int(sd))
+        torch.cuda.synchronize()
+        ms_p += (time.perf_counter() - t0) * 1e3
+    res_p = [c.charge_residual() for c in ctxs]
+    b.close()
+    for c in ctxs:
+        c.close()
+    R = args.replicas
+    value = R * args.steps / (ms_b * 1e-3)
+    plain = R * n_plain / (ms_p * 1e-3)
+    return {
+        "metric": "SRBE MD replica-steps/s on 1 GB300, batching form", "value": value, "unit": "replica-steps/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_batch_step": ms_b / args.steps,
+        "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+        "particle_steps_per_s": float(n_part.sum()) * args.steps / (ms_b * 1e-3),
+        "config": {"workload": "batch%d: %d replicas, %d-%d particles (total %d), %d-%d electrode sites, "
+                               "0-4 V, P 100-400, own seed each" % (R, R, n_part.min(), n_part.max(), n_part.sum(),
+                                                                    min(s.n_ele for s in slabs),
+                                                                    max(s.n_ele for s in slabs)),
+                   "l2": "state larger than L2 (electrode matrices %.1f GB)" %
+                         (sum(s.n_ele ** 2 * 24 for s in slabs) / 1e9)},
+        "launch": {"graph_launches_per_batch_step": 1, "stream_width": width,
+                   "autotune_ms_per_batch_step": {str(k): round(v, 4) for k, v in tune.items()}},
+        "fp64_charge_residual": {"batch_mixed_max": float(np.max(res)), "batch_mixed_median": float(np.median(res)),
+                                 "plain_fp64_max": float(np.max(res_p))},
+        "plain_fp64_one_by_one": {"value": plain, "unit": "replica-steps/s", "steps_per_replica": n_plain,
+                                  "what": "srbe_step per replica in turn, FP64, host-timed with a device sync "
+                                          "after each replica"},
+        "speedup_vs_plain_fp64": value / plain,
+        "gpu_launches": launches, "setup_s": t_setup, "clocks": clk,
+    }
 
 
 # ---------------------------------------------------------------------------------------------- CPU oracle
@@ -365,6 +468,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="md11072", choices=["md11072", "batch64"])
+    ap.add_argument("--replicas", type=int, default=64)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -374,6 +479,9 @@ def main():
         out = reference_arm(args, rank, world)
         if out is not None:
             print(json.dumps(out))
+        return
+    if args.workload == "batch64":
+        print(json.dumps(batch_arm(args)))
         return
     if world > 1:
         import torch

@@ -167,6 +167,19 @@ int srbe_get_counters(const srbe_ctx *ctx, int64_t *kernel_launches, int64_t *mo
  * (ms) and the number of timed intervals since tracing was switched on (arrays of 9; either
  * may be NULL).  Switching tracing on resets the sums. */
 int srbe_set_profiling(srbe_ctx *ctx, int on);
+
+/* CUDA graphs for srbe_step (no counterpart in the paper; launch-overhead removal).  With graphs on
+ * (the default) and tracing off, srbe_step runs its first step after any state change the ordinary
+ * way, then captures the device half of a step (mode-list copy from one of two pinned host slots,
+ * kick/drift, the full force pass, kick) into one graph per slot and replays it; the host samples
+ * the next step's modes into the other slot while the GPU runs.  Results are bitwise those of the
+ * ordinary path.  Every call other than srbe_step and the get/stat queries drops the graphs (they
+ * are captured again on the next srbe_step).  If capture fails the context keeps stepping the
+ * ordinary way until srbe_set_graphs is called again.  srbe_graph_state reports captured = 1
+ * (graphs live), 0 (none yet) or -1 (capture failed) and the kernels one replay runs; either
+ * pointer may be NULL. */
+int srbe_set_graphs(srbe_ctx *ctx, int on);
+int srbe_graph_state(srbe_ctx *ctx, int *captured, int64_t *kernels_per_step);
 int srbe_get_phase_times(srbe_ctx *ctx, double *ms, int64_t *count);
 
 /* ---- iterative charge solve and the learned warm start ------------------------------------------
@@ -202,6 +215,56 @@ int srbe_mlp_gradients(srbe_ctx *ctx, const float *D, const float *target, int64
  * weight decay); returns the mean loss of the last epoch. */
 int srbe_mlp_train(srbe_ctx *ctx, const float *D, const float *target, int64_t n, int epochs, int batch, float lr,
                    float weight_decay, uint64_t seed, double *final_loss);
+
+/* ---- checks, tuning and the batching form (no counterpart in the paper) ---------------------------
+ * srbe_charge_residual: relative FP64 residual of the constant-potential conditions met by the
+ * charges of the last pass, ||A Q - dpsi d - b - psi_bar e|| / ||dpsi d + b|| (A Q = dpsi d + b +
+ * psi_bar e follows from Eqs. 9-10), with A in FP64 whatever the precision of the solve.
+ * srbe_set_skin / srbe_get_skin: Verlet-list skin (nm, default 0.1); lists hold pairs within rc +
+ * skin and are rebuilt on the device once an ion has moved more than skin / 2.  Results do not
+ * depend on the skin beyond summation order.
+ * srbe_autotune_skin: times trial_steps MD steps (after two untimed ones) for each candidate skin,
+ * restores positions, velocities, forces, charges and the step counter after each trial, keeps the
+ * fastest skin and writes the per-candidate ms per step to ms_per_step (n_skins entries, or NULL). */
+int srbe_charge_residual(srbe_ctx *ctx, double *rel_residual);
+int srbe_set_skin(srbe_ctx *ctx, double skin);
+double srbe_get_skin(const srbe_ctx *ctx);
+int srbe_autotune_skin(srbe_ctx *ctx, int trial_steps, uint64_t seed, const double *skins, int n_skins,
+                       double *ms_per_step);
+
+/* A batch steps many independent replicas (contexts of any size, electrode, voltage, precision,
+ * solver and mode count, each with its own seed and so its own k-sample lists) as one unit: each
+ * batch step is ONE CUDA graph launch that runs Algorithm 1's step for every replica, the replicas
+ * spread over `width` streams inside the graph so that small systems overlap on the GPU.  The host
+ * samples every replica's next mode list (over a few host threads) into pinned slots while the GPU
+ * runs the current step.  A replica's trajectory is bitwise the one srbe_step gives it with the same
+ * seed.  Cooperative kernels of different replicas are ordered one after another inside the graph
+ * (two overlapping grid-wide barriers could starve each other of SMs).
+ *   srbe_batch_create: ctxs are borrowed (the caller keeps and destroys them, after the batch);
+ *     all on the current device, distinct; default width min(n, 16).
+ *   srbe_batch_step: nsteps steps, seeds[n] (replica r's modes of step t come from (seeds[r], t)).
+ *     The first step after creation, a width change or any state-changing call on a replica runs
+ *     the ordinary way and recaptures.  residuals (n entries, or NULL) receives each replica's
+ *     srbe_charge_residual after the last step: the FP64 check of the FP32 bulk of mixed replicas.
+ *     The call returns once the work is queued; each replica's own stream is ordered after it.
+ *   srbe_batch_set_width: streams inside the graph (0: one stream, replicas in order).
+ *   srbe_batch_autotune: for each candidate width, times trial_steps batch steps (after two
+ *     untimed ones), restores every replica's state (as srbe_autotune_skin does) and keeps the
+ *     fastest width; ms_per_step (n_widths entries, or NULL) receives the timings.
+ * Errors: SRBE_EINVAL (bad arguments), SRBE_ESTATE (a replica without electrode, positions or MD
+ * state, or with phase tracing on), SRBE_ECUDA (capture or launch failed), SRBE_ENOMEM;
+ * srbe_batch_last_error gives the message. */
+typedef struct srbe_batch srbe_batch;
+int srbe_batch_create(int n, srbe_ctx *const *ctxs, srbe_batch **out);
+int srbe_batch_destroy(srbe_batch *batch);
+const char *srbe_batch_last_error(const srbe_batch *batch);
+int srbe_batch_set_width(srbe_batch *batch, int width);
+int srbe_batch_get_width(const srbe_batch *batch);
+/* the batch's own stream (cudaStream_t as void*), on which every batch step is launched */
+void *srbe_batch_stream(const srbe_batch *batch);
+int srbe_batch_step(srbe_batch *batch, int nsteps, const uint64_t *seeds, double *residuals);
+int srbe_batch_autotune(srbe_batch *batch, int trial_steps, const uint64_t *seeds, const int *widths, int n_widths,
+                        double *ms_per_step);
 
 /* Structure factor without any device allocation (no counterpart in the paper; an interface
  * for callers that cannot allocate device memory, e.g. an MD engine that hands out every byte of

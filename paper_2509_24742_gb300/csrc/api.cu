@@ -3,7 +3,11 @@
 // host arrays, and the order of the device passes of Algorithm 1.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
+#include <chrono>
+#include <mutex>
 #include <new>
+#include <thread>
 
 #include "srbe_internal.cuh"
 
@@ -190,11 +194,17 @@ int fail(srbe_ctx *c, const Error &e) {
   return e.code;
 }
 
+// Every call that may change the state a captured step reads (buffers, sizes, settings) drops the
+// step's CUDA graphs; srbe_step and the read-only queries keep them.
 template <class Fn>
-int guarded(srbe_ctx *c, Fn &&fn) {
+int guarded(srbe_ctx *c, Fn &&fn, bool keeps_graph = false) {
   if (!c) return SRBE_EINVAL;
   try {
     c->err.clear();
+    if (!keeps_graph && c->hx) {
+      c->hx->graph_dirty = true;
+      c->hx->epoch++;
+    }
     fn();
     return SRBE_OK;
   } catch (const Error &e) {
@@ -267,6 +277,28 @@ struct srbe::HostExt {
   ModeSampler sampler;
   DevBuf<double> aos;      // AoS staging for positions / forces
   bool forces_valid = false;
+  // CUDA graphs of one MD step, one per pinned staging slot of the mode list (ping-pong)
+  struct Slot {
+    int4 *hm = nullptr;
+    double *hw = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+  } slot[2];
+  cudaStream_t cap = nullptr;   // capture stream (a legacy default stream cannot be captured)
+  int graph_K = -1;
+  int slot_cap = 0;
+  bool graph_dirty = true;
+  bool graph_failed = false;
+  uint64_t epoch = 0;           // counts calls that may change what a captured step reads
+  int64_t graph_kernels = 0;
+  void drop_graphs() {
+    for (auto &sl : slot)
+      if (sl.exec) {
+        cudaGraphExecDestroy(sl.exec);
+        sl.exec = nullptr;
+      }
+    graph_dirty = true;
+  }
   // phase tracing: a pool of event pairs, drained into per-phase sums when full or on request
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_phase;
@@ -276,6 +308,13 @@ struct srbe::HostExt {
   int64_t count[kPhCount];
   ~HostExt() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    drop_graphs();
+    if (cap) cudaStreamDestroy(cap);
+    for (auto &sl : slot) {
+      if (sl.hm) cudaFreeHost(sl.hm);
+      if (sl.hw) cudaFreeHost(sl.hw);
+      if (sl.done) cudaEventDestroy(sl.done);
+    }
   }
 };
 
@@ -318,6 +357,27 @@ void phase_end(srbe_ctx *c, int ph) {
   if (!c->profiling) return;
   Extra *e = extra(c);
   SRBE_CUDA(cudaEventRecord(e->ev[2 * e->open_phase[ph] + 1], c->stream));
+}
+
+// A cooperative kernel is only guaranteed to make progress when all its blocks can be resident at
+// once; two of them overlapping on one GPU could each hold part of the SMs while waiting for the
+// rest.  All cooperative launches (and graph launches that contain them) of the process on one
+// device are therefore ordered through one event per device.
+cudaEvent_t device_coop_chain() {
+  static std::mutex mu;
+  static std::vector<cudaEvent_t> ev;
+  int dev = 0;
+  SRBE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)ev.size() <= dev) ev.resize(dev + 1, nullptr);
+  if (!ev[dev]) SRBE_CUDA(cudaEventCreateWithFlags(&ev[dev], cudaEventDisableTiming));
+  return ev[dev];
+}
+void coop_before(srbe_ctx *c) {
+  SRBE_CUDA(cudaStreamWaitEvent(c->stream, c->coop_chain ? c->coop_chain : device_coop_chain(), 0));
+}
+void coop_after(srbe_ctx *c) {
+  SRBE_CUDA(cudaEventRecord(c->coop_chain ? c->coop_chain : device_coop_chain(), c->stream));
 }
 }  // namespace srbe
 
@@ -423,7 +483,7 @@ void upload_modes(srbe_ctx *c) {
 
 // SRBE mode list (Eqs. 24-25): I folded to +m_z with twice the Ewald weight, then the samples with
 // (G / P) 4 pi / (V k^2)
-void srbe_list_from_samples(srbe_ctx *c, const int32_t *samp, int P) {
+void srbe_host_list(srbe_ctx *c, const int32_t *samp, int P) {
   c->hm.clear();
   c->hc.clear();
   const double V = c->V;
@@ -446,7 +506,141 @@ void srbe_list_from_samples(srbe_ctx *c, const int32_t *samp, int P) {
   }
   c->hsamp.assign(samp, samp + 3 * P);
   c->explicit_list = false;
+}
+
+void srbe_list_from_samples(srbe_ctx *c, const int32_t *samp, int P) {
+  srbe_host_list(c, samp, P);
   upload_modes(c);
+}
+
+// ---- CUDA graph of one MD step ------------------------------------------------------------------
+// The device half of a step (mode-list copy from a pinned slot, kick/drift, the force pass, kick) has
+// no host synchronisation and no allocation once the buffers are reserved, so it is captured once
+// per slot and replayed; the host fills the other slot while the GPU runs.
+void forces_pass(srbe_ctx *c, bool energies);
+
+void device_step(srbe_ctx *c, int slot) {
+  Extra *e = extra(c);
+  const int K = c->K;
+  if (K > 0) {
+    SRBE_CUDA(cudaMemcpyAsync(c->dm.p, e->slot[slot].hm, sizeof(int4) * K, cudaMemcpyHostToDevice, c->stream));
+    SRBE_CUDA(cudaMemcpyAsync(c->dc.p, e->slot[slot].hw, sizeof(double) * K, cudaMemcpyHostToDevice, c->stream));
+  }
+  integrate_kick_drift(c, 0.5 * c->dt, true);
+  forces_pass(c, false);
+  integrate_kick_drift(c, 0.5 * c->dt, false);
+}
+
+void ensure_slot_buffers(srbe_ctx *c) {
+  Extra *e = extra(c);
+  SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  if (e->slot_cap < c->K) {
+    for (auto &sl : e->slot) {
+      if (sl.hm) cudaFreeHost(sl.hm);
+      if (sl.hw) cudaFreeHost(sl.hw);
+      sl.hm = nullptr;
+      sl.hw = nullptr;
+    }
+    e->slot_cap = 0;
+  }
+  for (auto &sl : e->slot) {
+    if (!sl.hm) SRBE_CUDA(cudaMallocHost((void **)&sl.hm, sizeof(int4) * std::max(c->K, 1)));
+    if (!sl.hw) SRBE_CUDA(cudaMallocHost((void **)&sl.hw, sizeof(double) * std::max(c->K, 1)));
+    if (!sl.done) {
+      SRBE_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+      SRBE_CUDA(cudaEventRecord(sl.done, c->stream));
+    }
+  }
+  e->slot_cap = std::max(e->slot_cap, std::max(c->K, 1));
+}
+
+void copy_to_slot(srbe_ctx *c, int slot) {
+  Extra *e = extra(c);
+  SRBE_REQUIRE((int)c->hc.size() == c->K && c->K <= e->slot_cap, SRBE_ESTATE, "mode count changed under a graph");
+  for (int k = 0; k < c->K; ++k) {
+    e->slot[slot].hm[k] = make_int4(c->hm[4 * k], c->hm[4 * k + 1], c->hm[4 * k + 2], 0);
+    e->slot[slot].hw[k] = c->hc[k];
+  }
+}
+
+void fill_slot(srbe_ctx *c, int slot) {
+  SRBE_CUDA(cudaEventSynchronize(extra(c)->slot[slot].done));
+  copy_to_slot(c, slot);
+}
+
+// Captures device_step of every context in ctxs into one executable graph per slot.  With width 0
+// all run in order on the capture stream; otherwise context r runs on forks[r % width], forked from
+// and joined back into the capture stream, so that up to width replicas overlap on the GPU.  The
+// cooperative kernels of all of them are chained through one capture-local event, so no two of them
+// ever run at the same time.  kernels[r] receives the kernels one replay runs for context r.
+// Returns false (and leaves nothing captured) when capture is not possible.
+bool capture_graphs(srbe_ctx *const *ctxs, int n, cudaStream_t main, int width, const cudaStream_t *forks,
+                    cudaGraphExec_t out[2], int64_t *kernels) {
+  std::vector<int64_t> launches0(n);
+  for (int r = 0; r < n; ++r) launches0[r] = ctxs[r]->launches;
+  std::vector<cudaStream_t> saved(n);
+  for (int r = 0; r < n; ++r) saved[r] = ctxs[r]->stream;
+  cudaEvent_t fork_ev = nullptr, chain = nullptr;
+  std::vector<cudaEvent_t> join(n, nullptr);
+  auto release = [&] {
+    for (int r = 0; r < n; ++r) {
+      ctxs[r]->stream = saved[r];
+      ctxs[r]->coop_chain = nullptr;
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (chain) cudaEventDestroy(chain);
+    for (auto &j : join)
+      if (j) cudaEventDestroy(j);
+  };
+  bool ok = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&chain, cudaEventDisableTiming) == cudaSuccess;
+  for (auto &j : join) ok = ok && cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess;
+  out[0] = out[1] = nullptr;
+  for (int slot = 0; slot < 2 && ok; ++slot) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    try {
+      SRBE_CUDA(cudaEventRecord(chain, main));
+      SRBE_CUDA(cudaEventRecord(fork_ev, main));
+      for (int r = 0; r < n; ++r) {
+        srbe_ctx *c = ctxs[r];
+        c->coop_chain = chain;
+        if (width > 0) {
+          c->stream = forks[r % width];
+          SRBE_CUDA(cudaStreamWaitEvent(c->stream, fork_ev, 0));
+        } else {
+          c->stream = main;
+        }
+        const int64_t l0 = c->launches;
+        device_step(c, slot);
+        kernels[r] = c->launches - l0;
+        if (width > 0) {
+          SRBE_CUDA(cudaEventRecord(join[r], c->stream));
+          SRBE_CUDA(cudaStreamWaitEvent(main, join[r], 0));
+        }
+        c->stream = saved[r];
+        c->coop_chain = nullptr;
+      }
+    } catch (const Error &) {
+      ok = false;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(main, &g);
+    if (!ok || ec != cudaSuccess || !g || cudaGraphInstantiate(&out[slot], g, 0) != cudaSuccess) ok = false;
+    if (g) cudaGraphDestroy(g);
+  }
+  release();
+  // capturing launches nothing
+  for (int r = 0; r < n; ++r) ctxs[r]->launches = launches0[r];
+  if (!ok) {
+    cudaGetLastError();
+    for (int k = 0; k < 2; ++k)
+      if (out[k]) cudaGraphExecDestroy(out[k]);
+    out[0] = out[1] = nullptr;
+  }
+  return ok;
 }
 
 void require_state(srbe_ctx *c, bool pos) {
@@ -486,13 +680,42 @@ void forces_pass(srbe_ctx *c, bool energies) {
   }
 }
 
-void sample_into(srbe_ctx *c, uint64_t seed, uint64_t step) {
+// host half of a step's mode list: samples (Eqs. 26-29) and weights (Eqs. 24-25) into c->hm / c->hc
+void build_host_list(srbe_ctx *c, uint64_t seed, uint64_t step) {
   Extra *e = extra(c);
-  std::vector<int32_t> s((size_t)3 * c->P);
-  if (c->sampler == SRBE_SAMPLER_EXACT) e->sampler.exact(seed, step, c->P, s.data());
-  else e->sampler.metropolis(seed, step, c->P, s.data());
-  srbe_list_from_samples(c, s.data(), c->P);
+  std::vector<int32_t> smp((size_t)3 * c->P);
+  if (c->sampler == SRBE_SAMPLER_EXACT) e->sampler.exact(seed, step, c->P, smp.data());
+  else e->sampler.metropolis(seed, step, c->P, smp.data());
+  srbe_host_list(c, smp.data(), c->P);
 }
+
+void sample_into(srbe_ctx *c, uint64_t seed, uint64_t step) {
+  build_host_list(c, seed, step);
+  upload_modes(c);
+}
+
+// forces at the starting positions (modes of step md_step), once after any change of the state
+void initial_forces(srbe_ctx *c, uint64_t seed0) {
+  Extra *e = extra(c);
+  if (e->forces_valid) return;
+  sample_into(c, seed0, c->md_step);
+  forces_pass(c, false);
+  e->forces_valid = true;
+}
+
+// one velocity-Verlet step of Algorithm 1 through ordinary launches
+void eager_step(srbe_ctx *c, uint64_t seed0) {
+  c->md_step++;
+  sample_into(c, seed0, c->md_step);
+  phase_begin(c, kPhIntegrate);
+  integrate_kick_drift(c, 0.5 * c->dt, true);
+  phase_end(c, kPhIntegrate);
+  forces_pass(c, false);
+  phase_begin(c, kPhIntegrate);
+  integrate_kick_drift(c, 0.5 * c->dt, false);
+  phase_end(c, kPhIntegrate);
+}
+
 
 void download_outputs(srbe_ctx *c, double *F, double *Q, double *psi, double *energy, double *b) {
   Extra *e = extra(c);
@@ -753,7 +976,7 @@ int srbe_get_positions(srbe_ctx *c, double *r, double *v) {
       SRBE_CUDA(cudaMemcpyAsync(v, aos, sizeof(double) * 3 * c->ni, cudaMemcpyDeviceToHost, c->stream));
       SRBE_CUDA(cudaStreamSynchronize(c->stream));
     }
-  });
+  }, true);
 }
 
 int srbe_set_md(srbe_ctx *c, const double *mass, const double *v, int ntype, const int32_t *itype,
@@ -861,7 +1084,7 @@ int srbe_get_k(const srbe_ctx *cc, int32_t *m, double *G) {
     SRBE_REQUIRE(c->have_modes && !c->explicit_list, SRBE_ESTATE, "no sampled mode list");
     if (m) std::memcpy(m, c->hsamp.data(), sizeof(int32_t) * c->hsamp.size());
     if (G) *G = c->G;
-  });
+  }, true);
 }
 
 int srbe_set_k(srbe_ctx *c, const int32_t *m, int P) {
@@ -927,25 +1150,60 @@ int srbe_step(srbe_ctx *c, int nsteps, uint64_t seed0) {
     SRBE_REQUIRE(c->have_ele && c->have_pos, SRBE_ESTATE, "electrode and positions are required");
     SRBE_REQUIRE(c->have_md, SRBE_ESTATE, "srbe_set_md has not been called");
     Extra *e = extra(c);
-    if (!e->forces_valid) {
-      // forces at the starting positions use the modes of step md_step
-      sample_into(c, seed0, c->md_step);
-      forces_pass(c, false);
-      e->forces_valid = true;
+    initial_forces(c, seed0);
+    const bool graphs = !c->profiling && c->use_graphs && !e->graph_failed && nsteps > 0;
+    if (graphs && (e->graph_dirty || e->graph_K != c->K)) {
+      // one step the ordinary way sizes every buffer the step touches, then the step is captured
+      eager_step(c, seed0);
+      --nsteps;
+      e->drop_graphs();
+      reserve(c);
+      ensure_slot_buffers(c);
+      cudaGraphExec_t ex[2] = {nullptr, nullptr};
+      srbe_ctx *one[1] = {c};
+      if (!e->cap) SRBE_CUDA(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
+      if (capture_graphs(one, 1, e->cap, 0, nullptr, ex, &e->graph_kernels)) {
+        e->slot[0].exec = ex[0];
+        e->slot[1].exec = ex[1];
+        e->graph_dirty = false;
+        e->graph_K = c->K;
+      } else {
+        e->graph_failed = true;
+      }
     }
-    for (int s = 0; s < nsteps; ++s) {
-      c->md_step++;
-      sample_into(c, seed0, c->md_step);
-      phase_begin(c, kPhIntegrate);
-      integrate_kick_drift(c, 0.5 * c->dt, true);
-      phase_end(c, kPhIntegrate);
-      forces_pass(c, false);
-      phase_begin(c, kPhIntegrate);
-      integrate_kick_drift(c, 0.5 * c->dt, false);
-      phase_end(c, kPhIntegrate);
+    if (graphs && !e->graph_failed) {
+      for (int s = 0; s < nsteps; ++s) {
+        c->md_step++;
+        const int slot = (int)(c->md_step & 1);
+        build_host_list(c, seed0, c->md_step);
+        fill_slot(c, slot);
+        coop_before(c);
+        SRBE_CUDA(cudaGraphLaunch(e->slot[slot].exec, c->stream));
+        coop_after(c);
+        SRBE_CUDA(cudaEventRecord(e->slot[slot].done, c->stream));
+        c->launches += e->graph_kernels;
+      }
+      return;
     }
+    for (int s = 0; s < nsteps; ++s) eager_step(c, seed0);
     SRBE_CUDA(cudaGetLastError());
+  }, true);
+}
+
+int srbe_set_graphs(srbe_ctx *c, int on) {
+  return guarded(c, [&] {
+    c->use_graphs = on != 0;
+    extra(c)->graph_failed = false;
   });
+}
+
+int srbe_graph_state(srbe_ctx *c, int *captured, int64_t *kernels_per_step) {
+  return guarded(c, [&] {
+    Extra *e = extra(c);
+    const bool ok = e->slot[0].exec && !e->graph_dirty && !e->graph_failed;
+    if (captured) *captured = ok ? 1 : (e->graph_failed ? -1 : 0);
+    if (kernels_per_step) *kernels_per_step = ok ? e->graph_kernels : 0;
+  }, true);
 }
 
 int srbe_set_profiling(srbe_ctx *c, int on) {
@@ -970,7 +1228,7 @@ int srbe_get_phase_times(srbe_ctx *c, double *ms, int64_t *count) {
       if (ms) ms[p] = e->ms[p];
       if (count) count[p] = e->count[p];
     }
-  });
+  }, true);
 }
 
 int srbe_minimize(srbe_ctx *c, int nsteps, double a, double dmax, uint64_t seed) {
@@ -1013,7 +1271,7 @@ int srbe_get_solver_stats(srbe_ctx *c, int *iterations, double *rel_residual) {
     SRBE_CUDA(cudaStreamSynchronize(c->stream));
     if (iterations) *iterations = it;
     if (rel_residual) *rel_residual = r;
-  });
+  }, true);
 }
 
 namespace {
@@ -1072,7 +1330,7 @@ int srbe_mlp_get_params(srbe_ctx *c, float *params, int64_t *count) {
     SRBE_CUDA(cudaMemcpyAsync(params, c->mlp.P.p, sizeof(float) * mlp_param_count(), cudaMemcpyDeviceToHost,
                               c->stream));
     SRBE_CUDA(cudaStreamSynchronize(c->stream));
-  });
+  }, true);
 }
 
 int srbe_mlp_set_params(srbe_ctx *c, const float *params, int64_t count) {
@@ -1219,6 +1477,444 @@ int srbe_get_counters(const srbe_ctx *cc, int64_t *kernel_launches, int64_t *mod
   if (kernel_launches) *kernel_launches = cc->launches;
   if (mode_evals) *mode_evals = cc->mode_evals;
   return SRBE_OK;
+}
+
+int srbe_charge_residual(srbe_ctx *c, double *rel_residual) {
+  return guarded(c, [&] {
+    require_state(c, true);
+    SRBE_REQUIRE(rel_residual, SRBE_EINVAL, "null output");
+    double *d = c->resid.ensure((size_t)2 * std::max<int64_t>(c->ne, 1) + 2) + 2 * std::max<int64_t>(c->ne, 1);
+    charge_residual(c, d);
+    double h[2];
+    SRBE_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    *rel_residual = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+  }, true);
+}
+
+int srbe_set_skin(srbe_ctx *c, double skin) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(std::isfinite(skin) && skin > 0.0 && skin <= 1.0, SRBE_EINVAL, "skin must be in (0, 1] nm");
+    c->nbr.skin = skin;
+    c->nbr.cap = 0;                    // list capacity follows the skin (recomputed by reserve)
+    if (c->have_pos) {
+      reserve(c);
+      neighbor_force_rebuild(c);
+    }
+  });
+}
+
+double srbe_get_skin(const srbe_ctx *c) { return c ? c->nbr.skin : 0.0; }
+
+}  // extern "C"
+
+// ---- replicas: snapshots and the batch ----------------------------------------------------------
+namespace {
+
+// device copy of the dynamical state of a context (positions, velocities, forces, charges, PCG
+// iterate) and its step counter; restoring it also forces a neighbour-list rebuild
+struct Snapshot {
+  DevBuf<double> buf;
+  uint64_t md_step = 0;
+  bool forces_valid = false;
+  bool pcg = false;
+};
+
+void snapshot_io(srbe_ctx *c, Snapshot &sn, bool save) {
+  const size_t n = (size_t)c->ni, ne = (size_t)c->ne;
+  if (save) sn.pcg = c->pcg.y.p != nullptr;
+  const bool pcg = sn.pcg;
+  SRBE_REQUIRE(!pcg || c->pcg.y.p, SRBE_ESTATE, "PCG state vanished under a snapshot");
+  double *b = save ? sn.buf.ensure(9 * n + ne + (pcg ? ne : 0) + 1) : sn.buf.p;
+  struct Part {
+    double *p;
+    size_t n;
+  } parts[] = {{c->x.p, n}, {c->y.p, n}, {c->z.p, n}, {c->vx.p, n}, {c->vy.p, n}, {c->vz.p, n},
+               {c->F.p, 3 * n}, {c->Q.p, ne}, {pcg ? c->pcg.y.p : nullptr, pcg ? ne : 0}};
+  size_t o = 0;
+  for (const Part &pt : parts) {
+    if (pt.p && pt.n) {
+      if (save) SRBE_CUDA(cudaMemcpyAsync(b + o, pt.p, sizeof(double) * pt.n, cudaMemcpyDeviceToDevice, c->stream));
+      else SRBE_CUDA(cudaMemcpyAsync(pt.p, b + o, sizeof(double) * pt.n, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    o += pt.n;
+  }
+  if (save) {
+    sn.md_step = c->md_step;
+    sn.forces_valid = extra(c)->forces_valid;
+  } else {
+    c->md_step = sn.md_step;
+    extra(c)->forces_valid = sn.forces_valid;
+    neighbor_force_rebuild(c);
+  }
+}
+
+}  // namespace
+
+struct srbe_batch {
+  std::vector<srbe_ctx *> ctx;
+  std::vector<uint64_t> epoch;       // state epochs of the replicas when the graphs were captured
+  std::vector<int64_t> kernels;      // kernels per replica in one replay
+  cudaStream_t main = nullptr;
+  std::vector<cudaStream_t> forks;
+  int width = 0;                     // concurrent replica streams (0: one stream, in order)
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  cudaEvent_t mark = nullptr;
+  DevBuf<double> res;                // residual sums [n][2]
+  double *h_res = nullptr;
+  uint64_t t = 0;
+  bool dirty = true;
+  int device = 0;
+  int threads = 1;
+  std::string err;
+
+  void drop() {
+    for (auto &x : exec)
+      if (x) {
+        cudaGraphExecDestroy(x);
+        x = nullptr;
+      }
+    dirty = true;
+  }
+  ~srbe_batch() {
+    if (main) cudaStreamSynchronize(main);
+    drop();
+    for (auto &f : forks) cudaStreamDestroy(f);
+    for (auto &d : done)
+      if (d) cudaEventDestroy(d);
+    if (mark) cudaEventDestroy(mark);
+    if (h_res) cudaFreeHost(h_res);
+    if (main) cudaStreamDestroy(main);
+  }
+};
+
+namespace {
+
+template <class Fn>
+int batch_guarded(srbe_batch *b, Fn &&fn) {
+  if (!b) return SRBE_EINVAL;
+  try {
+    b->err.clear();
+    SRBE_CUDA(cudaSetDevice(b->device));
+    fn();
+    return SRBE_OK;
+  } catch (const Error &e) {
+    b->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    b->err = "host allocation failed";
+    return SRBE_ENOMEM;
+  } catch (const std::exception &e) {
+    b->err = e.what();
+    return SRBE_EINVAL;
+  }
+}
+
+// runs fn(r) for every replica, spread over up to `threads` host threads
+template <class Fn>
+void for_replicas(int n, int threads, Fn &&fn) {
+  if (threads <= 1 || n < 4) {
+    for (int r = 0; r < n; ++r) fn(r);
+    return;
+  }
+  const int nt = std::min(threads, n);
+  std::vector<std::thread> pool;
+  std::vector<std::string> errs(nt);
+  std::vector<int> codes(nt, SRBE_OK);
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&, t] {
+      try {
+        for (int r = t; r < n; r += nt) fn(r);
+      } catch (const Error &e) {
+        codes[t] = e.code;
+        errs[t] = e.msg;
+      } catch (const std::exception &e) {
+        codes[t] = SRBE_EINVAL;
+        errs[t] = e.what();
+      }
+    });
+  for (auto &th : pool) th.join();
+  for (int t = 0; t < nt; ++t)
+    if (codes[t] != SRBE_OK) throw Error{codes[t], errs[t]};
+}
+
+// orders `to` after everything issued so far on `from`
+void stream_after(cudaStream_t to, cudaStream_t from, cudaEvent_t ev) {
+  SRBE_CUDA(cudaEventRecord(ev, from));
+  SRBE_CUDA(cudaStreamWaitEvent(to, ev, 0));
+}
+
+void batch_check_replicas(srbe_batch *b) {
+  for (srbe_ctx *c : b->ctx) {
+    SRBE_REQUIRE(c->have_ele && c->have_pos && c->have_md, SRBE_ESTATE,
+                 "every replica needs electrode, positions and srbe_set_md");
+    SRBE_REQUIRE(!c->profiling, SRBE_ESTATE, "switch phase tracing off on the replicas of a batch");
+  }
+}
+
+// (re)captures the batch graphs after one ordinary step of every replica
+void batch_capture(srbe_batch *b, const uint64_t *seeds) {
+  const int n = (int)b->ctx.size();
+  b->drop();
+  for (int r = 0; r < n; ++r) {
+    srbe_ctx *c = b->ctx[r];
+    stream_after(c->stream, b->main, b->mark);
+    initial_forces(c, seeds[r]);
+    eager_step(c, seeds[r]);
+    reserve(c);
+    ensure_slot_buffers(c);    // synchronises the replica's stream
+  }
+  while ((int)b->forks.size() < b->width) {
+    cudaStream_t f = nullptr;
+    SRBE_CUDA(cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking));
+    b->forks.push_back(f);
+  }
+  b->kernels.assign(n, 0);
+  SRBE_REQUIRE(capture_graphs(b->ctx.data(), n, b->main, b->width, b->forks.data(), b->exec, b->kernels.data()),
+               SRBE_ECUDA, "capture of the batch step failed");
+  b->epoch.resize(n);
+  for (int r = 0; r < n; ++r) {
+    b->epoch[r] = extra(b->ctx[r])->epoch;
+    extra(b->ctx[r])->graph_dirty = true;     // the replicas' own single-context graphs are stale now
+  }
+  b->dirty = false;
+}
+
+bool batch_stale(const srbe_batch *b) {
+  if (b->dirty || !b->exec[0]) return true;
+  for (size_t r = 0; r < b->ctx.size(); ++r) {
+    const srbe_ctx *c = b->ctx[r];
+    if (c->hx->epoch != b->epoch[r] || !c->hx->forces_valid || (int)c->hc.size() != c->K) return true;
+  }
+  return false;
+}
+
+// nsteps MD steps of every replica; the first step after a change of state runs the ordinary way
+void batch_run(srbe_batch *b, int nsteps, const uint64_t *seeds) {
+  const int n = (int)b->ctx.size();
+  if (nsteps <= 0) return;
+  for (srbe_ctx *c : b->ctx) {
+    stream_after(b->main, c->stream, b->mark);
+    // a replica's own step graph may still read its pinned slots
+    for (auto &sl : extra(c)->slot)
+      if (sl.done) SRBE_CUDA(cudaEventSynchronize(sl.done));
+  }
+  if (batch_stale(b)) {
+    batch_capture(b, seeds);
+    --nsteps;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    const int slot = (int)(b->t & 1);
+    b->t++;
+    for_replicas(n, b->threads, [&](int r) {
+      srbe_ctx *c = b->ctx[r];
+      c->md_step++;
+      build_host_list(c, seeds[r], c->md_step);
+    });
+    SRBE_CUDA(cudaEventSynchronize(b->done[slot]));
+    for (int r = 0; r < n; ++r) copy_to_slot(b->ctx[r], slot);
+    SRBE_CUDA(cudaStreamWaitEvent(b->main, device_coop_chain(), 0));
+    SRBE_CUDA(cudaGraphLaunch(b->exec[slot], b->main));
+    SRBE_CUDA(cudaEventRecord(device_coop_chain(), b->main));
+    SRBE_CUDA(cudaEventRecord(b->done[slot], b->main));
+    for (int r = 0; r < n; ++r) b->ctx[r]->launches += b->kernels[r];
+  }
+  // later work on a replica's own stream sees the batch's results, and its own step graph waits
+  // for the batch's reads of the shared pinned slots before refilling them
+  SRBE_CUDA(cudaEventRecord(b->mark, b->main));
+  for (srbe_ctx *c : b->ctx) {
+    SRBE_CUDA(cudaStreamWaitEvent(c->stream, b->mark, 0));
+    for (auto &sl : extra(c)->slot)
+      if (sl.done) SRBE_CUDA(cudaEventRecord(sl.done, b->main));
+  }
+}
+
+void batch_residuals(srbe_batch *b, double *out) {
+  const int n = (int)b->ctx.size();
+  double *d = b->res.ensure((size_t)2 * n);
+  for (int r = 0; r < n; ++r) {
+    srbe_ctx *c = b->ctx[r];
+    stream_after(b->main, c->stream, b->mark);
+    const cudaStream_t own = c->stream;
+    c->stream = b->main;
+    try {
+      charge_residual(c, d + 2 * r);
+    } catch (...) {
+      c->stream = own;
+      throw;
+    }
+    c->stream = own;
+  }
+  SRBE_CUDA(cudaMemcpyAsync(b->h_res, d, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, b->main));
+  SRBE_CUDA(cudaStreamSynchronize(b->main));
+  for (int r = 0; r < n; ++r) {
+    const double a = b->h_res[2 * r], q = b->h_res[2 * r + 1];
+    out[r] = q > 0 ? std::sqrt(a / q) : std::sqrt(a);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int srbe_batch_create(int n, srbe_ctx *const *ctxs, srbe_batch **out) {
+  if (!out) return SRBE_EINVAL;
+  *out = nullptr;
+  if (n < 1 || !ctxs) return SRBE_EINVAL;
+  for (int r = 0; r < n; ++r) {
+    if (!ctxs[r]) return SRBE_EINVAL;
+    for (int q = 0; q < r; ++q)
+      if (ctxs[q] == ctxs[r]) return SRBE_EINVAL;
+  }
+  srbe_batch *b = new (std::nothrow) srbe_batch;
+  if (!b) return SRBE_ENOMEM;
+  b->ctx.assign(ctxs, ctxs + n);
+  const int rc = batch_guarded(b, [&] {
+    SRBE_CUDA(cudaGetDevice(&b->device));
+    SRBE_CUDA(cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking));
+    for (auto &d : b->done) {
+      SRBE_CUDA(cudaEventCreateWithFlags(&d, cudaEventDisableTiming));
+      SRBE_CUDA(cudaEventRecord(d, b->main));
+    }
+    SRBE_CUDA(cudaEventCreateWithFlags(&b->mark, cudaEventDisableTiming));
+    SRBE_CUDA(cudaMallocHost((void **)&b->h_res, sizeof(double) * 2 * n));
+    b->width = std::min(n, 16);
+    const unsigned hw = std::thread::hardware_concurrency();
+    b->threads = (int)std::max(1u, std::min(8u, hw ? hw : 1u));
+  });
+  if (rc != SRBE_OK) {
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return SRBE_OK;
+}
+
+int srbe_batch_destroy(srbe_batch *b) {
+  if (!b) return SRBE_EINVAL;
+  cudaSetDevice(b->device);
+  delete b;
+  return SRBE_OK;
+}
+
+const char *srbe_batch_last_error(const srbe_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+int srbe_batch_set_width(srbe_batch *b, int width) {
+  return batch_guarded(b, [&] {
+    SRBE_REQUIRE(width >= 0, SRBE_EINVAL, "negative width");
+    b->width = std::min<int>(width, (int)b->ctx.size());
+    b->dirty = true;
+  });
+}
+
+int srbe_batch_get_width(const srbe_batch *b) { return b ? b->width : -1; }
+
+void *srbe_batch_stream(const srbe_batch *b) { return b ? (void *)b->main : nullptr; }
+
+int srbe_batch_step(srbe_batch *b, int nsteps, const uint64_t *seeds, double *residuals) {
+  return batch_guarded(b, [&] {
+    SRBE_REQUIRE(nsteps >= 0, SRBE_EINVAL, "negative step count");
+    SRBE_REQUIRE(seeds, SRBE_EINVAL, "null seed array");
+    batch_check_replicas(b);
+    batch_run(b, nsteps, seeds);
+    if (residuals) batch_residuals(b, residuals);
+  });
+}
+
+int srbe_batch_autotune(srbe_batch *b, int trial_steps, const uint64_t *seeds, const int *widths, int n_widths,
+                        double *ms_per_step) {
+  return batch_guarded(b, [&] {
+    SRBE_REQUIRE(trial_steps >= 1 && seeds && widths && n_widths >= 1, SRBE_EINVAL,
+                 "need trial_steps >= 1, seeds and candidate widths");
+    for (int i = 0; i < n_widths; ++i) SRBE_REQUIRE(widths[i] >= 0, SRBE_EINVAL, "negative width");
+    batch_check_replicas(b);
+    const int n = (int)b->ctx.size();
+    std::vector<Snapshot> snap(n);
+    for (int r = 0; r < n; ++r) {
+      SRBE_CUDA(cudaStreamSynchronize(b->main));
+      initial_forces(b->ctx[r], seeds[r]);
+      snapshot_io(b->ctx[r], snap[r], true);
+    }
+    cudaEvent_t t0, t1;
+    SRBE_CUDA(cudaEventCreate(&t0));
+    SRBE_CUDA(cudaEventCreate(&t1));
+    double best = 1e300;
+    int best_w = b->width;
+    for (int i = 0; i < n_widths; ++i) {
+      const int w = std::min(widths[i], n);
+      b->width = w;
+      b->dirty = true;
+      batch_run(b, 2, seeds);                        // ordinary first step, capture, one replay
+      SRBE_CUDA(cudaEventRecord(t0, b->main));
+      batch_run(b, trial_steps, seeds);
+      SRBE_CUDA(cudaEventRecord(t1, b->main));
+      SRBE_CUDA(cudaEventSynchronize(t1));
+      float ms = 0.f;
+      SRBE_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+      if (ms / trial_steps < best) {
+        best = ms / trial_steps;
+        best_w = w;
+      }
+      if (ms_per_step) ms_per_step[i] = ms / trial_steps;
+      for (int r = 0; r < n; ++r) {
+        srbe_ctx *c = b->ctx[r];
+        SRBE_CUDA(cudaStreamSynchronize(c->stream));
+        snapshot_io(c, snap[r], false);
+      }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    for (int r = 0; r < n; ++r) SRBE_CUDA(cudaStreamSynchronize(b->ctx[r]->stream));
+    b->width = best_w;
+    b->dirty = true;
+  });
+}
+
+int srbe_autotune_skin(srbe_ctx *c, int trial_steps, uint64_t seed, const double *skins, int n_skins,
+                       double *ms_per_step) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(trial_steps >= 1 && skins && n_skins >= 1, SRBE_EINVAL, "need trial steps and candidate skins");
+    SRBE_REQUIRE(c->have_md && c->have_pos && c->have_ele, SRBE_ESTATE, "the context needs an MD state");
+    for (int i = 0; i < n_skins; ++i)
+      SRBE_REQUIRE(std::isfinite(skins[i]) && skins[i] > 0.0 && skins[i] <= 1.0, SRBE_EINVAL, "skin out of (0, 1]");
+    const bool prof = c->profiling;
+    c->profiling = false;
+    initial_forces(c, seed);
+    Snapshot snap;
+    snapshot_io(c, snap, true);
+    cudaEvent_t t0, t1;
+    SRBE_CUDA(cudaEventCreate(&t0));
+    SRBE_CUDA(cudaEventCreate(&t1));
+    double best = 1e300, best_skin = c->nbr.skin;
+    for (int i = 0; i < n_skins; ++i) {
+      c->nbr.skin = skins[i];
+      c->nbr.cap = 0;
+      reserve(c);
+      neighbor_force_rebuild(c);
+      extra(c)->graph_dirty = true;
+      SRBE_REQUIRE(srbe_step(c, 2, seed) == SRBE_OK, SRBE_ECUDA, c->err);
+      SRBE_CUDA(cudaEventRecord(t0, c->stream));
+      SRBE_REQUIRE(srbe_step(c, trial_steps, seed) == SRBE_OK, SRBE_ECUDA, c->err);
+      SRBE_CUDA(cudaEventRecord(t1, c->stream));
+      SRBE_CUDA(cudaEventSynchronize(t1));
+      float ms = 0.f;
+      SRBE_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+      if (ms_per_step) ms_per_step[i] = ms / trial_steps;
+      if (ms / trial_steps < best) {
+        best = ms / trial_steps;
+        best_skin = skins[i];
+      }
+      snapshot_io(c, snap, false);
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    c->nbr.skin = best_skin;
+    c->nbr.cap = 0;
+    reserve(c);
+    neighbor_force_rebuild(c);
+    c->profiling = prof;
+  });
 }
 
 }  // extern "C"

@@ -994,7 +994,9 @@ void neighbor_update(srbe_ctx *c) {
   const int want = (int)std::max<int64_t>(1, std::min<int64_t>((std::max<int64_t>(n, c->ne) * 32 + 255) / 256,
                                                                  (int64_t)blocks_per_sm * nsm));
   void *args[] = {&a};
+  coop_before(c);
   SRBE_CUDA(cudaLaunchCooperativeKernel((const void *)k_neighbor_update, dim3(want), dim3(256), args, 0, c->stream));
+  coop_after(c);
   c->launches++;
 }
 

@@ -615,7 +615,9 @@ void charge_update_pcg(srbe_ctx *c) {
   a.stats = c->pcg.stats.p;
   a.res = c->pcg.res.p;
   void *args[] = {&a};
+  coop_before(c);
   SRBE_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg, dim3(grid), dim3(256), args, 0, c->stream));
+  coop_after(c);
   c->launches++;
 }
 
@@ -661,6 +663,64 @@ void charge_update(srbe_ctx *c) {
     k_charges_fp64<<<nb, 256, 0, c->stream>>>(ne, c->Bmat.p, c->bvec.p, c->dpsi, c->qd.p, c->we.p, c->wd, c->s_e,
                                               c->Q.p, c->Q32.p, c->scal.p);
   c->launches++;
+  SRBE_CUDA(cudaGetLastError());
+}
+
+// FP64 check of the constant-potential conditions (Eqs. 9-10) met by the charges in use:
+// A Q = dpsi d + b + psi_bar e, so row i of the residual is (A Q)_i - dpsi d_i - b_i - psi_bar.
+// Warp per row; the squared residual and the squared right-hand side of each row go to rr[2 i].
+__global__ void __launch_bounds__(256)
+k_cp_residual_rows(int64_t n, const double *__restrict__ A, const double *__restrict__ Q, const double *__restrict__ d,
+                   const double *__restrict__ b, double dpsi, const double *__restrict__ scal,
+                   double *__restrict__ rr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  const double *a = A + row * n;
+  double acc = 0.0;
+  for (int64_t j = lane; j < n; j += 32) acc = fma(__ldcs(a + j), __ldg(Q + j), acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    const double rhs = fma(dpsi, d[row], b[row]);
+    const double r = acc - rhs - scal[kScalPsi];
+    rr[2 * row] = r * r;
+    rr[2 * row + 1] = rhs * rhs;
+  }
+}
+
+// one block: out[0] = sum of squared residuals, out[1] = sum of squared right-hand sides (fixed order)
+__global__ void k_cp_residual_sum(int64_t n, const double *__restrict__ rr, double *__restrict__ out) {
+  __shared__ double red[2][256];
+  const int t = threadIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int64_t i = t; i < n; i += 256) {
+    a += rr[2 * i];
+    b += rr[2 * i + 1];
+  }
+  red[0][t] = a;
+  red[1][t] = b;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (t < s) {
+      red[0][t] += red[0][t + s];
+      red[1][t] += red[1][t + s];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    out[0] = red[0][0];
+    out[1] = red[1][0];
+  }
+}
+
+void charge_residual(srbe_ctx *c, double *out_dev) {
+  const int64_t n = c->ne;
+  double *rr = c->resid.ensure((size_t)2 * std::max<int64_t>(n, 1));
+  k_cp_residual_rows<<<blocks_for(n * 32, 256), 256, 0, c->stream>>>(n, c->Amat.p, c->Q.p, c->ed.p, c->bvec.p,
+                                                                      c->dpsi, c->scal.p, rr);
+  k_cp_residual_sum<<<1, 256, 0, c->stream>>>(n, rr, out_dev);
+  c->launches += 2;
   SRBE_CUDA(cudaGetLastError());
 }
 

@@ -220,12 +220,17 @@ struct srbe_ctx {
   srbe::DevBuf<double> scal;                   // device scalars (see kScal* indices)
   srbe::DevBuf<double> epart;                  // per-block energy partials
   srbe::DevBuf<int> flag;                      // device error flag
+  srbe::DevBuf<double> resid;                  // per-row squared residuals of the FP64 check
   double h_scal[16];
 
   srbe::HostExt *hx = nullptr;
 
   // phase tracing
   bool profiling = false;
+  bool use_graphs = true;                      // srbe_step replays a captured CUDA graph per step
+  // Cooperative kernels (grid-wide barriers) never overlap one another: each waits on and then
+  // records a chain event, the process-wide one of the device, or during a capture a capture-local one
+  cudaEvent_t coop_chain = nullptr;
 
   // counters
   int64_t launches = 0;
@@ -319,6 +324,10 @@ void steepest_descent_move(srbe_ctx *c, double a, double dmax);
 void build_A_and_inverse(srbe_ctx *c);
 void energy_scalars(srbe_ctx *c);
 enum Phase { kPhUpload = 0, kPhCells, kPhS1, kPhRhs, kPhSolve, kPhS2, kPhForces, kPhIntegrate, kPhEnergy, kPhCount };
+void coop_before(srbe_ctx *c);
+void coop_after(srbe_ctx *c);
+cudaEvent_t device_coop_chain();
+void charge_residual(srbe_ctx *c, double *out_dev);
 void phase_begin(srbe_ctx *c, int ph);
 void phase_end(srbe_ctx *c, int ph);
 void reserve(srbe_ctx *c);

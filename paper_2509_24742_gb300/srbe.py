@@ -63,6 +63,8 @@ EXPORTS = {
     "srbe_forces_dev": ([_vp, _vp, _vp], _int),
     "srbe_get_counters": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _int),
     "srbe_set_profiling": ([_vp, _int], _int),
+    "srbe_set_graphs": ([_vp, _int], _int),
+    "srbe_graph_state": ([_vp, ctypes.POINTER(_int), ctypes.POINTER(_i64)], _int),
     "srbe_get_phase_times": ([_vp, _dp, ctypes.POINTER(_i64)], _int),
     "srbe_structure_factor_noalloc": ([_dp, _i64, _vp, _vp, _int, _vp, _vp, _vp], _int),
     "srbe_minimize": ([_vp, _int, _dbl, _dbl, _u64], _int),
@@ -77,6 +79,18 @@ EXPORTS = {
     "srbe_mlp_gradients": ([_vp, _fp, _fp, _i64, _fp, ctypes.POINTER(_dbl)], _int),
     "srbe_mlp_train": ([_vp, _fp, _fp, _i64, _int, _int, ctypes.c_float, ctypes.c_float, _u64,
                         ctypes.POINTER(_dbl)], _int),
+    "srbe_charge_residual": ([_vp, _dp], _int),
+    "srbe_set_skin": ([_vp, _dbl], _int),
+    "srbe_get_skin": ([_vp], _dbl),
+    "srbe_autotune_skin": ([_vp, _int, _u64, _dp, _int, _dp], _int),
+    "srbe_batch_create": ([_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _int),
+    "srbe_batch_destroy": ([_vp], _int),
+    "srbe_batch_last_error": ([_vp], ctypes.c_char_p),
+    "srbe_batch_set_width": ([_vp, _int], _int),
+    "srbe_batch_get_width": ([_vp], _int),
+    "srbe_batch_stream": ([_vp], _vp),
+    "srbe_batch_step": ([_vp, _int, ctypes.POINTER(_u64), _dp], _int),
+    "srbe_batch_autotune": ([_vp, _int, ctypes.POINTER(_u64), ctypes.POINTER(_int), _int, _dp], _int),
 }
 PHASES = ("upload", "cells", "S1", "rhs", "solve", "S2", "forces", "integrate", "energy")
 
@@ -253,6 +267,15 @@ class Context:
     def step(self, nsteps, seed0):
         self._check(self.lib.srbe_step(self.h, int(nsteps), int(seed0)))
 
+    def set_graphs(self, on=True):
+        self._check(self.lib.srbe_set_graphs(self.h, 1 if on else 0))
+
+    def graph_state(self):
+        """(1 live / 0 none / -1 capture failed, kernels per replayed step)."""
+        cap, k = _int(), _i64()
+        self._check(self.lib.srbe_graph_state(self.h, ctypes.byref(cap), ctypes.byref(k)))
+        return cap.value, k.value
+
     def set_profiling(self, on=True):
         self._check(self.lib.srbe_set_profiling(self.h, 1 if on else 0))
 
@@ -324,6 +347,96 @@ class Context:
         a, b = _i64(), _i64()
         self._check(self.lib.srbe_get_counters(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def charge_residual(self):
+        """FP64 relative residual of the constant-potential conditions met by the current charges."""
+        r = _dbl()
+        self._check(self.lib.srbe_charge_residual(self.h, ctypes.byref(r)))
+        return r.value
+
+    def set_skin(self, skin):
+        self._check(self.lib.srbe_set_skin(self.h, float(skin)))
+
+    def skin(self):
+        return self.lib.srbe_get_skin(self.h)
+
+    def autotune_skin(self, trial_steps, seed, skins=(0.05, 0.075, 0.1, 0.15, 0.2)):
+        """Times each candidate Verlet skin, keeps the fastest; returns {skin: ms per step}."""
+        sk = _d(skins)
+        ms = np.zeros(sk.size)
+        self._check(self.lib.srbe_autotune_skin(self.h, int(trial_steps), int(seed), _ptr(sk), sk.size, _ptr(ms)))
+        return dict(zip(sk.tolist(), ms.tolist()))
+
+
+class Batch:
+    """Many replicas (Contexts) stepped as one CUDA graph launch per step; the contexts are borrowed
+    and must outlive the batch."""
+
+    def __init__(self, contexts):
+        self.lib = load()
+        self.ctxs = list(contexts)
+        arr = (_vp * len(self.ctxs))(*[c.h for c in self.ctxs])
+        h = _vp()
+        code = self.lib.srbe_batch_create(len(self.ctxs), arr, ctypes.byref(h))
+        if code != SRBE_OK:
+            raise SrbeError(code, "srbe_batch_create failed")
+        self.h = h
+
+    def _check(self, code):
+        if code != SRBE_OK:
+            raise SrbeError(code, (self.lib.srbe_batch_last_error(self.h) or b"").decode())
+
+    def _seeds(self, seeds):
+        s = np.ascontiguousarray(seeds, dtype=np.uint64)
+        if s.size != len(self.ctxs):
+            raise ValueError("one seed per replica")
+        return s, s.ctypes.data_as(ctypes.POINTER(_u64))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.srbe_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_width(self, width):
+        self._check(self.lib.srbe_batch_set_width(self.h, int(width)))
+
+    def width(self):
+        return self.lib.srbe_batch_get_width(self.h)
+
+    def stream(self):
+        """The batch's cudaStream_t as an integer (for torch.cuda.ExternalStream)."""
+        return self.lib.srbe_batch_stream(self.h) or 0
+
+    def step(self, nsteps, seeds, residuals=False):
+        """nsteps steps of every replica; with residuals=True returns each replica's FP64 check."""
+        s, sp = self._seeds(seeds)
+        res = np.zeros(len(self.ctxs)) if residuals else None
+        self._check(self.lib.srbe_batch_step(self.h, int(nsteps), sp, _ptr(res) if residuals else None))
+        return res
+
+    def autotune(self, trial_steps, seeds, widths=None):
+        """Times each candidate stream width, keeps the fastest; returns {width: ms per batch step}."""
+        n = len(self.ctxs)
+        if widths is None:
+            widths = sorted({0, 1, 2, 4, 8, 16, 32, n} & set(range(n + 1)))
+        w = np.ascontiguousarray(widths, dtype=np.int32)
+        ms = np.zeros(w.size)
+        s, sp = self._seeds(seeds)
+        self._check(self.lib.srbe_batch_autotune(self.h, int(trial_steps), sp,
+                                                 w.ctypes.data_as(ctypes.POINTER(_int)), w.size, _ptr(ms)))
+        return dict(zip(w.tolist(), ms.tolist()))
 
 
 def structure_factor_noalloc(box, n, r_ptr, w_ptr, K, m_ptr, S_ptr, stream_ptr=None):

@@ -179,6 +179,55 @@ def place_electrolyte(rng, Lx, Ly, zlo, zhi, n_pairs, cation_sites, d_min, max_t
     return np.asarray(r), np.asarray(q), np.asarray(mol, np.int32), np.asarray(kind, np.int32)
 
 
+def place_electrolyte_lattice(rng, Lx, Ly, zlo, zhi, n_pairs, cation_sites):
+    """Fast placement for large replicas: one molecule per cell of a near-cubic grid filling the
+    region (cells drawn at random when there are more cells than molecules), cation or anion at
+    random, centre jittered by up to 15 % of the cell, triangles randomly rotated.  Returns
+    (r, q, mol, kind, cell) like place_electrolyte plus the cell edge; neighbouring molecules can
+    start closer than in RSA, which the capped steepest-descent relaxation before MD removes."""
+    n_mol = 2 * n_pairs
+    h = zhi - zlo
+    c = (Lx * Ly * h / n_mol) ** (1.0 / 3.0)
+    nx, ny = max(1, int(Lx / c)), max(1, int(Ly / c))
+    nz = max(1, int(math.ceil(n_mol / (nx * ny))))
+    cx, cy, cz = Lx / nx, Ly / ny, h / nz
+    cells = rng.permutation(nx * ny * nz)[:n_mol]
+    ix, iy, iz = cells % nx, (cells // nx) % ny, cells // (nx * ny)
+    centre = np.c_[(ix + 0.5) * cx, (iy + 0.5) * cy, zlo + (iz + 0.5) * cz]
+    centre += rng.uniform(-0.15, 0.15, size=(n_mol, 3)) * np.array([cx, cy, cz])
+    is_cat = np.zeros(n_mol, bool)
+    is_cat[rng.permutation(n_mol)[:n_pairs]] = True
+    side_len = 0.35
+    circ = side_len / math.sqrt(3.0)
+    tri = np.array([[circ, 0.0, 0.0], [-0.5 * circ, 0.5 * side_len, 0.0], [-0.5 * circ, -0.5 * side_len, 0.0]])
+    r, q, mol, kind = [], [], [], []
+    # random rotations for every cation (uniform quaternions)
+    u = rng.uniform(size=(n_mol, 3))
+    qa = np.c_[np.sqrt(1 - u[:, 0]) * np.sin(2 * np.pi * u[:, 1]), np.sqrt(1 - u[:, 0]) * np.cos(2 * np.pi * u[:, 1]),
+               np.sqrt(u[:, 0]) * np.sin(2 * np.pi * u[:, 2]), np.sqrt(u[:, 0]) * np.cos(2 * np.pi * u[:, 2])]
+    for m in range(n_mol):
+        if is_cat[m] and cation_sites == 3:
+            a, b, cc, d = qa[m]
+            rot = np.array([[1 - 2 * (cc * cc + d * d), 2 * (b * cc - a * d), 2 * (b * d + a * cc)],
+                            [2 * (b * cc + a * d), 1 - 2 * (b * b + d * d), 2 * (cc * d - a * b)],
+                            [2 * (b * d - a * cc), 2 * (cc * d + a * b), 1 - 2 * (b * b + cc * cc)]])
+            sites = centre[m] + tri @ rot.T
+            r.extend(sites)
+            q.extend([0.26, 0.26, 0.26])
+            kind.extend([0, 1, 2])
+            mol.extend([m, m, m])
+        else:
+            r.append(centre[m])
+            q.append(0.78 if is_cat[m] else -0.78)
+            kind.append(0 if is_cat[m] else 3)
+            mol.append(m)
+    r = np.asarray(r)
+    r[:, 0] %= Lx
+    r[:, 1] %= Ly
+    r[:, 2] = np.clip(r[:, 2], zlo, zhi)
+    return r, np.asarray(q), np.asarray(mol, np.int32), np.asarray(kind, np.int32), min(cx, cy, cz)
+
+
 def maxwell_velocities(rng, mass, T):
     v = rng.normal(size=(mass.size, 3)) * np.sqrt(KB * T / mass)[:, None]
     v -= (mass[:, None] * v).sum(0) / mass.sum()
@@ -190,16 +239,20 @@ def _dmin_for_fraction(n_sites, volume, frac=0.3, cap=0.3):
 
 
 def make_slab(name, box, nx, ny, n_pairs, cation_sites, *, alpha, eta_inv, rc, P, M=None,
-              dpsi_volt=1.0, seed=0, ax=None, ay=None, T=400.0, with_md=False, lam=1.5):
+              dpsi_volt=1.0, seed=0, ax=None, ay=None, T=400.0, with_md=False, lam=1.5, placement="rsa"):
     Lx, Ly, Lz = box
     H = Lz / lam
     rng = np.random.Generator(np.random.Philox(seed))
     R, side = electrode_lattice(Lx, Ly, H, nx, ny, ax, ay)
     zlo, zhi = 2 * LAYER_DZ + WALL_GAP, H - 2 * LAYER_DZ - WALL_GAP
     n_sites = n_pairs * (cation_sites + 1)
-    # RSA of rigid triangles jams near 0.25 volume fraction; single sites fill to 0.3
-    d_min = _dmin_for_fraction(n_sites, Lx * Ly * (zhi - zlo), frac=0.3 if cation_sites == 1 else 0.2)
-    r, q, mol, kind = place_electrolyte(rng, Lx, Ly, zlo, zhi, n_pairs, cation_sites, d_min)
+    if placement == "lattice":
+        r, q, mol, kind, cell = place_electrolyte_lattice(rng, Lx, Ly, zlo, zhi, n_pairs, cation_sites)
+        d_min = min(0.3, 0.8 * cell)
+    else:
+        # RSA of rigid triangles jams near 0.25 volume fraction; single sites fill to 0.3
+        d_min = _dmin_for_fraction(n_sites, Lx * Ly * (zhi - zlo), frac=0.3 if cation_sites == 1 else 0.2)
+        r, q, mol, kind = place_electrolyte(rng, Lx, Ly, zlo, zhi, n_pairs, cation_sites, d_min)
     if M is None:
         M = int(Lz // max(Lx, Ly))
     # types: 0..2 cation sites, 3 anion, 4 electrode; masses 67/42/15 and 145 amu
@@ -249,6 +302,35 @@ def precision_100k(seed=1003, dpsi_volt=2.0):
     pairs (87,712 sites), P=500, 0-4 V."""
     return make_slab("prec100k_P500", (8.0, 8.0, 32.0), 64, 32, 21928, 3, alpha=3.5, eta_inv=19.79, rc=1.2,
                      P=500, M=4, dpsi_volt=dpsi_volt, seed=seed, with_md=True)
+
+
+def batch_replicas(n=64, seed=1004, n_total=(5000, 60000), sides=(16, 20, 24, 28, 32), aspect=(3.0, 8.0),
+                   rho=50.0, P_choices=(100, 150, 200, 250, 300, 350, 400)):
+    """Uneven replicas for the batching form: per replica an s x s lattice per layer at 0.25 nm
+    (s from `sides`, so 1,536-6,144 electrode sites and Lx = Ly = s / 4 nm), a total particle count
+    drawn from `n_total`, the electrolyte (3-site cations, 1-site anions) at `rho` sites per nm^3
+    between the walls, Lz / Lx kept in `aspect` (the ion count follows when the aspect clamps),
+    P from `P_choices`, a voltage 0-4 V in 0.0625 V steps and a seed of its own.  Placement on a
+    jittered grid (place_electrolyte_lattice) keeps generation fast at millions of sites."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    gap = 2 * (2 * LAYER_DZ + WALL_GAP)
+    for i in range(n):
+        s = int(sides[rng.integers(len(sides))])
+        L = 0.25 * s
+        ne = 6 * s * s
+        sites = max(400.0, rng.uniform(*n_total) - ne)
+        h = sites / (rho * L * L)
+        a = min(max(1.5 * (h + gap) / L, aspect[0]), aspect[1])
+        Lz = a * L
+        h = Lz / 1.5 - gap
+        n_pairs = max(50, int(rho * L * L * h / 4))
+        P = int(P_choices[rng.integers(len(P_choices))])
+        dpsi = 0.0625 * int(rng.integers(0, 65))
+        out.append(make_slab("replica%d_s%d_P%d" % (i, s, P), (L, L, Lz), s, s, n_pairs, 3, alpha=3.5,
+                             eta_inv=19.79, rc=1.2, P=P, M=None, dpsi_volt=dpsi, seed=seed * 1000 + i,
+                             with_md=True, placement="lattice"))
+    return out
 
 
 def tiny_slab(seed=7, n_pairs=3, nx=2, ny=2, box=(1.2, 1.4, 9.0), alpha=2.0, rc=1.0, P=20, M=2,

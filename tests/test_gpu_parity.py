@@ -159,3 +159,31 @@ def test_md_steps_match_oracle(orc):
     d[:, :2] -= np.asarray(s.box[:2]) * np.round(d[:, :2] / np.asarray(s.box[:2]))
     assert np.abs(d).max() < 1e-9
     assert rel(vg, v) < 1e-8
+
+
+@pytest.mark.parametrize("precision,solver", [(srbe.FP64, srbe.DIRECT), (srbe.MIXED, srbe.DIRECT),
+                                              (srbe.MIXED, srbe.PCG)])
+def test_graph_replay_is_bitwise_the_ordinary_path(precision, solver):
+    """srbe_step replaying its captured CUDA graphs gives bitwise the trajectory of the ordinary
+    launch path, across several calls, a read-back in between and a state change that recaptures."""
+    s = wl.make_slab("md_small", (2.0, 2.0, 12.0), 8, 8, 60, 3, alpha=3.5, eta_inv=19.79, rc=1.2, P=50, M=2,
+                     dpsi_volt=1.0, seed=21, ax=0.25, ay=0.25, with_md=True)
+    out = []
+    for graphs in (False, True):
+        with srbe.from_slab(s, precision=precision, alpha_A=ALPHA_A, md=True) as ctx:
+            ctx.set_graphs(graphs)
+            if solver == srbe.PCG:
+                ctx.set_solver(srbe.PCG, tol=1e-10, maxit=500, warm=srbe.WARM_PREVIOUS)
+            ctx.step(3, 91)
+            r1, v1 = ctx.get_positions(velocities=True)
+            ctx.step(5, 91)
+            state = ctx.graph_state()
+            ctx.set_solver(solver, tol=1e-10, maxit=500, warm=srbe.WARM_ZERO)   # drops the graphs
+            ctx.step(4, 91)
+            r2, v2 = ctx.get_positions(velocities=True)
+            F, Q, psi = ctx.forces()
+        out.append((r1, v1, r2, v2, F, Q, state))
+    assert out[0][6] == (0, 0)
+    assert out[1][6][0] == 1 and out[1][6][1] > 5
+    for a, b in zip(out[0][:6], out[1][:6]):
+        assert np.array_equal(a, b)
