@@ -66,7 +66,8 @@ def lib():
         L.orc_force_kspace.argtypes = [_i64, _dp, _dp, _i64, _dp, _dp, _dp, _dp]
         L.orc_dipole_z.argtypes = [_i64, _dp, _dp, _i64, _dp, _dp]
         L.orc_dipole_z.restype = _dbl
-        L.orc_force_real.argtypes = [_dp, _dbl, _dbl, _dbl, _i64, _dp, _dp, _i64, _dp, _dp, _dp, _dp]
+        L.orc_force_real.argtypes = [_dp, _dbl, _dbl, _dbl, _i64, _dp, _dp, _i64, _dp, _dp, _i64, ctypes.c_void_p,
+                                     _dp, _dp]
         L.orc_energy_ee_real.argtypes = [_dp, _dbl, _dbl, _dbl, _i64, _dp, _dp]
         L.orc_energy_ee_real.restype = _dbl
         L.orc_force_lj.argtypes = [_dp, _dbl, _i64, _dp, _ip, _ip, _i64, _dp, ctypes.c_int32, ctypes.c_int32,
@@ -305,7 +306,7 @@ def evaluate(slab, factor, m, c, *, Q_fixed=None, with_lj=True):
     Fk[:, 2] += -(4.0 * math.pi / V) * q * Mz
     Fr = np.empty_like(r)
     Er = np.empty(2)
-    lib().orc_force_real(L, slab.alpha, slab.eta, slab.rc, r.shape[0], r, q, R.shape[0], R, _d(Q), Fr, Er)
+    lib().orc_force_real(L, slab.alpha, slab.eta, slab.rc, r.shape[0], r, q, R.shape[0], R, _d(Q), 0, None, Fr, Er)
     Eee = lib().orc_energy_ee_real(L, slab.alpha, slab.eta, slab.rc, R.shape[0], R, _d(Q))
     UF = 0.5 * float((c * (S ** 2).sum(1)).sum())
     Uself = (1.0 / (math.sqrt(2 * math.pi) * slab.eta) - slab.alpha / math.sqrt(math.pi)) * float(Q @ Q) \
@@ -322,6 +323,41 @@ def evaluate(slab, factor, m, c, *, Q_fixed=None, with_lj=True):
         out.update(E_lj=E_lj, E_bond=E_b)
     out["F"] = F
     return out
+
+
+def sampled_b(slab, m, c, sites):
+    """b (e/nm, Eq. 24 with Eq. 19's near and slab parts) of the electrode sites `sites` only, from
+    the structure factor of every ion: for checks at sizes where the full solve is out of reach."""
+    L = np.asarray(slab.box, float)
+    r, q = _d(slab.r), _d(slab.q)
+    R = _d(np.asarray(slab.R)[np.asarray(sites)])
+    m = _i(m).reshape(-1, 3)
+    S1 = sfac(r, q, m, L)
+    return b_far(R, m, _d(c), S1, L) + b_near(L, slab.alpha, slab.eta, slab.rc, r, q, R) + b_slab(L, r, q, R)
+
+
+def sampled_forces(slab, m, c, Q, targets):
+    """Electrostatic forces (kJ/mol/nm) on the ions `targets` only, for given electrode charges Q:
+    k-space part of Eq. 25 with S = S1 + S2 over every particle, the slab term and the real-space
+    pairs of Eq. 13 over every image within rc."""
+    L = np.asarray(slab.box, float)
+    V = L[0] * L[1] * L[2]
+    r, q, R, Q = _d(slab.r), _d(slab.q), _d(slab.R), _d(Q)
+    m = _i(m).reshape(-1, 3)
+    c = _d(c)
+    t = np.ascontiguousarray(targets, dtype=np.int64)
+    S = sfac(r, q, m, L) + sfac(R, Q, m, L)
+    kv = kvectors(L, m)
+    rt, qt = _d(r[t]), _d(q[t])
+    Fk = np.empty_like(rt)
+    lib().orc_force_kspace(rt.shape[0], rt, qt, kv.shape[0], kv, c, _d(S), Fk)
+    Mz = lib().orc_dipole_z(r.shape[0], r, q, R.shape[0], R, Q)
+    Fk[:, 2] += -(4.0 * math.pi / V) * qt * Mz
+    Fr = np.empty_like(rt)
+    Er = np.empty(2)
+    lib().orc_force_real(L, slab.alpha, slab.eta, slab.rc, r.shape[0], r, q, R.shape[0], R, Q, t.size,
+                         t.ctypes.data_as(ctypes.c_void_p), Fr, Er)
+    return (Fk + Fr) * K_E
 
 
 def lj_bonds(slab, r):

@@ -207,14 +207,20 @@ double orc_dipole_z(int64_t ni, const double *r, const double *q, int64_t ne, co
 
 /* Real-space Coulomb forces and energies of Eq. 13 (ion-ion and ion-electrode
  * terms) for all images within rc.  E[0] = ion-ion, E[1] = ion-electrode.
- * F_i = - dU/dr_i; for a pair kernel phi(d):  F_i = - q_i q_j phi'(d) (r_i - r_j)/d. */
+ * F_i = - dU/dr_i; for a pair kernel phi(d):  F_i = - q_i q_j phi'(d) (r_i - r_j)/d.
+ * With targets != NULL only the nt ions targets[0..nt) are evaluated (row t of F is
+ * ion targets[t]; E then sums over those ions only); with NULL, nt is ignored and
+ * every ion is a target. */
 void orc_force_real(const double L[3], double alpha, double eta, double rc, int64_t ni, const double *r,
-                    const double *q, int64_t ne, const double *R, const double *Q, double *F, double *E) {
+                    const double *q, int64_t ne, const double *R, const double *Q, int64_t nt,
+                    const int64_t *targets, double *F, double *E) {
   int nx = n_images(rc, L[0]), ny = n_images(rc, L[1]);
   const double tpa = 2.0 / sqrt(M_PI);
   double eii = 0.0, eie = 0.0;
+  if (!targets) nt = ni;
 #pragma omp parallel for schedule(dynamic, 8) reduction(+ : eii, eie)
-  for (int64_t i = 0; i < ni; ++i) {
+  for (int64_t t = 0; t < nt; ++t) {
+    const int64_t i = targets ? targets[t] : t;
     nsum f[3] = {{0, 0}, {0, 0}, {0, 0}};
     nsum ui = {0, 0}, ue = {0, 0};
     for (int64_t j = 0; j < ni; ++j) {
@@ -251,7 +257,7 @@ void orc_force_real(const double L[3], double alpha, double eta, double rc, int6
           nadd(&ue, q[i] * Q[j] * phi_ie(d, alpha, eta));
         }
     }
-    for (int d = 0; d < 3; ++d) F[3 * i + d] = nval(&f[d]);
+    for (int d = 0; d < 3; ++d) F[3 * t + d] = nval(&f[d]);
     eii += nval(&ui);
     eie += nval(&ue);
   }

@@ -274,3 +274,17 @@ def test_lj_and_bond_forces_are_gradients(orc):
             rm[i, d] -= h
             fd = -(energy(rp) - energy(rm)) / (2 * h)
             assert abs(fd - F[i, d]) < 1e-5 * np.abs(F).max() + 1e-6, (i, d, fd, F[i, d])
+
+
+def test_sampled_evaluation_equals_rows_of_the_full_one(orc):
+    """The subset evaluations used for checks at full size give the rows of the full evaluation."""
+    from paper_2509_24742_gb300 import workloads as wl
+    s = wl.one_shot_784()
+    ref = orc.System(s, alpha_A=1.7)
+    m, c = ref.modes(orc.sample_metropolis(s.box, s.alpha, s.M, s.P, 5, 0))
+    ev = ref.evaluate(m, c, with_lj=False)
+    t = np.array([0, 7, 399, 123, 250])
+    Ft = orc.sampled_forces(s, m, c, ev["Q"], t)
+    np.testing.assert_allclose(Ft, ev["F"][t], rtol=1e-13, atol=1e-12 * np.abs(ev["F"]).max())
+    j = np.array([383, 0, 17, 200])
+    np.testing.assert_allclose(orc.sampled_b(s, m, c, j), ev["b"][j], rtol=1e-13, atol=1e-13)
