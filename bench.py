@@ -43,6 +43,8 @@ UNIT = "steps/s"
 DT_NS = 2e-6                        # 2 fs
 SEED = 3002
 N_MIN = 100
+N_MIN_BATCH = 200
+GAMMA, T_BATH = 50.0, 400.0         # Langevin thermostat of the MD step (1/ps, K)
 KB = 0.0083144626
 FLUSH_BYTES = 256 << 20             # larger than the 129 MB L2
 PEAKS = {"hbm_gbs": 6694.5, "fp32_tflops": 152 * 128 * 2 * 2.070e9 / 1e12, "fp64_tflops": 1.25}
@@ -206,6 +208,7 @@ def gpu_arm(args, rank, world):
     for name, prec in (("fp64", srbe.FP64), ("mixed", srbe.MIXED)):
         c = srbe.from_slab(slab, precision=prec, md=True)
         c.set_stream(stream.cuda_stream)
+        c.set_thermostat(GAMMA, T_BATH, SEED)
         c.sample_k(SEED, 0)
         ctxs[name] = c
     F64, Q64, _ = ctxs["fp64"].forces()
@@ -238,20 +241,20 @@ def gpu_arm(args, rank, world):
         l1, _ = ctx.counters()
         ms = sum(a.elapsed_time(b) for a, b in ev)
         phases = ctx.phase_times() if traced else None
+        state = ctx.graph_state()
         ctx.set_profiling(False)
-        return ms, phases, l1 - l0
+        return ms, phases, l1 - l0, state
 
     clocks = ClockSampler(local)
     clocks.start()
-    ms_head, _, launches = timed(ctxs[head], args.steps, args.warmup)
+    ms_head, _, launches, graph_state = timed(ctxs[head], args.steps, args.warmup)
     clk = clocks.stop()
-    graph_state = ctxs[head].graph_state()
     # phase split of the same form: a traced pass (ordinary launches, event pair per phase) right after
     n_trace = max(3, min(args.steps, 200))
-    ms_trace, ph_head, _ = timed(ctxs[head], n_trace, 3, traced=True)
+    ms_trace, ph_head, _, _ = timed(ctxs[head], n_trace, 3, traced=True)
     other = "fp64" if head == "mixed" else "mixed"
     n_other = max(3, min(args.steps, 50))
-    ms_other, ph_other, _ = timed(ctxs[other], n_other, max(3, min(args.warmup, 5)), traced=True)
+    ms_other, ph_other, _, _ = timed(ctxs[other], n_other, max(3, min(args.warmup, 5)), traced=True)
 
     if world > 1:
         t = torch.tensor([ms_head], device="cuda", dtype=torch.float64)
@@ -299,7 +302,9 @@ def gpu_arm(args, rank, world):
                        "phases_ms_per_step": {p: round(v[0] / n_other, 5) for p, v in ph_other.items() if v[1]}},
         "pairs_within_rc": {"ion_ion": n_ii, "ion_electrode": n_ie},
         "md": {"T_end_K": T_end, "T_start_K": 400.0, "start": "%d capped steepest-descent steps from the "
-               "seeded random packing" % N_MIN},
+               "seeded random packing" % N_MIN,
+               "thermostat": "Langevin (Eq. 39), gamma %.0f/ps, T %.0f K, exact OU step after the closing kick"
+                             % (GAMMA, T_BATH)},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
@@ -336,6 +341,67 @@ def e2e_arm(ctx, slab, stream, flush, steps):
             "what": "host-pointer force provider: srbe_set_positions + srbe_sample_k + srbe_forces per step"}
 
 
+# ---------------------------------------------------------------------------------------------- precision form
+def prec_arm(args):
+    """The 100k-particle slab (12,288 electrode sites, P = 500, 2 V): MD steps/s of the mixed form
+    and of the plain FP64 path, their errors and FP64 charge residuals, and the phase split."""
+    import torch
+    from paper_2509_24742_gb300 import srbe, workloads
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    slab = workloads.precision_100k()
+    stream = torch.cuda.Stream()
+    ctx = srbe.from_slab(slab, precision=srbe.MIXED, md=True)
+    t_setup = time.time() - t0
+    ctx.set_stream(stream.cuda_stream)
+    ctx.minimize(N_MIN)
+    ctx.set_thermostat(GAMMA, T_BATH, SEED)
+    ctx.sample_k(SEED, 0)
+    F32, Q32, _ = ctx.forces()
+    res32 = ctx.charge_residual()
+    ctx.set_precision(srbe.FP64)
+    F64, Q64, _ = ctx.forces()
+    res64 = ctx.charge_residual()
+    rms_f = float(np.sqrt(((F32 - F64) ** 2).sum(1).mean() / (F64 ** 2).sum(1).mean()))
+    rms_q = float(np.sqrt(((Q32 - Q64) ** 2).mean() / (Q64 ** 2).mean()))
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, prec, steps in (("mixed", srbe.MIXED, args.steps), ("fp64", srbe.FP64, max(3, min(args.steps, 30)))):
+        ctx.set_precision(prec)
+        ctx.step(args.warmup, SEED)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            ev[i][0].record(stream)
+            ctx.step(1, SEED)
+            ev[i][1].record(stream)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        ctx.set_profiling(True)
+        ctx.step(max(3, min(steps, 20)), SEED)
+        ph = ctx.phase_times()
+        ctx.set_profiling(False)
+        n_tr = max(3, min(steps, 20))
+        out[name] = {"steps_per_s": steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "phases_ms_per_step": {p: round(v[0] / n_tr, 5) for p, v in ph.items() if v[1]}}
+    _, v = ctx.get_positions(velocities=True)
+    T_end = float((slab.mass[:, None] * v ** 2).sum() / (3 * slab.n_ion * KB))
+    lat = ctx.lattice_info()
+    ctx.close()
+    return {"metric": "SRBE MD steps/sec on 1 GB300, precision form, 100k-particle slab",
+            "value": out["mixed"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "prec100k_P500: 8x8x32 nm, 12,288 electrode + 87,712 ion sites, P=500, M=4, "
+                                   "2 V, dt=2 fs", "l2": "flushed between timed steps (256 MB write)",
+                       "lattice_electrode": lat},
+            "accuracy": {"rms_force_err_vs_fp64_gpu": rms_f, "rms_charge_err_vs_fp64_gpu": rms_q,
+                         "fp64_charge_residual_mixed": res32, "fp64_charge_residual_fp64": res64},
+            "mixed": out["mixed"], "fp64": out["fp64"], "speedup_vs_fp64": out["mixed"]["steps_per_s"] /
+            out["fp64"]["steps_per_s"], "setup_s": t_setup, "md": {"T_end_K": T_end}}
+
+
 # ---------------------------------------------------------------------------------------------- batching form
 def batch_arm(args):
     """R uneven replicas: the mixed-precision batch (one graph launch per batch step, autotuned
@@ -350,7 +416,8 @@ def batch_arm(args):
     ctxs = []
     for s in slabs:
         c = srbe.from_slab(s, precision=srbe.MIXED, md=True)
-        c.minimize(50)
+        c.minimize(N_MIN_BATCH)
+        c.set_thermostat(GAMMA, T_BATH, int(seeds[len(ctxs)]))
         ctxs.append(c)
     torch.cuda.synchronize()
     t_setup = time.time() - t_setup
@@ -376,13 +443,20 @@ def batch_arm(args):
     clk = clocks.stop()
     res = b.step(1, seeds, residuals=True)
     launches = sum(c.counters()[0] for c in ctxs)
+    Ts, finite = [], 0
+    for s, c in zip(slabs, ctxs):
+        r, v = c.get_positions(velocities=True)
+        ok = bool(np.isfinite(r).all() and np.isfinite(v).all())
+        finite += ok
+        if ok:
+            Ts.append(float((s.mass[:, None] * v ** 2).sum() / (3 * s.n_ion * KB)))
 
     # the same replicas one after another, plain FP64 path (srbe_step, its own step graph)
     for c in ctxs:
         c.set_precision(srbe.FP64)
-    n_plain = max(3, min(args.steps, 20))
+    n_plain = max(3, min(args.steps, 5))
     for c, sd in zip(ctxs, seeds):
-        c.step(3, int(sd))
+        c.step(2, int(sd))
     torch.cuda.synchronize()
     ms_p = 0.0
     for c, sd in zip(ctxs, seeds):
@@ -410,12 +484,16 @@ def batch_arm(args):
                          (sum(s.n_ele ** 2 * 24 for s in slabs) / 1e9)},
         "launch": {"graph_launches_per_batch_step": 1, "stream_width": width,
                    "autotune_ms_per_batch_step": {str(k): round(v, 4) for k, v in tune.items()}},
-        "fp64_charge_residual": {"batch_mixed_max": float(np.max(res)), "batch_mixed_median": float(np.median(res)),
-                                 "plain_fp64_max": float(np.max(res_p))},
+        "fp64_charge_residual": {"batch_mixed_max": float(np.nanmax(res)), "batch_mixed_median": float(np.nanmedian(res)),
+                                 "plain_fp64_max": float(np.nanmax(res_p)),
+                                 "replicas_with_finite_residual": int(np.isfinite(res).sum())},
         "plain_fp64_one_by_one": {"value": plain, "unit": "replica-steps/s", "steps_per_replica": n_plain,
                                   "what": "srbe_step per replica in turn, FP64, host-timed with a device sync "
                                           "after each replica"},
         "speedup_vs_plain_fp64": value / plain,
+        "md": {"replicas_finite": finite, "T_K_min_median_max": [min(Ts), float(np.median(Ts)), max(Ts)] if Ts else None,
+               "start": "%d capped steepest-descent steps per replica" % N_MIN_BATCH,
+               "thermostat": "Langevin, gamma %.0f/ps, T %.0f K" % (GAMMA, T_BATH)},
         "gpu_launches": launches, "setup_s": t_setup, "clocks": clk,
     }
 
@@ -435,7 +513,7 @@ def oracle_steps(budget_s, max_steps, min_steps=2):
     n = 0
     while n < max_steps and (n < min_steps or time.perf_counter() - t0 < budget_s):
         m, c = sysm.modes(oracle.sample_metropolis(slab.box, slab.alpha, slab.M, slab.P, SEED, n + 1))
-        r, v, ev = sysm.md_step(r, v, F, m, c)
+        r, v, ev = sysm.md_step(r, v, F, m, c, thermostat=(GAMMA, T_BATH, SEED), step=n + 1)
         F = ev["F"]
         n += 1
     return n, time.perf_counter() - t0, int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
@@ -468,7 +546,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="md11072", choices=["md11072", "batch64"])
+    ap.add_argument("--workload", default="md11072", choices=["md11072", "batch64", "prec100k"])
     ap.add_argument("--replicas", type=int, default=64)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -482,6 +560,9 @@ def main():
         return
     if args.workload == "batch64":
         print(json.dumps(batch_arm(args)))
+        return
+    if args.workload == "prec100k":
+        print(json.dumps(prec_arm(args)))
         return
     if world > 1:
         import torch

@@ -118,12 +118,14 @@ int srbe_sample_k(srbe_ctx *ctx, uint64_t seed, uint64_t step);
 int srbe_get_k(const srbe_ctx *ctx, int32_t *m, double *G);
 
 /* Sets the P sampled modes explicitly (m [P][3]); weights follow Eq. 24/25 with the
- * context's G.  P may differ from srbe_create's.  Errors: SRBE_EINVAL for a mode in I u {0}. */
+ * context's G.  P may differ from srbe_create's.  Errors: SRBE_EINVAL for a mode in I u {0} or
+ * more than 2,097,120 modes in all. */
 int srbe_set_k(srbe_ctx *ctx, const int32_t *m, int P);
 
 /* Replaces the whole mode list by an explicit deterministic list m [K][3] with per-mode
  * weights w [K] (the factor c_k multiplying Re/Im terms in Eqs. 20-21; for full Ewald
- * w = 4 pi exp(-k^2/4 alpha^2) / (V k^2)).  Used to evaluate full Ewald on the same path. */
+ * w = 4 pi exp(-k^2/4 alpha^2) / (V k^2)).  Used to evaluate full Ewald on the same path.
+ * Errors: SRBE_EINVAL for k = 0, non-finite weights or K > 2,097,120. */
 int srbe_set_mode_list(srbe_ctx *ctx, const int32_t *m, const double *w, int K);
 
 /* Electrode-charge update of Algorithm 1 ("compute b, update Q"): S1 (Eq. 15), b (Eq. 24 with
@@ -227,6 +229,28 @@ int srbe_mlp_train(srbe_ctx *ctx, const float *D, const float *target, int64_t n
  * restores positions, velocities, forces, charges and the step counter after each trial, keeps the
  * fastest skin and writes the per-candidate ms per step to ms_per_step (n_skins entries, or NULL). */
 int srbe_charge_residual(srbe_ctx *ctx, double *rel_residual);
+
+/* Lattice electrodes (an evaluation order of Eqs. 15 and 24, not a change of the method): when every
+ * electrode layer (sites of equal z, at most 8 layers) is a full nx x ny rectangular lattice whose
+ * spacing divides Lx and Ly (the same nx, ny in every layer; any in-plane origin per layer),
+ * srbe_set_electrode recognises it and the electrode sums run through per-layer 2D discrete Fourier
+ * transforms: S2(k) = sum_l e^{i k.(x0_l, y0_l, Z_l)} Qhat_l[m_x mod nx, m_y mod ny] and the far part
+ * of b from the modes binned by (m_x mod nx, m_y mod ny), in FP64 in both precision forms.  The
+ * results equal the plain per-site sums up to rounding.  The transforms cost a fixed handful of small
+ * launches, so they only pay for large electrodes: srbe_set_lattice(ctx, mode) with mode 0 = never,
+ * 1 = when N_ele x K >= 4e6 (the default), 2 = always (whenever the lattice is recognised).
+ * srbe_lattice_info gives (layers, nx, ny), or zeros when the electrode is not such a lattice. */
+int srbe_set_lattice(srbe_ctx *ctx, int mode);
+int srbe_lattice_info(srbe_ctx *ctx, int32_t dims[3]);
+
+/* Thermostat of Algorithm 1's integration step: the Langevin equation of Eq. 39, read with gamma as
+ * a collision rate (1/ps): friction m gamma v and noise sqrt(2 m gamma kB T) dW per ion component.
+ * srbe_step applies its exact Ornstein-Uhlenbeck solution over each step after the closing half
+ * kick: v <- c1 v + sqrt((1 - c1^2) kB T / m) g, c1 = exp(-gamma dt), g standard normal from
+ * Philox4x64-10 with key (seed, 0x4C414E47) and counter (step, ion, 0, 0) through Box-Muller (the
+ * same numbers as any other implementation of that recipe).  gamma = 0 (the default) is plain
+ * velocity Verlet.  Errors: SRBE_EINVAL for negative or non-finite gamma or T. */
+int srbe_set_thermostat(srbe_ctx *ctx, double gamma, double T, uint64_t seed);
 int srbe_set_skin(srbe_ctx *ctx, double skin);
 double srbe_get_skin(const srbe_ctx *ctx);
 int srbe_autotune_skin(srbe_ctx *ctx, int trial_steps, uint64_t seed, const double *skins, int n_skins,

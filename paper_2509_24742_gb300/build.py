@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsrbe.so")
-SOURCES = ["api.cu", "kspace.cu", "realspace.cu", "solve.cu", "learned.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "kspace.cu", "realspace.cu", "solve.cu", "learned.cu", "lattice.cu", "noalloc.cu"]
 HEADERS = ["srbe_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

@@ -443,22 +443,26 @@ void reserve(srbe_ctx *c) {
   nb.pfb.ensure(nn);
   nb.cell_s.ensure(nn);
   nb.flag.ensure(2);
+  if (c->lat.nl > 0) c->lat.E.ensure((size_t)K * c->lat.nl);
 }
 
 }  // namespace srbe
 
 namespace {
 
+// the word after the mode list carries the MD step number (low, high 32 bits) for the thermostat
+inline int4 step_word(uint64_t step) { return make_int4((int)(uint32_t)step, (int)(uint32_t)(step >> 32), 0, 0); }
+
 void upload_modes(srbe_ctx *c) {
   const int K = (int)c->hc.size();
-  if ((size_t)K > c->stage_cap) {
+  if ((size_t)K + 1 > c->stage_cap) {
     if (c->h_mode_stage) cudaFreeHost(c->h_mode_stage);
     if (c->h_w_stage) cudaFreeHost(c->h_w_stage);
     c->h_mode_stage = nullptr;
     c->h_w_stage = nullptr;
-    SRBE_CUDA(cudaMallocHost((void **)&c->h_mode_stage, sizeof(int4) * std::max(K, 1)));
-    SRBE_CUDA(cudaMallocHost((void **)&c->h_w_stage, sizeof(double) * std::max(K, 1)));
-    c->stage_cap = (size_t)K;
+    SRBE_CUDA(cudaMallocHost((void **)&c->h_mode_stage, sizeof(int4) * (K + 1)));
+    SRBE_CUDA(cudaMallocHost((void **)&c->h_w_stage, sizeof(double) * (K + 1)));
+    c->stage_cap = (size_t)K + 1;
   }
   // the previous copy out of the pinned buffer must have finished before it is overwritten
   SRBE_CUDA(cudaEventSynchronize(c->stage_done));
@@ -466,15 +470,15 @@ void upload_modes(srbe_ctx *c) {
     c->h_mode_stage[k] = make_int4(c->hm[4 * k], c->hm[4 * k + 1], c->hm[4 * k + 2], 0);
     c->h_w_stage[k] = c->hc[k];
   }
-  c->dm.ensure(std::max(K, 1));
+  c->h_mode_stage[K] = step_word(c->md_step);
+  c->dm.ensure(K + 1);
   c->dc.ensure(std::max(K, 1));
   c->S1.ensure(std::max(K, 1));
   c->S2.ensure(std::max(K, 1));
   phase_begin(c, kPhUpload);
-  if (K > 0) {
-    SRBE_CUDA(cudaMemcpyAsync(c->dm.p, c->h_mode_stage, sizeof(int4) * K, cudaMemcpyHostToDevice, c->stream));
+  SRBE_CUDA(cudaMemcpyAsync(c->dm.p, c->h_mode_stage, sizeof(int4) * (K + 1), cudaMemcpyHostToDevice, c->stream));
+  if (K > 0)
     SRBE_CUDA(cudaMemcpyAsync(c->dc.p, c->h_w_stage, sizeof(double) * K, cudaMemcpyHostToDevice, c->stream));
-  }
   phase_end(c, kPhUpload);
   SRBE_CUDA(cudaEventRecord(c->stage_done, c->stream));
   c->K = K;
@@ -522,10 +526,9 @@ void forces_pass(srbe_ctx *c, bool energies);
 void device_step(srbe_ctx *c, int slot) {
   Extra *e = extra(c);
   const int K = c->K;
-  if (K > 0) {
-    SRBE_CUDA(cudaMemcpyAsync(c->dm.p, e->slot[slot].hm, sizeof(int4) * K, cudaMemcpyHostToDevice, c->stream));
+  SRBE_CUDA(cudaMemcpyAsync(c->dm.p, e->slot[slot].hm, sizeof(int4) * (K + 1), cudaMemcpyHostToDevice, c->stream));
+  if (K > 0)
     SRBE_CUDA(cudaMemcpyAsync(c->dc.p, e->slot[slot].hw, sizeof(double) * K, cudaMemcpyHostToDevice, c->stream));
-  }
   integrate_kick_drift(c, 0.5 * c->dt, true);
   forces_pass(c, false);
   integrate_kick_drift(c, 0.5 * c->dt, false);
@@ -544,7 +547,7 @@ void ensure_slot_buffers(srbe_ctx *c) {
     e->slot_cap = 0;
   }
   for (auto &sl : e->slot) {
-    if (!sl.hm) SRBE_CUDA(cudaMallocHost((void **)&sl.hm, sizeof(int4) * std::max(c->K, 1)));
+    if (!sl.hm) SRBE_CUDA(cudaMallocHost((void **)&sl.hm, sizeof(int4) * (std::max(c->K, 1) + 1)));
     if (!sl.hw) SRBE_CUDA(cudaMallocHost((void **)&sl.hw, sizeof(double) * std::max(c->K, 1)));
     if (!sl.done) {
       SRBE_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
@@ -561,6 +564,7 @@ void copy_to_slot(srbe_ctx *c, int slot) {
     e->slot[slot].hm[k] = make_int4(c->hm[4 * k], c->hm[4 * k + 1], c->hm[4 * k + 2], 0);
     e->slot[slot].hw[k] = c->hc[k];
   }
+  e->slot[slot].hm[c->K] = step_word(c->md_step);
 }
 
 void fill_slot(srbe_ctx *c, int slot) {
@@ -668,7 +672,8 @@ void charges_pass(srbe_ctx *c) {
 void forces_pass(srbe_ctx *c, bool energies) {
   charges_pass(c);
   phase_begin(c, kPhS2);
-  structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele, 1);
+  if (c->lat.active(c->ne, c->K)) lattice_s2(c, c->S2.p, c->S1.p, kScalMele);
+  else structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele, 1);
   phase_end(c, kPhS2);
   phase_begin(c, kPhForces);
   ion_forces(c, energies);
@@ -761,7 +766,7 @@ int srbe_create(const double box[3], double alpha, double eta, double rc, int P,
   if (!out) return SRBE_EINVAL;
   *out = nullptr;
   if (!box || !(box[0] > 0) || !(box[1] > 0) || !(box[2] > 0) || !std::isfinite(box[0]) || !std::isfinite(box[1]) ||
-      !std::isfinite(box[2]) || !(alpha > 0) || !(eta > 0) || !(rc > 0) || P < 0 || kz0 < 0 ||
+      !std::isfinite(box[2]) || !(alpha > 0) || !(eta > 0) || !(rc > 0) || P < 0 || kz0 < 0 || (int64_t)P + kz0 > kMaxModes ||
       !std::isfinite(psi_left) || !std::isfinite(psi_right) || !std::isfinite(alpha) || !std::isfinite(eta) ||
       !std::isfinite(rc))
     return SRBE_EINVAL;
@@ -899,6 +904,7 @@ int srbe_set_electrode(srbe_ctx *c, int64_t n_ele, const double *R, const int8_t
                                                                             1.0 / c->L[2]),
                                                                c->eu.p);
     SRBE_CUDA(cudaGetLastError());
+    lattice_setup(c, x, y, z);
     build_A_and_inverse(c);
     c->have_ele = true;
     extra(c)->forces_valid = false;
@@ -1090,6 +1096,7 @@ int srbe_get_k(const srbe_ctx *cc, int32_t *m, double *G) {
 int srbe_set_k(srbe_ctx *c, const int32_t *m, int P) {
   return guarded(c, [&] {
     SRBE_REQUIRE(P >= 0 && (P == 0 || m), SRBE_EINVAL, "bad sampled-mode list");
+    SRBE_REQUIRE((int64_t)P + c->M <= kMaxModes, SRBE_EINVAL, "too many modes (at most 2,097,120)");
     for (int l = 0; l < P; ++l)
       SRBE_REQUIRE(!(m[3 * l] == 0 && m[3 * l + 1] == 0 && std::abs(m[3 * l + 2]) <= c->M), SRBE_EINVAL,
                    "sampled mode lies in I u {0}");
@@ -1100,6 +1107,7 @@ int srbe_set_k(srbe_ctx *c, const int32_t *m, int P) {
 int srbe_set_mode_list(srbe_ctx *c, const int32_t *m, const double *w, int K) {
   return guarded(c, [&] {
     SRBE_REQUIRE(K >= 0 && (K == 0 || (m && w)), SRBE_EINVAL, "bad mode list");
+    SRBE_REQUIRE(K <= kMaxModes, SRBE_EINVAL, "too many modes (at most 2,097,120)");
     SRBE_REQUIRE(finite_all(w, K), SRBE_EINVAL, "non-finite mode weight");
     c->hm.clear();
     c->hc.assign(w, w + K);
@@ -1477,6 +1485,32 @@ int srbe_get_counters(const srbe_ctx *cc, int64_t *kernel_launches, int64_t *mod
   if (kernel_launches) *kernel_launches = cc->launches;
   if (mode_evals) *mode_evals = cc->mode_evals;
   return SRBE_OK;
+}
+
+int srbe_set_lattice(srbe_ctx *c, int on) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(on >= 0 && on <= 2, SRBE_EINVAL, "lattice mode is 0 (never), 1 (when it pays) or 2 (always)");
+    c->lat.mode = on;
+  });
+}
+
+int srbe_lattice_info(srbe_ctx *c, int32_t dims[3]) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(dims, SRBE_EINVAL, "null output");
+    dims[0] = c->lat.nl;
+    dims[1] = c->lat.nx;
+    dims[2] = c->lat.ny;
+  }, true);
+}
+
+int srbe_set_thermostat(srbe_ctx *c, double gamma, double T, uint64_t seed) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(std::isfinite(gamma) && gamma >= 0.0 && std::isfinite(T) && T >= 0.0, SRBE_EINVAL,
+                 "thermostat needs gamma >= 0 (1/ps) and T >= 0 (K)");
+    c->lang_gamma = gamma;
+    c->lang_T = T;
+    c->lang_seed = seed;
+  });
 }
 
 int srbe_charge_residual(srbe_ctx *c, double *rel_residual) {

@@ -618,7 +618,7 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
                 const double2 *__restrict__ coefS, const float2 *__restrict__ coefS32,
                 const double2 *__restrict__ tab, double3 invL, CellsDev ions, ListsDev nl,
                 double Lx, double Ly, double alpha, double eta, double rc, double slab, const double *__restrict__ scal,
-                double *__restrict__ b, float2 *__restrict__ bsplit) {
+                double *__restrict__ b, float2 *__restrict__ bsplit, const double *__restrict__ bfar) {
   __shared__ int2 wq[kWarpsPerBlock][64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t j = ((int64_t)blockIdx.x * kGatherThreads + threadIdx.x) >> 5;
@@ -627,7 +627,9 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
   const uint64_t ux = eu[j], uy = eu[ne + j], uz = eu[2 * ne + j];
   double acc = 0.0;
   KahanF32 fk;
-  if (!F32) {
+  if (bfar) {
+    // far part precomputed by the lattice transforms
+  } else if (!F32) {
     for (int k = lane; k < K; k += 32) {
       double cs, sn;
       sincos_turns(phase64(__ldg(&modes[k]), ux, uy, uz), tab, cs, sn);
@@ -681,7 +683,7 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
     // FP32 to the end of the warp sum: on this GPU every FP64 warp instruction is costly
     const float accf = warp_sum_f(fk.valuef() + fn.valuef());
     if (lane == 0) {
-      const double bj = fma(-slab * Z, scal[kScalMion], (double)accf);
+      const double bj = fma(-slab * Z, scal[kScalMion], (double)accf + (bfar ? bfar[j] : 0.0));
       const float hi = (float)bj;
       b[j] = bj;
       bsplit[j] = make_float2(hi, (float)(bj - (double)hi));
@@ -689,7 +691,7 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
   } else {
     acc = warp_sum(acc + near);
     // slab part (FP64 in every form): -(4 pi / V) Z_j sum_i q_i z_i
-    if (lane == 0) b[j] = fma(-slab * Z, scal[kScalMion], acc);
+    if (lane == 0) b[j] = fma(-slab * Z, scal[kScalMion], bfar ? acc + bfar[j] : acc);
   }
 }
 
@@ -1002,6 +1004,11 @@ void neighbor_update(srbe_ctx *c) {
 
 void electrode_rhs(srbe_ctx *c) {
   const int K = c->K;
+  const double *bfar = nullptr;
+  if (c->lat.active(c->ne, K)) {
+    lattice_bfar(c);
+    bfar = c->lat.bF.p;
+  }
   double2 *coef = c->coef.p;   // written by the S1 reduction
   const double3 invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
   const double slab = 4.0 * kPi / c->V;
@@ -1011,14 +1018,16 @@ void electrode_rhs(srbe_ctx *c) {
     k_electrode_rhs<true><<<nb, kGatherThreads, 0, c->stream>>>(c->ne, c->ex.p, c->ey.p, c->ez.p, c->eu.p, K, c->dm.p,
                                                                coef,
                                                                c->coef32.p, c->tab.p, invL, ions, lists_dev(c), c->L[0], c->L[1], c->alpha,
-                                                               c->eta, c->rc, slab, c->scal.p, c->bvec.p, c->bsplit.p);
+                                                               c->eta, c->rc, slab, c->scal.p, c->bvec.p, c->bsplit.p,
+                                                               bfar);
   else
     k_electrode_rhs<false><<<nb, kGatherThreads, 0, c->stream>>>(c->ne, c->ex.p, c->ey.p, c->ez.p, c->eu.p, K, c->dm.p,
                                                                coef,
                                                                 c->coef32.p, c->tab.p, invL, ions, lists_dev(c), c->L[0], c->L[1], c->alpha,
-                                                                c->eta, c->rc, slab, c->scal.p, c->bvec.p, c->bsplit.p);
+                                                                c->eta, c->rc, slab, c->scal.p, c->bvec.p, c->bsplit.p,
+                                                                bfar);
   c->launches++;
-  c->mode_evals += c->ne * (int64_t)K;
+  if (!bfar) c->mode_evals += c->ne * (int64_t)K;
   SRBE_CUDA(cudaGetLastError());
 }
 
@@ -1296,14 +1305,44 @@ void ion_forces(srbe_ctx *c, bool energies) {
 // ------------------------------------------------------------------------------------------------
 // velocity Verlet: v += fac F / m ; optionally r += dt v with x, y wrapped into [0, L)
 // ------------------------------------------------------------------------------------------------
+// Langevin part of Eq. 39 over one step, solved exactly (Ornstein-Uhlenbeck):
+// v <- c1 v + sqrt((1 - c1^2) kB T / m) g with c1 = exp(-gamma dt) and g three standard normals per
+// ion from Philox4x64-10, key (seed, 'LANG'), counter (step, i, 0, 0), Box-Muller on 53-bit uniforms
+// strictly inside (0, 1).  The step number is read from device memory (the word after the mode list)
+// so that a replayed graph draws fresh noise every step.
+struct Thermo {
+  int on = 0;
+  double c1 = 1.0, s2 = 0.0;          // e^{-gamma dt}, (1 - c1^2) kB T
+  uint64_t seed = 0;
+  const int4 *step = nullptr;
+};
+
 __global__ void k_kick_drift(int64_t n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                              double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                              const double *__restrict__ F, const double *__restrict__ minv, double fac, double dt,
-                             int drift, double Lx, double Ly) {
+                             int drift, double Lx, double Ly, Thermo th) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double w = fac * minv[i];
   double a = fma(w, F[i], vx[i]), b = fma(w, F[n + i], vy[i]), c = fma(w, F[2 * n + i], vz[i]);
+  if (th.on) {
+    const int4 st = *th.step;
+    const uint64_t step = (uint64_t)(uint32_t)st.x | ((uint64_t)(uint32_t)st.y << 32);
+    uint64_t wd[4];
+    philox4x64_dev(step, (uint64_t)i, 0, 0, th.seed, 0x4C414E47ull, wd);
+    double u[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[q] = ((double)(wd[q] >> 11) + 0.5) * 0x1.0p-53;
+    const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
+    double s0, c0, s1, c1v;
+    sincospi(2.0 * u[1], &s0, &c0);
+    sincospi(2.0 * u[3], &s1, &c1v);
+    (void)s1;
+    const double sig = sqrt(th.s2 * minv[i]);
+    a = fma(th.c1, a, sig * r0 * c0);
+    b = fma(th.c1, b, sig * r0 * s0);
+    c = fma(th.c1, c, sig * r1 * c1v);
+  }
   vx[i] = a;
   vy[i] = b;
   vz[i] = c;
@@ -1324,9 +1363,18 @@ __global__ void k_sd_move(int64_t n, double *__restrict__ x, double *__restrict_
                           const double *__restrict__ F, double a, double dmax, double Lx, double Ly) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double fx = F[i], fy = F[n + i], fz = F[2 * n + i];
-  const double fn = sqrt(fx * fx + fy * fy + fz * fz);
-  const double s = fn > 0.0 ? fmin(a, dmax / fn) : 0.0;
+  double fx = F[i], fy = F[n + i], fz = F[2 * n + i];
+  double fn = sqrt(fx * fx + fy * fy + fz * fz);
+  double s = fn > 0.0 ? fmin(a, dmax / fn) : 0.0;
+  if (!isfinite(fn)) {
+    // a force that overflowed (sites on top of each other): the full capped step along the signs of
+    // its infinite components; NaN components do not move
+    fx = isinf(fx) ? copysign(1.0, fx) : 0.0;
+    fy = isinf(fy) ? copysign(1.0, fy) : 0.0;
+    fz = isinf(fz) ? copysign(1.0, fz) : 0.0;
+    fn = sqrt(fx * fx + fy * fy + fz * fz);
+    s = fn > 0.0 ? dmax / fn : 0.0;
+  }
   double X = fma(s, fx, x[i]), Y = fma(s, fy, y[i]);
   X -= Lx * floor(X / Lx);
   Y -= Ly * floor(Y / Ly);
@@ -1347,9 +1395,19 @@ void steepest_descent_move(srbe_ctx *c, double a, double dmax) {
 
 void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift) {
   if (c->ni == 0) return;
+  Thermo th;
+  if (!drift && c->lang_gamma > 0.0) {
+    // the closing half kick of a step also applies the thermostat; the step number sits in dm[K]
+    SRBE_REQUIRE(c->dm.p && c->dm.cap > (size_t)c->K, SRBE_ESTATE, "mode list without its step word");
+    th.on = 1;
+    th.c1 = std::exp(-c->lang_gamma * c->dt);
+    th.s2 = (1.0 - th.c1 * th.c1) * kBoltz * c->lang_T;
+    th.seed = c->lang_seed;
+    th.step = c->dm.p + c->K;
+  }
   k_kick_drift<<<blocks_for(c->ni, 256), 256, 0, c->stream>>>(c->ni, c->x.p, c->y.p, c->z.p, c->vx.p, c->vy.p,
                                                              c->vz.p, c->F.p, c->minv.p, fac_kick, c->dt,
-                                                             drift ? 1 : 0, c->L[0], c->L[1]);
+                                                             drift ? 1 : 0, c->L[0], c->L[1], th);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }

@@ -15,6 +15,8 @@
 namespace srbe {
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr double kBoltz = 0.0083144626;     // kJ mol^-1 K^-1
+constexpr int64_t kMaxModes = 32 * 65535;   // modes per list: 32-mode tiles on a grid's y dimension
 constexpr int kTabBits = 10;                  // sin/cos table of 1024 entries per turn
 constexpr int kTab = 1 << kTabBits;
 constexpr int kGatherThreads = 256;           // gather kernels: one warp per particle
@@ -138,6 +140,27 @@ struct HostExt;   // host-only per-context state (sampler, staging), defined in 
 // ------------------------------------------------------------------------------------------------
 // the context
 // ------------------------------------------------------------------------------------------------
+namespace srbe {
+// electrode recognised as layers of a rectangular lattice commensurate with the box (nl = 0: not)
+constexpr int kLatMaxLayers = 8;
+constexpr int kLatMaxN = 960;                  // lattice points per row / column (shared-memory lines)
+struct Lattice {
+  int nl = 0, nx = 0, ny = 0;
+  DevBuf<int32_t> site;                        // [nl][ny][nx] -> site index
+  DevBuf<uint64_t> lu;                         // [3][nl] layer origins in turns
+  DevBuf<double2> twx, twy;                    // e^{2 pi i t / nx}, e^{2 pi i t / ny}
+  DevBuf<double> Zl;                           // layer heights
+  DevBuf<double2> T, Qh;                       // [nl][ny][nx] transform scratch
+  DevBuf<double> bF;                           // far part of b per site
+  DevBuf<double2> E;                           // per-step e^{i phi_l(k)} [K][nl]
+  int mode = 1;                                // 0 never, 1 when it pays (N_ele K large), 2 always
+  int64_t min_work = 4000000;                  // N_ele x K from which mode 1 takes the lattice path
+  bool active(int64_t ne, int K) const {
+    return nl > 0 && (mode == 2 || (mode == 1 && ne * (int64_t)K >= min_work));
+  }
+};
+}  // namespace srbe
+
 struct srbe_ctx {
   // problem parameters
   double L[3] = {0, 0, 0};
@@ -232,6 +255,12 @@ struct srbe_ctx {
   // records a chain event, the process-wide one of the device, or during a capture a capture-local one
   cudaEvent_t coop_chain = nullptr;
 
+  srbe::Lattice lat;                           // lattice electrode path (Eqs. 15, 24 separated per layer)
+
+  // Langevin thermostat (Eq. 39): collision rate (1/ps, 0 = off), temperature (K), noise seed
+  double lang_gamma = 0.0, lang_T = 0.0;
+  uint64_t lang_seed = 0;
+
   // counters
   int64_t launches = 0;
   int64_t mode_evals = 0;
@@ -248,6 +277,29 @@ enum {
   kScalEnergy = 4, kScalEii = 4, kScalEie = 5, kScalElj = 6, kScalEbond = 7, kScalEee = 8,
   kScalUF = 9, kScalQ2 = 10, kScalq2 = 11, kScalCount = 16
 };
+
+// ------------------------------------------------------------------------------------------------
+// Philox4x64-10 on the device (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 64x64->128
+// multiplications with the published multipliers and Weyl key increments
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x64_dev(uint64_t x0, uint64_t x1, uint64_t x2, uint64_t x3, uint64_t k0,
+                                               uint64_t k1, uint64_t out[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t hA = __umul64hi(0xD2E7470EE14C6C93ull, x0), lA = 0xD2E7470EE14C6C93ull * x0;
+    const uint64_t hB = __umul64hi(0xCA5A826395121157ull, x2), lB = 0xCA5A826395121157ull * x2;
+    x0 = hB ^ x1 ^ k0;
+    x1 = lB;
+    x2 = hA ^ x3 ^ k1;
+    x3 = lA;
+    k0 += 0x9E3779B97F4A7C15ull;
+    k1 += 0xBB67AE8584CAA73Bull;
+  }
+  out[0] = x0;
+  out[1] = x1;
+  out[2] = x2;
+  out[3] = x3;
+}
 
 // ------------------------------------------------------------------------------------------------
 // fixed-point phases and sin/cos
@@ -324,6 +376,10 @@ void steepest_descent_move(srbe_ctx *c, double a, double dmax);
 void build_A_and_inverse(srbe_ctx *c);
 void energy_scalars(srbe_ctx *c);
 enum Phase { kPhUpload = 0, kPhCells, kPhS1, kPhRhs, kPhSolve, kPhS2, kPhForces, kPhIntegrate, kPhEnergy, kPhCount };
+void lattice_setup(srbe_ctx *c, const std::vector<double> &x, const std::vector<double> &y,
+                   const std::vector<double> &z);
+void lattice_bfar(srbe_ctx *c);
+void lattice_s2(srbe_ctx *c, double2 *S, const double2 *S1, int mslot);
 void coop_before(srbe_ctx *c);
 void coop_after(srbe_ctx *c);
 cudaEvent_t device_coop_chain();

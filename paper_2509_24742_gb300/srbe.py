@@ -80,6 +80,9 @@ EXPORTS = {
     "srbe_mlp_train": ([_vp, _fp, _fp, _i64, _int, _int, ctypes.c_float, ctypes.c_float, _u64,
                         ctypes.POINTER(_dbl)], _int),
     "srbe_charge_residual": ([_vp, _dp], _int),
+    "srbe_set_thermostat": ([_vp, _dbl, _dbl, _u64], _int),
+    "srbe_set_lattice": ([_vp, _int], _int),
+    "srbe_lattice_info": ([_vp, _ip], _int),
     "srbe_set_skin": ([_vp, _dbl], _int),
     "srbe_get_skin": ([_vp], _dbl),
     "srbe_autotune_skin": ([_vp, _int, _u64, _dp, _int, _dp], _int),
@@ -347,6 +350,20 @@ class Context:
         a, b = _i64(), _i64()
         self._check(self.lib.srbe_get_counters(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def set_lattice(self, mode=1):
+        """Lattice-electrode transforms: 0 never, 1 when N_ele x K is large (default), 2 always."""
+        self._check(self.lib.srbe_set_lattice(self.h, int(mode)))
+
+    def lattice_info(self):
+        """(layers, nx, ny) of a recognised lattice electrode, else (0, 0, 0)."""
+        d = np.zeros(3, np.int32)
+        self._check(self.lib.srbe_lattice_info(self.h, d.ctypes.data_as(_ip)))
+        return tuple(int(v) for v in d)
+
+    def set_thermostat(self, gamma, T, seed=0):
+        """Langevin thermostat of the MD step (gamma in 1/ps, 0 = off; T in K)."""
+        self._check(self.lib.srbe_set_thermostat(self.h, float(gamma), float(T), int(seed)))
 
     def charge_residual(self):
         """FP64 relative residual of the constant-potential conditions met by the current charges."""

@@ -179,12 +179,26 @@ def place_electrolyte(rng, Lx, Ly, zlo, zhi, n_pairs, cation_sites, d_min, max_t
     return np.asarray(r), np.asarray(q), np.asarray(mol, np.int32), np.asarray(kind, np.int32)
 
 
-def place_electrolyte_lattice(rng, Lx, Ly, zlo, zhi, n_pairs, cation_sites):
+def _rotations(u):
+    """Rotation matrices from uniform triples (random unit quaternions, Shoemake's method)."""
+    a = np.sqrt(1 - u[:, 0]) * np.sin(2 * np.pi * u[:, 1])
+    b = np.sqrt(1 - u[:, 0]) * np.cos(2 * np.pi * u[:, 1])
+    c = np.sqrt(u[:, 0]) * np.sin(2 * np.pi * u[:, 2])
+    d = np.sqrt(u[:, 0]) * np.cos(2 * np.pi * u[:, 2])
+    return np.stack([np.stack([1 - 2 * (c * c + d * d), 2 * (b * c - a * d), 2 * (b * d + a * c)], -1),
+                     np.stack([2 * (b * c + a * d), 1 - 2 * (b * b + d * d), 2 * (c * d - a * b)], -1),
+                     np.stack([2 * (b * d - a * c), 2 * (c * d + a * b), 1 - 2 * (b * b + c * c)], -1)], -2)
+
+
+def place_electrolyte_lattice(rng, Lx, Ly, zlo, zhi, n_pairs, cation_sites, min_gap=0.08, rounds=50):
     """Fast placement for large replicas: one molecule per cell of a near-cubic grid filling the
     region (cells drawn at random when there are more cells than molecules), cation or anion at
-    random, centre jittered by up to 15 % of the cell, triangles randomly rotated.  Returns
-    (r, q, mol, kind, cell) like place_electrolyte plus the cell edge; neighbouring molecules can
-    start closer than in RSA, which the capped steepest-descent relaxation before MD removes."""
+    random, centre jittered by up to 15 % of the cell, triangles randomly rotated; molecules with a
+    site closer than `min_gap` nm to a site of another molecule draw a new jitter and rotation
+    (up to `rounds` times).  Returns (r, q, mol, kind, cell) like place_electrolyte plus the cell
+    edge; neighbouring molecules start closer than in RSA, which the capped steepest-descent
+    relaxation before MD removes."""
+    from scipy.spatial import cKDTree
     n_mol = 2 * n_pairs
     h = zhi - zlo
     c = (Lx * Ly * h / n_mol) ** (1.0 / 3.0)
@@ -193,39 +207,42 @@ def place_electrolyte_lattice(rng, Lx, Ly, zlo, zhi, n_pairs, cation_sites):
     cx, cy, cz = Lx / nx, Ly / ny, h / nz
     cells = rng.permutation(nx * ny * nz)[:n_mol]
     ix, iy, iz = cells % nx, (cells // nx) % ny, cells // (nx * ny)
-    centre = np.c_[(ix + 0.5) * cx, (iy + 0.5) * cy, zlo + (iz + 0.5) * cz]
-    centre += rng.uniform(-0.15, 0.15, size=(n_mol, 3)) * np.array([cx, cy, cz])
+    base = np.c_[(ix + 0.5) * cx, (iy + 0.5) * cy, zlo + (iz + 0.5) * cz]
     is_cat = np.zeros(n_mol, bool)
     is_cat[rng.permutation(n_mol)[:n_pairs]] = True
+    tri_mol = is_cat & (cation_sites == 3)
+    nsite = np.where(tri_mol, 3, 1)
+    first = np.concatenate([[0], np.cumsum(nsite)[:-1]])
+    mol = np.repeat(np.arange(n_mol), nsite).astype(np.int32)
+    kind = np.concatenate([[0, 1, 2] if t else ([0] if k else [3]) for t, k in zip(tri_mol, is_cat)]).astype(np.int32)
+    q = np.where(kind == 3, -0.78, np.where(np.repeat(tri_mol, nsite), 0.26, 0.78))
     side_len = 0.35
     circ = side_len / math.sqrt(3.0)
     tri = np.array([[circ, 0.0, 0.0], [-0.5 * circ, 0.5 * side_len, 0.0], [-0.5 * circ, -0.5 * side_len, 0.0]])
-    r, q, mol, kind = [], [], [], []
-    # random rotations for every cation (uniform quaternions)
-    u = rng.uniform(size=(n_mol, 3))
-    qa = np.c_[np.sqrt(1 - u[:, 0]) * np.sin(2 * np.pi * u[:, 1]), np.sqrt(1 - u[:, 0]) * np.cos(2 * np.pi * u[:, 1]),
-               np.sqrt(u[:, 0]) * np.sin(2 * np.pi * u[:, 2]), np.sqrt(u[:, 0]) * np.cos(2 * np.pi * u[:, 2])]
-    for m in range(n_mol):
-        if is_cat[m] and cation_sites == 3:
-            a, b, cc, d = qa[m]
-            rot = np.array([[1 - 2 * (cc * cc + d * d), 2 * (b * cc - a * d), 2 * (b * d + a * cc)],
-                            [2 * (b * cc + a * d), 1 - 2 * (b * b + d * d), 2 * (cc * d - a * b)],
-                            [2 * (b * d - a * cc), 2 * (cc * d + a * b), 1 - 2 * (b * b + cc * cc)]])
-            sites = centre[m] + tri @ rot.T
-            r.extend(sites)
-            q.extend([0.26, 0.26, 0.26])
-            kind.extend([0, 1, 2])
-            mol.extend([m, m, m])
-        else:
-            r.append(centre[m])
-            q.append(0.78 if is_cat[m] else -0.78)
-            kind.append(0 if is_cat[m] else 3)
-            mol.append(m)
-    r = np.asarray(r)
-    r[:, 0] %= Lx
-    r[:, 1] %= Ly
-    r[:, 2] = np.clip(r[:, 2], zlo, zhi)
-    return r, np.asarray(q), np.asarray(mol, np.int32), np.asarray(kind, np.int32), min(cx, cy, cz)
+    r = np.empty((int(nsite.sum()), 3))
+
+    def draw(ms):
+        centre = base[ms] + rng.uniform(-0.15, 0.15, size=(ms.size, 3)) * np.array([cx, cy, cz])
+        rot = _rotations(rng.uniform(size=(ms.size, 3)))
+        t3 = tri_mol[ms]
+        pts = centre[t3][:, None, :] + np.einsum("sd,med->mse", tri, rot[t3])
+        r[(first[ms[t3]][:, None] + np.arange(3)).ravel()] = pts.reshape(-1, 3)
+        r[first[ms[~t3]]] = centre[~t3]
+        idx = np.concatenate([(first[ms[t3]][:, None] + np.arange(3)).ravel(), first[ms[~t3]]])
+        r[idx, 0] %= Lx
+        r[idx, 1] %= Ly
+        r[idx, 2] = np.clip(r[idx, 2], zlo, zhi)
+
+    draw(np.arange(n_mol))
+    for _ in range(rounds):
+        tree = cKDTree(np.c_[r[:, :2], r[:, 2] - zlo + 1.0], boxsize=[Lx, Ly, 1e6])
+        pairs = tree.query_pairs(min_gap, output_type="ndarray")
+        if pairs.size:
+            pairs = pairs[mol[pairs[:, 0]] != mol[pairs[:, 1]]]
+        if not pairs.size:
+            break
+        draw(np.unique(mol[pairs[:, 1]]))
+    return r, q, mol, kind, min(cx, cy, cz)
 
 
 def maxwell_velocities(rng, mass, T):
@@ -299,19 +316,25 @@ def md_11072(seed=1002):
 
 def precision_100k(seed=1003, dpsi_volt=2.0):
     """Precision-form case: 8 x 8 x 32 nm, 2 x 3 layers of 64 x 32 (12,288 sites), 21,928 cation/anion
-    pairs (87,712 sites), P=500, 0-4 V."""
-    return make_slab("prec100k_P500", (8.0, 8.0, 32.0), 64, 32, 21928, 3, alpha=3.5, eta_inv=19.79, rc=1.2,
-                     P=500, M=4, dpsi_volt=dpsi_volt, seed=seed, with_md=True)
+    pairs (87,712 sites), P=500, 0-4 V.  alpha = 1.87 nm^-1 and rc = 1.6 nm, the paper's values for
+    its own slab (§4): with alpha = 3.5 nm^-1 the sampled modes cover too small a share of this box's
+    Fourier weight and the random-batch charge noise exceeds the charges tenfold.  Ions on the
+    jittered grid (place_electrolyte_lattice): RSA at this size takes minutes."""
+    return make_slab("prec100k_P500", (8.0, 8.0, 32.0), 64, 32, 21928, 3, alpha=1.87, eta_inv=19.79, rc=1.6,
+                     P=500, M=4, dpsi_volt=dpsi_volt, seed=seed, with_md=True, placement="lattice")
 
 
 def batch_replicas(n=64, seed=1004, n_total=(5000, 60000), sides=(16, 20, 24, 28, 32), aspect=(3.0, 8.0),
-                   rho=50.0, P_choices=(100, 150, 200, 250, 300, 350, 400)):
+                   rho=50.0, P_range=(100, 400), alpha=1.87, rc=1.6):
     """Uneven replicas for the batching form: per replica an s x s lattice per layer at 0.25 nm
     (s from `sides`, so 1,536-6,144 electrode sites and Lx = Ly = s / 4 nm), a total particle count
     drawn from `n_total`, the electrolyte (3-site cations, 1-site anions) at `rho` sites per nm^3
     between the walls, Lz / Lx kept in `aspect` (the ion count follows when the aspect clamps),
-    P from `P_choices`, a voltage 0-4 V in 0.0625 V steps and a seed of its own.  Placement on a
-    jittered grid (place_electrolyte_lattice) keeps generation fast at millions of sites."""
+    a voltage 0-4 V in 0.0625 V steps and a seed of its own.  P grows with the box volume V:
+    50 ceil(V / 250 nm^3) clamped to `P_range` (a larger box spreads the same Fourier weight over
+    more modes, and a fixed P would leave the charge noise growing with it).  alpha and rc are the
+    paper's (§4).  Placement on a jittered grid (place_electrolyte_lattice) keeps generation fast at
+    millions of sites."""
     rng = np.random.Generator(np.random.Philox(seed))
     out = []
     gap = 2 * (2 * LAYER_DZ + WALL_GAP)
@@ -325,10 +348,10 @@ def batch_replicas(n=64, seed=1004, n_total=(5000, 60000), sides=(16, 20, 24, 28
         Lz = a * L
         h = Lz / 1.5 - gap
         n_pairs = max(50, int(rho * L * L * h / 4))
-        P = int(P_choices[rng.integers(len(P_choices))])
+        P = int(min(P_range[1], max(P_range[0], 50 * math.ceil(L * L * Lz / 250.0))))
         dpsi = 0.0625 * int(rng.integers(0, 65))
-        out.append(make_slab("replica%d_s%d_P%d" % (i, s, P), (L, L, Lz), s, s, n_pairs, 3, alpha=3.5,
-                             eta_inv=19.79, rc=1.2, P=P, M=None, dpsi_volt=dpsi, seed=seed * 1000 + i,
+        out.append(make_slab("replica%d_s%d_P%d" % (i, s, P), (L, L, Lz), s, s, n_pairs, 3, alpha=alpha,
+                             eta_inv=19.79, rc=rc, P=P, M=None, dpsi_volt=dpsi, seed=seed * 1000 + i,
                              with_md=True, placement="lattice"))
     return out
 

@@ -1,0 +1,51 @@
+"""Checks at the full size of the precision-form slab (8 x 8 x 32 nm, 12,288 electrode sites,
+87,712 ion sites, P = 500): the oracle cannot solve for the charges at this size, so the test
+compares sampled outputs it can compute one by one (b on sampled electrode sites, electrostatic
+forces on sampled ions for the charges the GPU found) and checks properties that hold at any size
+(neutrality, the FP64 residual of the constant-potential conditions, the mixed form against FP64)."""
+import numpy as np
+import pytest
+
+from paper_2509_24742_gb300 import srbe, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def big():
+    return wl.precision_100k()
+
+
+def test_precision_100k_sampled_parity_and_properties(orc, big):
+    L = big.box
+    samples = orc.sample_metropolis(L, big.alpha, big.M, big.P, 5003, 0)
+    m, c = orc.srbe_modes(L, big.alpha, big.M, samples, orc.G_closed(L, big.alpha, big.M))
+    with srbe.from_slab(big, precision=srbe.FP64) as ctx:
+        assert ctx.lattice_info() == (6, 64, 32)
+        ctx.set_k(samples)
+        F, Q, psi = ctx.forces()
+        _, _, b = ctx.solve_charges()
+        res64 = ctx.charge_residual()
+        ctx.set_lattice(0)                      # the plain per-site sums at the same size
+        F0, Q0, _ = ctx.forces()
+        ctx.set_lattice(1)
+        ctx.set_precision(srbe.MIXED)
+        F32, Q32, _ = ctx.forces()
+        res32 = ctx.charge_residual()
+    assert res64 < 1e-11 and res32 < 1e-9
+    assert abs(Q.sum()) < 1e-10 * np.abs(Q).sum()
+    assert rel(F, F0) < 1e-11 and rel(Q, Q0) < 1e-11
+    rng = np.random.default_rng(0)
+    sites = np.sort(rng.choice(big.n_ele, 48, replace=False))
+    ions = np.sort(rng.choice(big.n_ion, 48, replace=False))
+    assert rel(b[sites] * srbe.VOLT, orc.sampled_b(big, m, c, sites)) < 1e-10
+    assert rel(F[ions], orc.sampled_forces(big, m, c, Q, ions)) < 1e-10
+    rms_f = np.sqrt(((F32 - F) ** 2).sum(1).mean() / (F ** 2).sum(1).mean())
+    rms_q = np.sqrt(((Q32 - Q) ** 2).mean() / (Q ** 2).mean())
+    print("100k slab: FP64 residual %.2e, mixed residual %.2e, mixed RMS force err %.2e, charge err %.2e"
+          % (res64, res32, rms_f, rms_q))
+    assert rms_f < 1e-3 and rms_q < 1e-4

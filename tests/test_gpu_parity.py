@@ -138,9 +138,11 @@ def test_errors_are_reported(slab784):
         assert e.value.code == srbe.SRBE_EINVAL
 
 
-def test_md_steps_match_oracle(orc):
-    """Algorithm 1 with velocity Verlet: a few steps of the MD slab (3-site cations, LJ, bonds)
-    on a reduced copy, with the mode list of each step drawn by the oracle's own sampler."""
+@pytest.mark.parametrize("thermostat", [None, (5.0, 400.0, 17)])
+def test_md_steps_match_oracle(orc, thermostat):
+    """Algorithm 1 with velocity Verlet (and optionally the Langevin thermostat of Eq. 39): a few
+    steps of the MD slab (3-site cations, LJ, bonds) on a reduced copy, with the mode list of each
+    step drawn by the oracle's own sampler and the thermostat noise by the oracle's own generator."""
     s = wl.make_slab("md_small", (2.0, 2.0, 12.0), 8, 8, 60, 3, alpha=3.5, eta_inv=19.79, rc=1.2, P=50, M=2,
                      dpsi_volt=1.0, seed=21, ax=0.25, ay=0.25, with_md=True)
     seed, nsteps = 77, 4
@@ -150,9 +152,11 @@ def test_md_steps_match_oracle(orc):
     F = orc.evaluate(ref.at(r), ref.factor, m, c)["F"]
     for step in range(1, nsteps + 1):
         m, c = ref.modes(orc.sample_metropolis(s.box, s.alpha, s.M, s.P, seed, step))
-        r, v, ev = ref.md_step(r, v, F, m, c)
+        r, v, ev = ref.md_step(r, v, F, m, c, thermostat=thermostat, step=step)
         F = ev["F"]
     with gpu_ctx(s, md=True) as ctx:
+        if thermostat:
+            ctx.set_thermostat(*thermostat)
         ctx.step(nsteps, seed)
         rg, vg = ctx.get_positions(velocities=True)
     d = rg - r
@@ -161,9 +165,11 @@ def test_md_steps_match_oracle(orc):
     assert rel(vg, v) < 1e-8
 
 
-@pytest.mark.parametrize("precision,solver", [(srbe.FP64, srbe.DIRECT), (srbe.MIXED, srbe.DIRECT),
-                                              (srbe.MIXED, srbe.PCG)])
-def test_graph_replay_is_bitwise_the_ordinary_path(precision, solver):
+@pytest.mark.parametrize("precision,solver,thermo,lattice", [(srbe.FP64, srbe.DIRECT, 0.0, 0),
+                                                             (srbe.MIXED, srbe.DIRECT, 5.0, 0),
+                                                             (srbe.MIXED, srbe.PCG, 0.0, 0),
+                                                             (srbe.FP64, srbe.DIRECT, 5.0, 2)])
+def test_graph_replay_is_bitwise_the_ordinary_path(precision, solver, thermo, lattice):
     """srbe_step replaying its captured CUDA graphs gives bitwise the trajectory of the ordinary
     launch path, across several calls, a read-back in between and a state change that recaptures."""
     s = wl.make_slab("md_small", (2.0, 2.0, 12.0), 8, 8, 60, 3, alpha=3.5, eta_inv=19.79, rc=1.2, P=50, M=2,
@@ -172,6 +178,8 @@ def test_graph_replay_is_bitwise_the_ordinary_path(precision, solver):
     for graphs in (False, True):
         with srbe.from_slab(s, precision=precision, alpha_A=ALPHA_A, md=True) as ctx:
             ctx.set_graphs(graphs)
+            ctx.set_thermostat(thermo, 400.0, 5)
+            ctx.set_lattice(lattice)
             if solver == srbe.PCG:
                 ctx.set_solver(srbe.PCG, tol=1e-10, maxit=500, warm=srbe.WARM_PREVIOUS)
             ctx.step(3, 91)
