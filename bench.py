@@ -44,6 +44,7 @@ DT_NS = 2e-6                        # 2 fs
 SEED = 3002
 N_MIN = 100
 N_MIN_BATCH = 200
+SKINS = (0.06, 0.08, 0.1, 0.13, 0.16)
 GAMMA, T_BATH = 50.0, 400.0         # Langevin thermostat of the MD step (1/ps, K)
 KB = 0.0083144626
 FLUSH_BYTES = 256 << 20             # larger than the 129 MB L2
@@ -216,6 +217,9 @@ def gpu_arm(args, rank, world):
     rms_f = float(np.sqrt(((F32 - F64) ** 2).sum(1).mean() / (F64 ** 2).sum(1).mean()))
     rms_q = float(np.sqrt(((Q32 - Q64) ** 2).mean() / (Q64 ** 2).mean()))
     head = "mixed" if rms_f <= 1e-3 else "fp64"
+    # untimed set-up: the Verlet skin of the headline form picked by timing (state restored after)
+    skin_ms = ctxs[head].autotune_skin(20, SEED, skins=SKINS)
+    skin = ctxs[head].skin()
 
     def timed(ctx, steps, warm, traced=False):
         """Device time of `steps` MD steps, each bracketed by CUDA events on the context's stream,
@@ -293,6 +297,8 @@ def gpu_arm(args, rank, world):
         "accuracy": {"rms_force_err_vs_fp64_gpu": rms_f, "rms_charge_err_vs_fp64_gpu": rms_q},
         "roofline": roof,
         "phases_ms_per_step": {p: round(v, 5) for p, v in per_step.items()},
+        "verlet_skin_nm": {"chosen": skin, "autotune_ms_per_step": {str(k): round(v, 5) for k, v in
+                                                                                 skin_ms.items()}},
         "launch": {"timed_steps": "CUDA-graph replay, one graph launch per step" if graph_state[0] == 1
                    else "ordinary launches", "kernels_per_step": graph_state[1] or None,
                    "traced_pass": {"steps": n_trace, "steps_per_s": n_trace / (ms_trace * 1e-3),

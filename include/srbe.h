@@ -248,7 +248,8 @@ int srbe_lattice_info(srbe_ctx *ctx, int32_t dims[3]);
  * srbe_step applies its exact Ornstein-Uhlenbeck solution over each step after the closing half
  * kick: v <- c1 v + sqrt((1 - c1^2) kB T / m) g, c1 = exp(-gamma dt), g standard normal from
  * Philox4x64-10 with key (seed, 0x4C414E47) and counter (step, ion, 0, 0) through Box-Muller (the
- * same numbers as any other implementation of that recipe).  gamma = 0 (the default) is plain
+ * same numbers as any other implementation of that recipe; the mixed form takes the top 24 bits of
+ * the same words as FP32 uniforms and transforms them in FP32).  gamma = 0 (the default) is plain
  * velocity Verlet.  Errors: SRBE_EINVAL for negative or non-finite gamma or T. */
 int srbe_set_thermostat(srbe_ctx *ctx, double gamma, double T, uint64_t seed);
 int srbe_set_skin(srbe_ctx *ctx, double skin);

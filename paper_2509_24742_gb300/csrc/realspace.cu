@@ -399,12 +399,15 @@ struct MdDev {
 struct PairSite {
   double X, Y, Z, qi, Lx, Ly, alpha, eta, rc2;
   float Xf, Yf, Zf, qf, Lxf, Lyf, af, etaf;
+  float qke;                          // K_E q_i (FP32 form: Coulomb folded into kJ/mol/nm)
   int ti, mi;
   int64_t p;
 };
 
+// FP32 form: one plain sum per component of K_E x Coulomb + LJ (each lane adds ~20 terms, then a
+// warp tree; errors stay near 1e-6 of the largest term, far inside the form's 1e-3 budget)
 struct PairAcc {
-  KahanF32 c0, c1, c2, l0, l1, l2;   // FP32 form: Coulomb (Gaussian units) and LJ
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f;
   float eii = 0.f, eie = 0.f, elj = 0.f;
   double r[3] = {0, 0, 0}, l[3] = {0, 0, 0};   // FP64 form
   double dii = 0, die = 0, dlj = 0;
@@ -414,7 +417,7 @@ __device__ __forceinline__ int pack_image(int ix, int iy) { return (ix + 512) | 
 __device__ __forceinline__ int image_x(int v) { return (v & 1023) - 512; }
 __device__ __forceinline__ int image_y(int v) { return ((v >> 10) & 1023) - 512; }
 
-template <bool F32>
+template <bool F32, bool EN>
 __device__ __forceinline__ void pair_ion_ion(const PairSite &S, const CellsDev &ions, const MdDev &md, int2 e,
                                              PairAcc &A) {
   const int pp = e.x, ix = image_x(e.y), iy = image_y(e.y);
@@ -425,20 +428,17 @@ __device__ __forceinline__ void pair_ion_ion(const PairSite &S, const CellsDev &
     const float r2 = dx * dx + dy * dy + dz * dz;
     float phi, md2;
     pair_ii_f(r2, S.af, phi, md2);
-    const float qq = S.qf * o.w, s = qq * md2;
-    A.c0.add(s * dx);
-    A.c1.add(s * dy);
-    A.c2.add(s * dz);
-    A.eii += 0.5f * qq * phi;
+    float fs = S.qke * o.w * md2;
+    if (EN) A.eii += 0.5f * S.qf * o.w * phi;
     if (lj) {
       const float2 sg = md.lj32[S.ti * md.ntype + ions.ts[pp]];
       const float ir2 = __frcp_rn(r2), sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
-      const float fs = 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
-      A.l0.add(fs * dx);
-      A.l1.add(fs * dy);
-      A.l2.add(fs * dz);
-      A.elj += 2.f * sg.y * (sr6 * sr6 - sr6);
+      fs += 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
+      if (EN) A.elj += 2.f * sg.y * (sr6 * sr6 - sr6);
     }
+    A.f0 = fmaf(fs, dx, A.f0);
+    A.f1 = fmaf(fs, dy, A.f1);
+    A.f2 = fmaf(fs, dz, A.f2);
   } else {
     const double dx = S.X - (ions.xs[pp] + ix * S.Lx), dy = S.Y - (ions.ys[pp] + iy * S.Ly), dz = S.Z - ions.zs[pp];
     const double r2 = dx * dx + dy * dy + dz * dz;
@@ -449,7 +449,7 @@ __device__ __forceinline__ void pair_ion_ion(const PairSite &S, const CellsDev &
     A.r[0] = fma(s, dx, A.r[0]);
     A.r[1] = fma(s, dy, A.r[1]);
     A.r[2] = fma(s, dz, A.r[2]);
-    A.dii = fma(0.5 * qq, phi, A.dii);
+    if (EN) A.dii = fma(0.5 * qq, phi, A.dii);
     if (lj) {
       const double2 sg = md.lj[S.ti * md.ntype + ions.ts[pp]];
       const double sr2 = sg.x / r2, sr6 = sr2 * sr2 * sr2;
@@ -457,12 +457,12 @@ __device__ __forceinline__ void pair_ion_ion(const PairSite &S, const CellsDev &
       A.l[0] = fma(fs, dx, A.l[0]);
       A.l[1] = fma(fs, dy, A.l[1]);
       A.l[2] = fma(fs, dz, A.l[2]);
-      A.dlj += 0.5 * 4.0 * sg.y * (sr6 * sr6 - sr6);
+      if (EN) A.dlj += 0.5 * 4.0 * sg.y * (sr6 * sr6 - sr6);
     }
   }
 }
 
-template <bool F32>
+template <bool F32, bool EN>
 __device__ __forceinline__ void pair_ion_ele(const PairSite &S, const CellsDev &eles, const MdDev &md,
                                              const double *__restrict__ Q, const float *__restrict__ Q32, int2 e,
                                              PairAcc &A) {
@@ -474,20 +474,17 @@ __device__ __forceinline__ void pair_ion_ele(const PairSite &S, const CellsDev &
     const float Qj = Q32[eles.order[pe]];
     float phi, md2;
     pair_ie_f(r2, S.af, S.etaf, phi, md2);
-    const float s = S.qf * Qj * md2;
-    A.c0.add(s * dx);
-    A.c1.add(s * dy);
-    A.c2.add(s * dz);
-    A.eie += S.qf * Qj * phi;
+    float fs = S.qke * Qj * md2;
+    if (EN) A.eie += S.qf * Qj * phi;
     if (md.ntype) {
       const float2 sg = md.lj32[S.ti * md.ntype + (md.ntype - 1)];
       const float ir2 = __frcp_rn(r2), sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
-      const float fs = 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
-      A.l0.add(fs * dx);
-      A.l1.add(fs * dy);
-      A.l2.add(fs * dz);
-      A.elj += 4.f * sg.y * (sr6 * sr6 - sr6);
+      fs += 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
+      if (EN) A.elj += 4.f * sg.y * (sr6 * sr6 - sr6);
     }
+    A.f0 = fmaf(fs, dx, A.f0);
+    A.f1 = fmaf(fs, dy, A.f1);
+    A.f2 = fmaf(fs, dz, A.f2);
   } else {
     const double dx = S.X - (eles.xs[pe] + ix * S.Lx), dy = S.Y - (eles.ys[pe] + iy * S.Ly), dz = S.Z - eles.zs[pe];
     const double r2 = dx * dx + dy * dy + dz * dz;
@@ -499,7 +496,7 @@ __device__ __forceinline__ void pair_ion_ele(const PairSite &S, const CellsDev &
     A.r[0] = fma(s, dx, A.r[0]);
     A.r[1] = fma(s, dy, A.r[1]);
     A.r[2] = fma(s, dz, A.r[2]);
-    A.die = fma(S.qi * Qj, phi, A.die);
+    if (EN) A.die = fma(S.qi * Qj, phi, A.die);
     if (md.ntype) {
       const double2 sg = md.lj[S.ti * md.ntype + (md.ntype - 1)];
       const double sr2 = sg.x / r2, sr6 = sr2 * sr2 * sr2;
@@ -507,7 +504,7 @@ __device__ __forceinline__ void pair_ion_ele(const PairSite &S, const CellsDev &
       A.l[0] = fma(fs, dx, A.l[0]);
       A.l[1] = fma(fs, dy, A.l[1]);
       A.l[2] = fma(fs, dz, A.l[2]);
-      A.dlj += 4.0 * sg.y * (sr6 * sr6 - sr6);
+      if (EN) A.dlj += 4.0 * sg.y * (sr6 * sr6 - sr6);
     }
   }
 }
@@ -776,15 +773,17 @@ __device__ __forceinline__ int build_list(const NbrKernelArgs &a, const int4 *ru
   return count;
 }
 
-__global__ void __launch_bounds__(256) k_neighbor_update(NbrKernelArgs a) {
-  cg::grid_group grid = cg::this_grid();
-  __shared__ int32_t part[256];
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid, gsize = (int64_t)gridDim.x * blockDim.x;
-  const int64_t gwarp = gtid >> 5, nwarps = gsize >> 5;
-  const int forced = __ldcg(&a.flag[1]);
-  // ---- phase 0: refresh + displacement test
-  if (!forced) {
+// Every step: the sorted copies follow the ions (unwrapped against the build positions, so the
+// lists' image shifts stay valid) and any ion that moved more than skin / 2 since the build raises
+// flag[0]; a forced rebuild (flag[1]) skips the refresh and raises flag[0] itself.
+__global__ void __launch_bounds__(256) k_nbr_refresh(NbrKernelArgs a) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (__ldcg(&a.flag[1])) {
+    if (gtid == 0) a.flag[0] = 1;
+    return;
+  }
+  {
+    const int64_t gsize = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = gtid; p < a.n; p += gsize) {
       const int32_t i = a.order[p];
       double dx = a.x[i] - a.xb[p], dy = a.y[i] - a.yb[p];
@@ -802,11 +801,18 @@ __global__ void __launch_bounds__(256) k_neighbor_update(NbrKernelArgs a) {
       const float ex = (float)X - b.x, ey = (float)Y - b.y, ez = (float)Z - b.z;
       if (ex * ex + ey * ey + ez * ez > a.half_skin2) atomicOr(&a.flag[0], 1);
     }
-  } else if (gtid == 0) {
-    atomicOr(&a.flag[0], 1);
   }
-  grid.sync();
-  // one L2 read of the flag per block (a grid-wide atomic read serialises), uniform over the grid
+}
+
+// The rebuild, one cooperative launch whose phases are separated by grid-wide barriers.  The
+// decision (flag[0], final once k_nbr_refresh has run) is read once per block and is the same for
+// every block, so without a rebuild the whole grid returns before its first barrier.
+__global__ void __launch_bounds__(256) k_neighbor_update(NbrKernelArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ int32_t part[256];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid, gsize = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gwarp = gtid >> 5, nwarps = gsize >> 5;
   __shared__ int s_rebuild;
   if (tid == 0) s_rebuild = __ldcg(&a.flag[0]);
   __syncthreads();
@@ -995,11 +1001,13 @@ void neighbor_update(srbe_ctx *c) {
   }
   const int want = (int)std::max<int64_t>(1, std::min<int64_t>((std::max<int64_t>(n, c->ne) * 32 + 255) / 256,
                                                                  (int64_t)blocks_per_sm * nsm));
+  k_nbr_refresh<<<blocks_for(std::max<int64_t>(n, 1), 256), 256, 0, c->stream>>>(a);
+  SRBE_CUDA(cudaGetLastError());
   void *args[] = {&a};
   coop_before(c);
   SRBE_CUDA(cudaLaunchCooperativeKernel((const void *)k_neighbor_update, dim3(want), dim3(256), args, 0, c->stream));
   coop_after(c);
-  c->launches++;
+  c->launches += 2;
 }
 
 void electrode_rhs(srbe_ctx *c) {
@@ -1037,7 +1045,7 @@ void electrode_rhs(srbe_ctx *c) {
 
 // coefF[k] = (c_k Im S(k), c_k Re S(k)) with S = S1 + S2;
 // F_i = - q_i sum_k c_k k Im(S exp(-i k . r_i)) = - q_i sum_k k (cIm cos - cRe sin)   (Eq. 25)
-template <bool F32>
+template <bool F32, bool EN>
 __global__ void __launch_bounds__(kGatherThreads)
 k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double *__restrict__ Q,
              const float *__restrict__ Q32,
@@ -1061,7 +1069,7 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     const double tpx = 2.0 * kPi * invL.x, tpy = 2.0 * kPi * invL.y, tpz = 2.0 * kPi * invL.z;
     // ---- k-space gather
     double fk[3] = {0, 0, 0};
-    KahanF32 ak0, ak1, ak2;
+    float ak0 = 0.f, ak1 = 0.f, ak2 = 0.f;
     if (!F32) {
       for (int k = lane; k < K; k += 32) {
         const int4 m = __ldg(&modes[k]);
@@ -1081,9 +1089,9 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
         sincos_turns32((uint32_t)m.x * vx + (uint32_t)m.y * vy + (uint32_t)m.z * vz, cs, sn);
         const float2 cf = __ldg(&coefF32[k]);
         const float im = cf.x * cs - cf.y * sn;
-        ak0.add(kvf.x * (float)m.x * im);
-        ak1.add(kvf.y * (float)m.y * im);
-        ak2.add(kvf.z * (float)m.z * im);
+        ak0 = fmaf((float)m.x, im, ak0);
+        ak1 = fmaf((float)m.y, im, ak1);
+        ak2 = fmaf((float)m.z, im, ak2);
       }
     }
     // ---- real space: Coulomb of Eq. 13 (Gaussian units) and LJ (kJ/mol/nm), compacted pairs
@@ -1092,6 +1100,7 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     const float4 self = ions.pf[p];
     S.Xf = self.x; S.Yf = self.y; S.Zf = self.z; S.qf = self.w;
     S.Lxf = (float)Lx; S.Lyf = (float)Ly; S.af = (float)alpha; S.etaf = (float)eta;
+    S.qke = (float)kKe * self.w;
     S.ti = ti; S.mi = mi; S.p = p;
     const float rcf = (float)rc;
     const float cut2 = F32 ? rcf * rcf : (rcf + kPrecheckMargin) * (rcf + kPrecheckMargin);
@@ -1101,38 +1110,36 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     const int nii = nl.ii_n[p], nie = nl.ie_n[p];
     if (nii <= nl.cap)
       compacted_list(S, ions, nl.ii + p * nl.cap, nii, cut2, q, lane,
-                     [&](int2 e) { pair_ion_ion<F32>(S, ions, md, e, A); });
+                     [&](int2 e) { pair_ion_ion<F32, EN>(S, ions, md, e, A); });
     else
       compacted_pairs(S, ions, nl.cell_s[p], true, cut2, q, lane,
-                      [&](int2 e) { pair_ion_ion<F32>(S, ions, md, e, A); });
+                      [&](int2 e) { pair_ion_ion<F32, EN>(S, ions, md, e, A); });
     if (nie <= nl.cap)
       compacted_list(S, eles, nl.ie + p * nl.cap, nie, cut2, q, lane,
-                     [&](int2 e) { pair_ion_ele<F32>(S, eles, md, Q, Q32, e, A); });
+                     [&](int2 e) { pair_ion_ele<F32, EN>(S, eles, md, Q, Q32, e, A); });
     else
       compacted_pairs(S, eles, nl.cell_s[p], false, cut2, q, lane,
-                      [&](int2 e) { pair_ion_ele<F32>(S, eles, md, Q, Q32, e, A); });
+                      [&](int2 e) { pair_ion_ele<F32, EN>(S, eles, md, Q, Q32, e, A); });
     const float Xf = S.Xf, Yf = S.Yf, Zf = S.Zf, qf = S.qf;
     double rr[3] = {A.r[0], A.r[1], A.r[2]}, ll[3] = {A.l[0], A.l[1], A.l[2]};
     e_ii = A.dii;
     e_ie = A.die;
     e_lj = A.dlj;
     float eii = A.eii, eie = A.eie, elj = A.elj;
-    KahanF32 &ka0 = A.c0, &ka1 = A.c1, &ka2 = A.c2, &ka3 = A.l0, &ka4 = A.l1, &ka5 = A.l2;
     if (F32) {
       // FP32 to the end: sums, warp reductions, bonds and the force assembly; only M_z (an FP64
       // reduction over all charges) enters from FP64
-      float v[9] = {ak0.valuef(), ak1.valuef(), ak2.valuef(), ka0.valuef(), ka1.valuef(), ka2.valuef(),
-                    ka3.valuef(), ka4.valuef(), ka5.valuef()};
+      float v[6] = {ak0, ak1, ak2, A.f0, A.f1, A.f2};
 #pragma unroll
-      for (int d = 0; d < 9; ++d) v[d] = warp_sum_f(v[d]);
-      if (epart) {
+      for (int d = 0; d < 6; ++d) v[d] = warp_sum_f(v[d]);
+      if (EN) {
         eii = warp_sum_f(eii);
         eie = warp_sum_f(eie);
         elj = warp_sum_f(elj);
       }
       if (lane == 0) {
         const float Mz = (float)(scal[kScalMion] + scal[kScalMele]);
-        float Fx = -qf * v[0], Fy = -qf * v[1], Fz = -qf * v[2] - (float)slab * qf * Mz;
+        float Fx = -qf * kvf.x * v[0], Fy = -qf * kvf.y * v[1], Fz = -qf * kvf.z * v[2] - (float)slab * qf * Mz;
         float bx = 0.f, by = 0.f, bz = 0.f, eb = 0.f;
         if (md.ntype && md.bond_start) {
           const float Lxf = (float)Lx, Lyf = (float)Ly, kbf = (float)md.kb;
@@ -1151,9 +1158,9 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
           }
         }
         const float ke = (float)kKe;
-        F[i] = (double)(ke * (Fx + v[3]) + v[6] + bx);
-        F[ni + i] = (double)(ke * (Fy + v[4]) + v[7] + by);
-        F[2 * ni + i] = (double)(ke * (Fz + v[5]) + v[8] + bz);
+        F[i] = (double)(ke * Fx + v[3] + bx);
+        F[ni + i] = (double)(ke * Fy + v[4] + by);
+        F[2 * ni + i] = (double)(ke * Fz + v[5] + bz);
         e_ii = eii;
         e_ie = eie;
         e_lj = elj;
@@ -1165,7 +1172,7 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
         rr[d] = warp_sum(rr[d]);
         ll[d] = warp_sum(ll[d]);
       }
-      if (epart) {
+      if (EN) {
         e_ii = warp_sum(e_ii);
         e_ie = warp_sum(e_ie);
         e_lj = warp_sum(e_lj);
@@ -1197,7 +1204,7 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
       }
     }
   }
-  if (epart) {
+  if (EN && epart) {
     if (lane == 0) {
       red[warp][0] = e_ii;
       red[warp][1] = e_ie;
@@ -1276,14 +1283,12 @@ void ion_forces(srbe_ctx *c, bool energies) {
     ions.ms = nullptr;
   }
   if (c->ni > 0) {
-    if (c->precision == SRBE_MIXED)
-      k_ion_forces<true><<<nblk, kGatherThreads, 0, c->stream>>>(
-          c->ni, ions, eles, lists_dev(c), c->Q.p, c->Q32.p, K, c->dm.p, coef, c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta, c->rc,
-          slab, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep);
-    else
-      k_ion_forces<false><<<nblk, kGatherThreads, 0, c->stream>>>(
-          c->ni, ions, eles, lists_dev(c), c->Q.p, c->Q32.p, K, c->dm.p, coef, c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta, c->rc,
-          slab, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep);
+    const bool mixed = c->precision == SRBE_MIXED;
+    auto kern = mixed ? (energies ? k_ion_forces<true, true> : k_ion_forces<true, false>)
+                      : (energies ? k_ion_forces<false, true> : k_ion_forces<false, false>);
+    kern<<<nblk, kGatherThreads, 0, c->stream>>>(c->ni, ions, eles, lists_dev(c), c->Q.p, c->Q32.p, K, c->dm.p, coef,
+                                                 c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta,
+                                                 c->rc, slab, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep);
     c->launches++;
     c->mode_evals += c->ni * (int64_t)K;
   }
@@ -1312,6 +1317,7 @@ void ion_forces(srbe_ctx *c, bool energies) {
 // so that a replayed graph draws fresh noise every step.
 struct Thermo {
   int on = 0;
+  int f32 = 0;                        // mixed form: Box-Muller on 24-bit uniforms in FP32
   double c1 = 1.0, s2 = 0.0;          // e^{-gamma dt}, (1 - c1^2) kB T
   uint64_t seed = 0;
   const int4 *step = nullptr;
@@ -1330,18 +1336,38 @@ __global__ void k_kick_drift(int64_t n, double *__restrict__ x, double *__restri
     const uint64_t step = (uint64_t)(uint32_t)st.x | ((uint64_t)(uint32_t)st.y << 32);
     uint64_t wd[4];
     philox4x64_dev(step, (uint64_t)i, 0, 0, th.seed, 0x4C414E47ull, wd);
-    double u[4];
+    double g0, g1, g2;
+    if (th.f32) {
+      // the same words, their top 24 bits as FP32 uniforms in (0, 1): every FP64 instruction is
+      // costly on this GPU and the noise needs no more than FP32
+      float u[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) u[q] = ((double)(wd[q] >> 11) + 0.5) * 0x1.0p-53;
-    const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
-    double s0, c0, s1, c1v;
-    sincospi(2.0 * u[1], &s0, &c0);
-    sincospi(2.0 * u[3], &s1, &c1v);
-    (void)s1;
+      for (int q = 0; q < 4; ++q) u[q] = ((float)(uint32_t)(wd[q] >> 40) + 0.5f) * 0x1.0p-24f;
+      const float r0 = sqrtf(-2.f * logf(u[0])), r1 = sqrtf(-2.f * logf(u[2]));
+      float s0, c0, s1, c1v;
+      sincospif(2.f * u[1], &s0, &c0);
+      sincospif(2.f * u[3], &s1, &c1v);
+      (void)s1;
+      g0 = r0 * c0;
+      g1 = r0 * s0;
+      g2 = r1 * c1v;
+    } else {
+      double u[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) u[q] = ((double)(wd[q] >> 11) + 0.5) * 0x1.0p-53;
+      const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
+      double s0, c0, s1, c1v;
+      sincospi(2.0 * u[1], &s0, &c0);
+      sincospi(2.0 * u[3], &s1, &c1v);
+      (void)s1;
+      g0 = r0 * c0;
+      g1 = r0 * s0;
+      g2 = r1 * c1v;
+    }
     const double sig = sqrt(th.s2 * minv[i]);
-    a = fma(th.c1, a, sig * r0 * c0);
-    b = fma(th.c1, b, sig * r0 * s0);
-    c = fma(th.c1, c, sig * r1 * c1v);
+    a = fma(th.c1, a, sig * g0);
+    b = fma(th.c1, b, sig * g1);
+    c = fma(th.c1, c, sig * g2);
   }
   vx[i] = a;
   vy[i] = b;
@@ -1400,6 +1426,7 @@ void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift) {
     // the closing half kick of a step also applies the thermostat; the step number sits in dm[K]
     SRBE_REQUIRE(c->dm.p && c->dm.cap > (size_t)c->K, SRBE_ESTATE, "mode list without its step word");
     th.on = 1;
+    th.f32 = c->precision == SRBE_MIXED ? 1 : 0;
     th.c1 = std::exp(-c->lang_gamma * c->dt);
     th.s2 = (1.0 - th.c1 * th.c1) * kBoltz * c->lang_T;
     th.seed = c->lang_seed;

@@ -246,39 +246,56 @@ __device__ __forceinline__ DF df_add_df(DF a, DF b) {
 
 // Mixed form of the same update: B and b as (hi, lo) FP32 pairs; every term is the exact product
 // hi*hi (FMA remainder) plus the cross terms, accumulated as a double-float.  Only the final
-// combination with dpsi q_d and psi_bar run in FP64 (one lane per row).
+// combination with dpsi q_d and psi_bar run in FP64 (one lane per row).  The matrix is streamed
+// once per step from HBM, so each row is split over kSplitWarps warps (contiguous column segments)
+// to keep enough loads in flight; the segments' double-floats are combined in a fixed order.
+constexpr int kSplitWarps = 4;
 __global__ void __launch_bounds__(256)
 k_charges_split(int64_t n, const float2 *__restrict__ B, const float2 *__restrict__ b, double dpsi,
                 const double *__restrict__ qd, const float2 *__restrict__ we, double wd, double s_e,
                 double *__restrict__ Q, float *__restrict__ Q32, double *__restrict__ scal) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row > n) return;
-  const float2 *r = row < n ? B + row * n : we;
+  __shared__ DF part[256 / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = warp % kSplitWarps;
+  const int64_t row = (int64_t)blockIdx.x * (256 / 32 / kSplitWarps) + warp / kSplitWarps;
   DF acc{0.f, 0.f};
   float lo = 0.f;
-  int64_t k = lane;
-  for (; k + 96 < n; k += 128) {
-    float2 m[4], v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      m[u] = __ldcs(r + k + 32 * u);
-      v[u] = __ldg(b + k + 32 * u);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float p = m[u].x * v[u].x;
-      const float e = fmaf(m[u].x, v[u].x, -p);
-      lo += e + fmaf(m[u].x, v[u].y, m[u].y * v[u].x);
-      acc = df_add(acc, p);
-    }
-  }
-  for (; k < n; k += 32) {
-    const float2 m0 = __ldcs(r + k), v0 = __ldg(b + k);
-    const float p = m0.x * v0.x;
-    const float e = fmaf(m0.x, v0.x, -p);
-    lo += e + fmaf(m0.x, v0.y, m0.y * v0.x);
+  auto term = [&](float2 m, float2 v) {
+    const float p = m.x * v.x;
+    const float e = fmaf(m.x, v.x, -p);
+    lo += e + fmaf(m.x, v.y, m.y * v.x);
     acc = df_add(acc, p);
+  };
+  if (row <= n) {
+    const float2 *r = row < n ? B + row * n : we;
+    if ((n & 1) == 0) {
+      // even n: rows start on 16-byte boundaries; two entries per 16-byte load
+      const float4 *r4 = reinterpret_cast<const float4 *>(r);
+      const float4 *b4 = reinterpret_cast<const float4 *>(b);
+      const int64_t h = n >> 1, per = (h + kSplitWarps - 1) / kSplitWarps;
+      const int64_t k0 = seg * per, k1 = min(h, k0 + per);
+      int64_t k = k0 + lane;
+      for (; k + 96 < k1; k += 128) {
+        float4 m[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m[u] = __ldcs(r4 + k + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 v = __ldg(b4 + k + 32 * u);
+          term(make_float2(m[u].x, m[u].y), make_float2(v.x, v.y));
+          term(make_float2(m[u].z, m[u].w), make_float2(v.z, v.w));
+        }
+      }
+      for (; k < k1; k += 32) {
+        const float4 m = __ldcs(r4 + k), v = __ldg(b4 + k);
+        term(make_float2(m.x, m.y), make_float2(v.x, v.y));
+        term(make_float2(m.z, m.w), make_float2(v.z, v.w));
+      }
+    } else {
+      const int64_t per = (n + kSplitWarps - 1) / kSplitWarps;
+      const int64_t k0 = seg * per, k1 = min(n, k0 + per);
+      for (int64_t k = k0 + lane; k < k1; k += 32) term(__ldcs(r + k), __ldg(b + k));
+    }
   }
   acc.lo += lo;
 #pragma unroll
@@ -287,8 +304,12 @@ k_charges_split(int64_t n, const float2 *__restrict__ B, const float2 *__restric
     // order the operands by lane so that both partners compute the identical sum
     acc = (lane & o) ? df_add_df(other, acc) : df_add_df(acc, other);
   }
-  if (lane == 0) {
-    const double a = (double)acc.hi + (double)acc.lo;
+  if (lane == 0) part[warp] = acc;
+  __syncthreads();
+  if (seg == 0 && lane == 0 && row <= n) {
+    DF t = part[warp];
+    for (int w = 1; w < kSplitWarps; ++w) t = df_add_df(t, part[warp + w]);
+    const double a = (double)t.hi + (double)t.lo;
     if (row < n) {
       const double q = fma(dpsi, qd[row], a);
       Q[row] = q;
@@ -657,8 +678,8 @@ void charge_update(srbe_ctx *c) {
   const int64_t ne = c->ne;
   const unsigned nb = blocks_for((ne + 1) * 32, 256);
   if (c->precision == SRBE_MIXED)
-    k_charges_split<<<nb, 256, 0, c->stream>>>(ne, c->Bsplit.p, c->bsplit.p, c->dpsi, c->qd.p, c->wesplit.p, c->wd,
-                                               c->s_e, c->Q.p, c->Q32.p, c->scal.p);
+    k_charges_split<<<blocks_for(ne + 1, 256 / 32 / kSplitWarps), 256, 0, c->stream>>>(
+        ne, c->Bsplit.p, c->bsplit.p, c->dpsi, c->qd.p, c->wesplit.p, c->wd, c->s_e, c->Q.p, c->Q32.p, c->scal.p);
   else
     k_charges_fp64<<<nb, 256, 0, c->stream>>>(ne, c->Bmat.p, c->bvec.p, c->dpsi, c->qd.p, c->we.p, c->wd, c->s_e,
                                               c->Q.p, c->Q32.p, c->scal.p);
