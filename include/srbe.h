@@ -100,7 +100,7 @@ int srbe_get_positions(srbe_ctx *ctx, double *r, double *v);
  * type per ion (0..ntype-2; type ntype-1 is the electrode), a molecule id per ion (LJ is
  * excluded inside a molecule), ntype x ntype LJ sigma (nm) and epsilon (kJ/mol) tables,
  * nb harmonic bonds (pairs of ion indices, rest lengths r0, force constant kb) and the time
- * step dt (ps).  Must follow srbe_set_positions with the same n_ion. */
+ * step dt (ps).  1 <= ntype <= 16.  Must follow srbe_set_positions with the same n_ion. */
 int srbe_set_md(srbe_ctx *ctx, const double *mass, const double *v, int ntype, const int32_t *itype,
                 const int32_t *mol, const double *lj_sigma, const double *lj_eps, int64_t nb,
                 const int32_t *bonds, const double *r0, double kb, double dt);

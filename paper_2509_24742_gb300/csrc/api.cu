@@ -993,7 +993,7 @@ int srbe_set_md(srbe_ctx *c, const double *mass, const double *v, int ntype, con
     SRBE_CUDA(cudaStreamSynchronize(c->stream));
     const int64_t n = c->ni;
     SRBE_REQUIRE(n == 0 || (mass && itype && mol), SRBE_EINVAL, "null mass / type / molecule array");
-    SRBE_REQUIRE(ntype >= 1 && ntype <= 64 && lj_sigma && lj_eps, SRBE_EINVAL, "bad LJ tables");
+    SRBE_REQUIRE(ntype >= 1 && ntype <= 16 && lj_sigma && lj_eps, SRBE_EINVAL, "bad LJ tables");
     SRBE_REQUIRE(nb >= 0 && (nb == 0 || (bonds && r0)), SRBE_EINVAL, "bad bond list");
     SRBE_REQUIRE(dt > 0 && std::isfinite(dt) && std::isfinite(kb), SRBE_EINVAL, "bad dt or kb");
     std::vector<double> minv(n), lj(2 * ntype * ntype);

@@ -380,6 +380,8 @@ struct KahanF32 {
   __device__ __forceinline__ float valuef() const { return s - c; }
 };
 
+constexpr int kMaxLjTypes = 16;        // atom types of the LJ table (the FP32 forces keep it in shared memory)
+
 // FP32 pre-check margin: positions below 64 nm carry at most ~4e-6 nm of rounding in FP32
 constexpr float kPrecheckMargin = 1e-3f;
 
@@ -596,6 +598,94 @@ __device__ __forceinline__ void compacted_list(const PairSite &S, const CellsDev
   __syncwarp();
   if (lane < qn) pair(q[lane]);
   __syncwarp();
+}
+
+// FP32 passes over one Verlet list (the mixed form's forces): 32 entries per batch with a
+// three-stage software pipeline, the entries of batch b+2 and the particle data of batch b+1 in
+// flight while batch b computes, so that the two dependent gathers (entry, then particle) overlap
+// with arithmetic.  Lanes whose entry lies beyond rc (about a fifth of a list built at rc + skin)
+// sit out their batch instead of being compacted.  ljs: the LJ table in shared memory.
+template <bool EN>
+__device__ __forceinline__ void ii_list_f32(const PairSite &S, const CellsDev &ions, const MdDev &md,
+                                            const float2 *ljs, const int32_t *__restrict__ list, int count,
+                                            float cut2, int lane, PairAcc &A) {
+  const bool mdon = md.ntype != 0;
+  auto entry = [&](int k) { return k < count ? __ldg(list + k) : 0; };
+  int32_t e0 = entry(lane), e1 = entry(32 + lane);
+  int i0 = list_index(e0);
+  float4 o0 = ions.pf[i0];
+  int m0 = mdon ? ions.ms[i0] : 0, t0 = mdon ? ions.ts[i0] : 0;
+  for (int base = 0; base < count; base += 32) {
+    const int32_t e2 = entry(base + 64 + lane);
+    const int i1 = list_index(e1);
+    const float4 o1 = ions.pf[i1];
+    const int m1 = mdon ? ions.ms[i1] : 0, t1 = mdon ? ions.ts[i1] : 0;
+    // batch b
+    const float dx = S.Xf - (o0.x + (float)list_ix(e0) * S.Lxf);
+    const float dy = S.Yf - (o0.y + (float)list_iy(e0) * S.Lyf), dz = S.Zf - o0.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (base + lane < count && r2 < cut2 && r2 > 0.f) {
+      float phi, md2;
+      pair_ii_f(r2, S.af, phi, md2);
+      float fs = S.qke * o0.w * md2;
+      if (EN) A.eii += 0.5f * S.qf * o0.w * phi;
+      if (mdon && m0 != S.mi) {
+        const float2 sg = ljs[S.ti * md.ntype + t0];
+        const float ir2 = __frcp_rn(r2), sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
+        fs += 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
+        if (EN) A.elj += 2.f * sg.y * (sr6 * sr6 - sr6);
+      }
+      A.f0 = fmaf(fs, dx, A.f0);
+      A.f1 = fmaf(fs, dy, A.f1);
+      A.f2 = fmaf(fs, dz, A.f2);
+    }
+    e0 = e1;
+    e1 = e2;
+    o0 = o1;
+    m0 = m1;
+    t0 = t1;
+  }
+}
+
+template <bool EN>
+__device__ __forceinline__ void ie_list_f32(const PairSite &S, const CellsDev &eles, const MdDev &md,
+                                            const float2 *ljs, const float *__restrict__ Q32,
+                                            const int32_t *__restrict__ list, int count, float cut2, int lane,
+                                            PairAcc &A) {
+  auto entry = [&](int k) { return k < count ? __ldg(list + k) : 0; };
+  int32_t e0 = entry(lane), e1 = entry(32 + lane);
+  int j0 = list_index(e0);
+  float4 o0 = eles.pf[j0];
+  int s0 = eles.order[j0];
+  const float2 sg = md.ntype ? ljs[S.ti * md.ntype + (md.ntype - 1)] : make_float2(0.f, 0.f);
+  for (int base = 0; base < count; base += 32) {
+    const int32_t e2 = entry(base + 64 + lane);
+    const int j1 = list_index(e1);
+    const float4 o1 = eles.pf[j1];
+    const int s1 = eles.order[j1];
+    const float dx = S.Xf - (o0.x + (float)list_ix(e0) * S.Lxf);
+    const float dy = S.Yf - (o0.y + (float)list_iy(e0) * S.Lyf), dz = S.Zf - o0.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (base + lane < count && r2 < cut2 && r2 > 0.f) {
+      const float Qj = __ldg(Q32 + s0);
+      float phi, md2;
+      pair_ie_f(r2, S.af, S.etaf, phi, md2);
+      float fs = S.qke * Qj * md2;
+      if (EN) A.eie += S.qf * Qj * phi;
+      if (md.ntype) {
+        const float ir2 = __frcp_rn(r2), sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
+        fs += 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
+        if (EN) A.elj += 4.f * sg.y * (sr6 * sr6 - sr6);
+      }
+      A.f0 = fmaf(fs, dx, A.f0);
+      A.f1 = fmaf(fs, dy, A.f1);
+      A.f2 = fmaf(fs, dz, A.f2);
+    }
+    e0 = e1;
+    e1 = e2;
+    o0 = o1;
+    s0 = s1;
+  }
 }
 
 // Verlet-list view handed to the gathers
@@ -1057,9 +1147,14 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
              double *__restrict__ epart) {
   __shared__ double red[kWarpsPerBlock][4];
   __shared__ int2 wq[kWarpsPerBlock][64];
+  __shared__ float2 ljs[kMaxLjTypes * kMaxLjTypes];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   double e_ii = 0, e_ie = 0, e_lj = 0, e_b = 0;
+  if (F32 && md.ntype) {
+    for (int t = threadIdx.x; t < md.ntype * md.ntype; t += blockDim.x) ljs[t] = md.lj32[t];
+  }
+  __syncthreads();
   if (p < ni) {
     const int32_t i = ions.order[p];
     const double X = ions.xs[p], Y = ions.ys[p], Z = ions.zs[p], qi = ions.ws[p];
@@ -1108,13 +1203,17 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     int2 *q = wq[warp];
     // Verlet lists; a particle whose list overflowed walks the stencil of its build cell instead
     const int nii = nl.ii_n[p], nie = nl.ie_n[p];
-    if (nii <= nl.cap)
+    if (F32 && nii <= nl.cap)
+      ii_list_f32<EN>(S, ions, md, ljs, nl.ii + p * nl.cap, nii, cut2, lane, A);
+    else if (nii <= nl.cap)
       compacted_list(S, ions, nl.ii + p * nl.cap, nii, cut2, q, lane,
                      [&](int2 e) { pair_ion_ion<F32, EN>(S, ions, md, e, A); });
     else
       compacted_pairs(S, ions, nl.cell_s[p], true, cut2, q, lane,
                       [&](int2 e) { pair_ion_ion<F32, EN>(S, ions, md, e, A); });
-    if (nie <= nl.cap)
+    if (F32 && nie <= nl.cap)
+      ie_list_f32<EN>(S, eles, md, ljs, Q32, nl.ie + p * nl.cap, nie, cut2, lane, A);
+    else if (nie <= nl.cap)
       compacted_list(S, eles, nl.ie + p * nl.cap, nie, cut2, q, lane,
                      [&](int2 e) { pair_ion_ele<F32, EN>(S, eles, md, Q, Q32, e, A); });
     else
