@@ -187,6 +187,18 @@ def roofline(phase, ms_per_launch, slab, K, n_ii, n_ie, precision, pk):
             else "nominal GB300 FP64 1.25 TFLOP/s", "algorithmic_flops": flops, "kernel": kern}
 
 
+def job_throughput(ms_local, steps, world, device):
+    """Whole-job steps/s of `world` replicas that each timed `steps` steps in ms_local: the slowest
+    rank's time (max over ranks, a collective when world > 1) and world x steps / that time."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------------------------------------- GPU arm
 def gpu_arm(args, rank, world):
     import torch
@@ -260,11 +272,7 @@ def gpu_arm(args, rank, world):
     n_other = max(3, min(args.steps, 50))
     ms_other, ph_other, _, _ = timed(ctxs[other], n_other, max(3, min(args.warmup, 5)), traced=True)
 
-    if world > 1:
-        t = torch.tensor([ms_head], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_head = float(t.item())
-    value = world * args.steps / (ms_head * 1e-3)
+    ms_head, value = job_throughput(ms_head, args.steps, world, "cuda")
 
     # dominant phase and its roofline
     per_step = {p: v[0] / n_trace for p, v in ph_head.items() if v[1]}
