@@ -407,6 +407,11 @@ void reserve(srbe_ctx *c) {
   const size_t neb = blocks_for(std::max<int64_t>(c->ne, 1), 128);
   c->epart.ensure(nblk * 4 + 4 + neb + 8);
   c->scal.ensure(kScalCount);
+  const size_t tiles = (size_t)(K + 31) / 32;
+  if (c->sfdone.cap < tiles) {
+    c->sfdone.ensure(tiles);
+    SRBE_CUDA(cudaMemsetAsync(c->sfdone.p, 0, sizeof(int) * tiles, c->stream));
+  }
   // ion cell list and Verlet lists
   Cells &cl = c->icells;
   const size_t nn = (size_t)std::max<int64_t>(c->ni, 1), ne = (size_t)std::max<int64_t>(c->ne, 1);

@@ -27,6 +27,60 @@ struct KahanF {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// Finishes mode k (k < K) or, for k == K, the dipole: lanes take chunks lane, lane + 32, ..., then a
+// butterfly sum (every lane ends with the same value); lane 0 writes S (+ S_add) and the gather
+// coefficients, or the dipole into scal[mslot].  Partials are read through L2 (__ldcg): in the
+// fused form they were written by other blocks of the same launch.
+struct SfFinish {
+  int K, nchunk;
+  const double2 *partial;
+  const double *mpart;
+  double2 *S;
+  const double2 *S_add;
+  double *scal;
+  int mslot;
+  const double *cw;
+  double2 *coef;
+  float2 *coef32;
+  int swap;
+};
+
+__device__ __forceinline__ void sf_finish(const SfFinish &f, int k, int lane) {
+  double re = 0.0, im = 0.0;
+  if (k < f.K) {
+    for (int c = lane; c < f.nchunk; c += 32) {
+      const double2 p = __ldcg(f.partial + (int64_t)c * f.K + k);
+      re += p.x;
+      im += p.y;
+    }
+  } else {
+    for (int c = lane; c < f.nchunk; c += 32) re += __ldcg(f.mpart + c);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) {
+    if (k < f.K) {
+      if (f.S_add) {
+        re += f.S_add[k].x;
+        im += f.S_add[k].y;
+      }
+      f.S[k] = make_double2(re, im);
+      if (f.coef) {
+        // per-mode coefficients of the gathers: (c Re S, c Im S) for b, (c Im S, c Re S) for forces
+        const double c = f.cw[k];
+        const double2 v = f.swap ? make_double2(c * im, c * re) : make_double2(c * re, c * im);
+        f.coef[k] = v;
+        f.coef32[k] = make_float2((float)v.x, (float)v.y);
+      }
+    } else {
+      f.scal[f.mslot] = re;
+    }
+  }
+}
+
 // partial[c][k] = sum over the particles of chunk c of w_j exp(i k . r_j).  Lane = mode (32 per
 // block in y), the four warps take every fourth particle of each staged batch of 128, and the
 // four warp sums are added in warp order.  Blocks with blockIdx.y == 0 also sum w z per chunk.
@@ -35,7 +89,7 @@ __global__ void __launch_bounds__(kSfThreads)
 k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                const double *__restrict__ w, int K, const int4 *__restrict__ modes, double3 invL,
                const double2 *__restrict__ tab, int64_t chunk, double2 *__restrict__ partial,
-               double *__restrict__ mpart) {
+               double *__restrict__ mpart, SfFinish fin, int *__restrict__ done) {
   __shared__ uint64_t su[3][kSfThreads];
   __shared__ double sw[kSfThreads];
   __shared__ double2 red[4][32];
@@ -103,51 +157,58 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
     }
     if (t == 0) mpart[blockIdx.x] = mred[0];
   }
+  // the last block to finish a mode tile adds that tile's partials (the same order as
+  // k_sfac_reduce, so the result does not depend on which block comes last) and re-arms the counter
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(&done[blockIdx.y], 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // lane = mode of the tile, warp w takes chunks w, w + 4, ... (coalesced 512-byte rows of the
+  // partials), then the four warp sums are added in warp order
+  double2 acc = make_double2(0.0, 0.0);
+  if (kidx < K) {
+#pragma unroll 4
+    for (int c = warp; c < fin.nchunk; c += 4) {
+      const double2 p = __ldcg(partial + (int64_t)c * K + kidx);
+      acc.x += p.x;
+      acc.y += p.y;
+    }
+  }
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && kidx < K) {
+    double re = red[0][lane].x, im = red[0][lane].y;
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      re += red[q][lane].x;
+      im += red[q][lane].y;
+    }
+    if (fin.S_add) {
+      re += fin.S_add[kidx].x;
+      im += fin.S_add[kidx].y;
+    }
+    fin.S[kidx] = make_double2(re, im);
+    if (fin.coef) {
+      const double c = fin.cw[kidx];
+      const double2 v = fin.swap ? make_double2(c * im, c * re) : make_double2(c * re, c * im);
+      fin.coef[kidx] = v;
+      fin.coef32[kidx] = make_float2((float)v.x, (float)v.y);
+    }
+  }
+  if (blockIdx.y == 0 && warp == 1) sf_finish(fin, K, lane);     // the dipole partials
+  if (t == 0) done[blockIdx.y] = 0;
 }
 
 // S[k] = sum over chunks of the partials (+ S_add[k]): one warp per mode, lanes take chunks
 // lane, lane + 32, ..., then a butterfly sum (every lane ends with the same value).  Warp K sums
 // the dipole partials into scal[mslot].
-__global__ void k_sfac_reduce(int K, int nchunk, const double2 *__restrict__ partial, const double *__restrict__ mpart,
-                              double2 *__restrict__ S, const double2 *__restrict__ S_add, double *__restrict__ scal,
-                              int mslot, const double *__restrict__ cw, double2 *__restrict__ coef,
-                              float2 *__restrict__ coef32, int swap) {
-  const int lane = threadIdx.x & 31;
+__global__ void k_sfac_reduce(SfFinish f) {
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (k > K) return;
-  double re = 0.0, im = 0.0;
-  if (k < K) {
-    for (int c = lane; c < nchunk; c += 32) {
-      const double2 p = partial[(int64_t)c * K + k];
-      re += p.x;
-      im += p.y;
-    }
-  } else {
-    for (int c = lane; c < nchunk; c += 32) re += mpart[c];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    re += __shfl_xor_sync(0xffffffffu, re, o);
-    im += __shfl_xor_sync(0xffffffffu, im, o);
-  }
-  if (lane == 0) {
-    if (k < K) {
-      if (S_add) {
-        re += S_add[k].x;
-        im += S_add[k].y;
-      }
-      S[k] = make_double2(re, im);
-      if (coef) {
-        // per-mode coefficients of the gathers: (c Re S, c Im S) for b, (c Im S, c Re S) for forces
-        const double c = cw[k];
-        const double2 v = swap ? make_double2(c * im, c * re) : make_double2(c * re, c * im);
-        coef[k] = v;
-        coef32[k] = make_float2((float)v.x, (float)v.y);
-      }
-    } else {
-      scal[mslot] = re;
-    }
-  }
+  if (k > f.K) return;
+  sf_finish(f, k, threadIdx.x & 31);
 }
 
 // chunking of the particle sum: whole 128-particle batches, at most kSfMaxChunks chunks
@@ -173,21 +234,23 @@ void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, 
                    c->mpart.cap >= (size_t)std::max<int64_t>(nchunk, 1),
                SRBE_ESTATE, "scratch buffers not reserved for this size");
   const double3 invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
+  SfFinish f{K, (int)nchunk, c->partial.p, c->mpart.p, S, S_add, c->scal.p, mslot, c->dc.p,
+             coef_mode >= 0 ? c->coef.p : nullptr, c->coef32.p, coef_mode > 0 ? 1 : 0};
   if (nchunk > 0) {
+    SRBE_REQUIRE(c->sfdone.cap >= (size_t)ktiles, SRBE_ESTATE, "tile counters not reserved for this size");
     dim3 grid((unsigned)nchunk, (unsigned)ktiles);
     if (c->precision == SRBE_MIXED)
       k_sfac_partial<true><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, w, K, c->dm.p, invL, c->tab.p, chunk,
-                                                               c->partial.p, c->mpart.p);
+                                                               c->partial.p, c->mpart.p, f, c->sfdone.p);
     else
       k_sfac_partial<false><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, w, K, c->dm.p, invL, c->tab.p, chunk,
-                                                                c->partial.p, c->mpart.p);
+                                                                c->partial.p, c->mpart.p, f, c->sfdone.p);
     c->launches++;
     c->mode_evals += n * (int64_t)K;
+  } else {
+    k_sfac_reduce<<<blocks_for((int64_t)(K + 1) * 32, 256), 256, 0, c->stream>>>(f);
+    c->launches++;
   }
-  k_sfac_reduce<<<blocks_for((int64_t)(K + 1) * 32, 256), 256, 0, c->stream>>>(
-      K, (int)nchunk, c->partial.p, c->mpart.p, S, S_add, c->scal.p, mslot, c->dc.p,
-      coef_mode >= 0 ? c->coef.p : nullptr, c->coef32.p, coef_mode > 0 ? 1 : 0);
-  c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }
 

@@ -243,6 +243,7 @@ struct srbe_ctx {
   srbe::DevBuf<double> scal;                   // device scalars (see kScal* indices)
   srbe::DevBuf<double> epart;                  // per-block energy partials
   srbe::DevBuf<int> flag;                      // device error flag
+  srbe::DevBuf<int> sfdone;                    // per mode tile: blocks of the structure factor done (self re-arming)
   srbe::DevBuf<double> resid;                  // per-row squared residuals of the FP64 check
   double h_scal[16];
 
