@@ -416,6 +416,47 @@ def prec_arm(args):
             out["fp64"]["steps_per_s"], "setup_s": t_setup, "md": {"T_end_K": T_end}}
 
 
+# ---------------------------------------------------------------------------------------------- charge update
+def solve_arm(args):
+    """The per-step charge update alone (Eqs. 9-10 through the projected inverse) on a 6,144-site
+    electrode (2 x 3 layers of 32 x 32; the matrix, 302 MB in FP64, does not fit in L2): device
+    time of the solve phase from the library's event tracing, against the HBM roofline."""
+    import torch
+    from paper_2509_24742_gb300 import srbe, workloads
+    torch.cuda.set_device(0)
+    pk = peaks()
+    slab = workloads.make_slab("solve6144", (8.0, 8.0, 24.0), 32, 32, 400, 1, alpha=1.87, eta_inv=19.79, rc=1.6,
+                               P=100, M=3, dpsi_volt=2.0, seed=1005, placement="lattice")
+    ne = slab.n_ele
+    out = {}
+    with srbe.from_slab(slab, precision=srbe.MIXED) as ctx:
+        for name, prec, mbytes in (("mixed", srbe.MIXED, 8), ("fp64", srbe.FP64, 8)):
+            ctx.set_precision(prec)
+            ctx.sample_k(SEED, 0)
+            for _ in range(args.warmup):
+                ctx.forces()
+            ctx.set_profiling(True)
+            for i in range(args.steps):
+                ctx.sample_k(SEED, i + 1)
+                ctx.forces()
+            ph = ctx.phase_times()
+            ctx.set_profiling(False)
+            ms = ph["solve"][0] / ph["solve"][1]
+            byts = mbytes * ne * ne + 6 * 8 * ne    # (hi, lo) FP32 or FP64 matrix + the vectors
+            ach = byts / (ms * 1e-3) / 1e9
+            out[name] = {"ms_per_launch": ms, "algorithmic_bytes": byts,
+                         "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                      "frac": ach / pk["hbm_gbs"], "peak_source": pk["hbm_source"],
+                                      "kernel": "k_charges_split" if name == "mixed" else "k_charges_fp64"}}
+        res = ctx.charge_residual()
+    return {"metric": "CP charge update (projected inverse) on 1 GB300", "value": out["mixed"]["ms_per_launch"],
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "f32x2+f64", "data": "synthetic",
+            "config": {"workload": "solve6144: 2 x 3 layers of 32 x 32 electrode sites, 8 x 8 x 24 nm, P=100",
+                       "l2": "matrix (302 MB) larger than L2"},
+            "mixed": out["mixed"], "fp64": out["fp64"], "fp64_charge_residual": res}
+
+
 # ---------------------------------------------------------------------------------------------- batching form
 def batch_arm(args):
     """R uneven replicas: the mixed-precision batch (one graph launch per batch step, autotuned
@@ -560,7 +601,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="md11072", choices=["md11072", "batch64", "prec100k"])
+    ap.add_argument("--workload", default="md11072", choices=["md11072", "batch64", "prec100k", "solve6144"])
     ap.add_argument("--replicas", type=int, default=64)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -577,6 +618,9 @@ def main():
         return
     if args.workload == "prec100k":
         print(json.dumps(prec_arm(args)))
+        return
+    if args.workload == "solve6144":
+        print(json.dumps(solve_arm(args)))
         return
     if world > 1:
         import torch
