@@ -327,9 +327,10 @@ constexpr size_t kEventPool = 4096;   // event pairs per drain
 void drain_events(srbe_ctx *c) {
   Extra *e = extra(c);
   if (!e->ev_used) return;
-  SRBE_CUDA(cudaStreamSynchronize(c->stream));
   for (size_t i = 0; i < e->ev_used; ++i) {
     float t = 0.f;
+    // phases run on the main and the side stream: wait for each interval's own end event
+    SRBE_CUDA(cudaEventSynchronize(e->ev[2 * i + 1]));
     SRBE_CUDA(cudaEventElapsedTime(&t, e->ev[2 * i], e->ev[2 * i + 1]));
     e->ms[e->ev_phase[i]] += t;
     e->count[e->ev_phase[i]]++;
@@ -660,12 +661,26 @@ void require_state(srbe_ctx *c, bool pos) {
 
 void charges_pass(srbe_ctx *c) {
   reserve(c);
-  phase_begin(c, kPhCells);
-  neighbor_update(c);
-  phase_end(c, kPhCells);
+  // the neighbour refresh / rebuild (reads x, y, z; writes the sorted copies and lists) runs on the
+  // context's side stream beside S1 (reads x, y, z, q) and joins before b, which needs both
+  SRBE_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+  SRBE_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  const cudaStream_t main = c->stream;
+  c->stream = c->side;
+  try {
+    phase_begin(c, kPhCells);
+    neighbor_update(c);
+    phase_end(c, kPhCells);
+  } catch (...) {
+    c->stream = main;
+    throw;
+  }
+  c->stream = main;
+  SRBE_CUDA(cudaEventRecord(c->ev_join, c->side));
   phase_begin(c, kPhS1);
   structure_factor(c, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->S1.p, nullptr, kScalMion, 0);
   phase_end(c, kPhS1);
+  SRBE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   phase_begin(c, kPhRhs);
   electrode_rhs(c);
   phase_end(c, kPhRhs);
@@ -797,6 +812,9 @@ int srbe_create(const double box[3], double alpha, double eta, double rc, int P,
     c->own_stream = true;
     SRBE_CUDA(cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming));
     SRBE_CUDA(cudaEventRecord(c->stage_done, c->stream));
+    SRBE_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     upload_table(c);
     c->scal.ensure(kScalCount);
     SRBE_CUDA(cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScalCount, c->stream));
@@ -816,7 +834,11 @@ int srbe_destroy(srbe_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->h_mode_stage) cudaFreeHost(c->h_mode_stage);
   if (c->h_w_stage) cudaFreeHost(c->h_w_stage);
+  if (c->side) cudaStreamSynchronize(c->side);
   if (c->stage_done) cudaEventDestroy(c->stage_done);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   c->stream = nullptr;
   delete c->hx;

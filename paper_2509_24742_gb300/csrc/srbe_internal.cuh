@@ -177,6 +177,8 @@ struct srbe_ctx {
 
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t side = nullptr;                 // neighbour-list work beside S1 (joined before b)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
 
   bool have_ele = false, have_pos = false, have_modes = false, have_md = false;
