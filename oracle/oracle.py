@@ -83,6 +83,7 @@ def lib():
         L.orc_G_brute.argtypes = [_dp, _dbl, _int, _ip]
         L.orc_G_brute.restype = _dbl
         L.orc_langevin_gauss.argtypes = [_u64, _u64, _i64, _dp]
+        L.orc_A_rows.argtypes = [_dp, _dbl, _dbl, _dbl, _i64, _ip, _i64, _dp, _dp, _i64, ctypes.c_void_p, _dp]
         _lib = L
     return _lib
 
@@ -251,6 +252,17 @@ def build_A(L, eta, R, alpha_A, tol=1e-17, modes=None, rcut=None):
     A = np.empty((n, n))
     lib().orc_build_A(_d(L), alpha_A, eta, rc, m.shape[0], m, n, _d(R), A)
     return A
+
+
+def A_rows(L, eta, R, alpha_A, x, rows, tol=1e-17):
+    """(A x)[rows] for the A of build_A, without forming A."""
+    m = A_modes(L, alpha_A, tol)
+    rc = A_rcut(alpha_A, tol)
+    rws = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty(rws.size)
+    lib().orc_A_rows(_d(L), alpha_A, eta, rc, m.shape[0], m, R.shape[0], _d(R), _d(x), rws.size,
+                     rws.ctypes.data_as(ctypes.c_void_p), out)
+    return out
 
 
 def potential_split(side):

@@ -518,6 +518,61 @@ double orc_G_brute(const double L[3], double alpha, int M, const int32_t mmax[3]
   return nval(&g);
 }
 
+/* Rows of A x (Eq. 18) without forming A: out[r] = sum_j A[rows[r]][j] x_j with the terms of
+ * orc_build_A (full-lattice modes m [K][3], Gaussian-screened real-space images within rcut, self
+ * term, slab term), the k-space part as sum_k w_k Re(exp(-i k.R_i) S_x(k)), S_x(k) = sum_j x_j
+ * exp(i k.R_j).  For checks of a solve at sizes where A cannot be formed. */
+void orc_A_rows(const double L[3], double alpha, double eta, double rcut, int64_t K, const int32_t *m, int64_t ne,
+                const double *R, const double *x, int64_t nrow, const int64_t *rows, double *out) {
+  double V = L[0] * L[1] * L[2];
+  double *kv = (double *)malloc(sizeof(double) * 3 * (K > 0 ? K : 1));
+  double *S = (double *)malloc(sizeof(double) * 2 * (K > 0 ? K : 1));
+  orc_kvectors(L, K, m, kv);
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < K; ++k) {
+    nsum re = {0, 0}, im = {0, 0};
+    for (int64_t j = 0; j < ne; ++j) {
+      double ph = kv[3 * k] * R[3 * j] + kv[3 * k + 1] * R[3 * j + 1] + kv[3 * k + 2] * R[3 * j + 2];
+      nadd(&re, x[j] * cos(ph));
+      nadd(&im, x[j] * sin(ph));
+    }
+    S[2 * k] = nval(&re);
+    S[2 * k + 1] = nval(&im);
+  }
+  int nx = n_images(rcut, L[0]), ny = n_images(rcut, L[1]);
+  double self = 2.0 * (1.0 / (sqrt(2.0 * M_PI) * eta) - alpha / sqrt(M_PI));
+  nsum mz = {0, 0};
+  for (int64_t j = 0; j < ne; ++j) nadd(&mz, R[3 * j + 2] * x[j]);
+  double Mz = nval(&mz);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t r = 0; r < nrow; ++r) {
+    int64_t i = rows[r];
+    nsum acc = {0, 0};
+    for (int64_t k = 0; k < K; ++k) {
+      double k2 = kv[3 * k] * kv[3 * k] + kv[3 * k + 1] * kv[3 * k + 1] + kv[3 * k + 2] * kv[3 * k + 2];
+      double w = 4.0 * M_PI / (V * k2) * exp(-k2 / (4.0 * alpha * alpha));
+      double ph = kv[3 * k] * R[3 * i] + kv[3 * k + 1] * R[3 * i + 1] + kv[3 * k + 2] * R[3 * i + 2];
+      /* Re((cos ph - i sin ph)(S_re + i S_im)) */
+      nadd(&acc, w * (cos(ph) * S[2 * k] + sin(ph) * S[2 * k + 1]));
+    }
+    for (int64_t j = 0; j < ne; ++j) {
+      double dx0 = R[3 * i] - R[3 * j], dy0 = R[3 * i + 1] - R[3 * j + 1], dz = R[3 * i + 2] - R[3 * j + 2];
+      dx0 -= L[0] * floor(dx0 / L[0] + 0.5);
+      dy0 -= L[1] * floor(dy0 / L[1] + 0.5);
+      for (int a = -nx; a <= nx; ++a)
+        for (int b = -ny; b <= ny; ++b) {
+          double dx = dx0 + a * L[0], dy = dy0 + b * L[1];
+          double d = sqrt(dx * dx + dy * dy + dz * dz);
+          if (d > 0.0 && d < rcut) nadd(&acc, phi_ee(d, alpha, eta) * x[j]);
+        }
+    }
+    nadd(&acc, self * x[i]);
+    nadd(&acc, 4.0 * M_PI / V * R[3 * i + 2] * Mz);
+    out[r] = nval(&acc);
+  }
+  free(kv); free(S);
+}
+
 /* ---------------------------------------------------------------------------
  * Langevin thermostat noise (Eq. 39: the Wiener increments dW_i of every ion).
  * Three independent standard normal numbers per ion i and step n: Philox4x64-10

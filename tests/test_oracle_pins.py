@@ -288,3 +288,15 @@ def test_sampled_evaluation_equals_rows_of_the_full_one(orc):
     np.testing.assert_allclose(Ft, ev["F"][t], rtol=1e-13, atol=1e-12 * np.abs(ev["F"]).max())
     j = np.array([383, 0, 17, 200])
     np.testing.assert_allclose(orc.sampled_b(s, m, c, j), ev["b"][j], rtol=1e-13, atol=1e-13)
+
+
+def test_A_rows_equal_rows_of_the_formed_A(orc):
+    """The row evaluation used at sizes where A cannot be formed gives the rows of build_A times x."""
+    from paper_2509_24742_gb300 import workloads as wl
+    s = wl.tiny_slab(nx=3, ny=2)
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=s.n_ele)
+    A = orc.build_A(s.box, s.eta, s.R, 2.5)
+    rows = np.array([0, 5, s.n_ele - 1])
+    np.testing.assert_allclose(orc.A_rows(s.box, s.eta, s.R, 2.5, x, rows), (A @ x)[rows], rtol=1e-12,
+                               atol=1e-12 * np.abs(A @ x).max())
