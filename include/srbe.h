@@ -81,12 +81,16 @@ int srbe_set_precision(srbe_ctx *ctx, int mode);
  * so that the in-plane-only real-space sum stays exact) and truncated where
  * exp(-k^2/4 alpha_A^2) and erfc(alpha_A r) fall below tol (<= 0: 1e-17). */
 int srbe_set_A_params(srbe_ctx *ctx, double alpha_A, double tol);
+/* The alpha_A A was built with (after srbe_set_electrode; 0 for a NULL context). */
+double srbe_get_alpha_A(const srbe_ctx *ctx);
 
 /* Fixes the electrode: n_ele sites R [n_ele][3] and their side (0 = left, 1 = right).
  * Builds A (Eq. 18, slab term (4 pi / V) Z_i Z_j), inverts it on the GPU, and stores the
  * projected inverse J A^-1 (Eqs. 10-11) and A^-1 e.  Cost is paid once (§2: A is constant).
- * Errors: SRBE_EINVAL (n_ele < 2, a side other than 0/1, one side empty, non-finite R),
- * SRBE_ENOTCONV if A is not positive definite. */
+ * Up to 16,384 sites A is stored densely; lattice electrodes (srbe_set_lattice) also get the
+ * spectral form of A, and beyond 16,384 sites (up to 4,194,304) they get only that.
+ * Errors: SRBE_EINVAL (n_ele < 2 or too large, more than 16,384 sites that are not a lattice, a
+ * side other than 0/1, one side empty, non-finite R), SRBE_ENOTCONV if A is not positive definite. */
 int srbe_set_electrode(srbe_ctx *ctx, int64_t n_ele, const double *R, const int8_t *side);
 
 /* Sets the n_ion electrolyte positions r [n_ion][3] (nm) and charges q (e).  n_ion may be 0.
@@ -190,7 +194,13 @@ int srbe_get_phase_times(srbe_ctx *ctx, double *ms, int64_t *count);
  * direct projected inverse; Q and psi_bar then follow from Eqs. 9-10.  The starting guess is zero,
  * the previous step's solution, or the prediction of a per-site MLP (the learned form; no
  * counterpart in the paper).  tol is the relative residual ||dpsi d + b - A y|| / ||dpsi d + b||. */
-enum srbe_solver { SRBE_SOLVER_DIRECT = 0, SRBE_SOLVER_PCG = 1 };
+/* SRBE_SOLVER_LATTICE (lattice electrodes, see srbe_set_lattice): A is block-circulant over the
+ * lattice, so A^-1 acts as one nl x nl inverse per (m_x mod nx, m_y mod ny) bin between two of
+ * the lattice transforms; the solve is exact (no iteration; tol, maxit and warm are ignored) and
+ * needs no dense matrix.  srbe_set_electrode picks it for lattice electrodes of 8,192 sites or
+ * more; beyond 16,384 sites it is the only solver (A is not stored densely), otherwise
+ * SRBE_SOLVER_DIRECT is the default.  Errors: SRBE_ESTATE for a solver the electrode cannot use. */
+enum srbe_solver { SRBE_SOLVER_DIRECT = 0, SRBE_SOLVER_PCG = 1, SRBE_SOLVER_LATTICE = 2 };
 enum srbe_warm { SRBE_WARM_ZERO = 0, SRBE_WARM_PREVIOUS = 1, SRBE_WARM_MODEL = 2 };
 int srbe_set_solver(srbe_ctx *ctx, int kind, double tol, int maxit, int warm);
 /* Iterations and the recomputed relative residual of the last PCG solve. */

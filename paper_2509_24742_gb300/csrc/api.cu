@@ -883,7 +883,7 @@ int srbe_set_A_params(srbe_ctx *c, double alpha_A, double tol) {
 int srbe_set_electrode(srbe_ctx *c, int64_t n_ele, const double *R, const int8_t *side) {
   return guarded(c, [&] {
     SRBE_REQUIRE(R && side && n_ele >= 2, SRBE_EINVAL, "need at least two electrode sites");
-    SRBE_REQUIRE(n_ele <= 65535, SRBE_EINVAL, "at most 65535 electrode sites are supported");
+    SRBE_REQUIRE(n_ele <= (1 << 22), SRBE_EINVAL, "at most 4,194,304 electrode sites are supported");
     SRBE_REQUIRE(finite_all(R, 3 * n_ele), SRBE_EINVAL, "non-finite electrode position");
     int64_t nl = 0, nr = 0;
     for (int64_t j = 0; j < n_ele; ++j) {
@@ -1284,10 +1284,16 @@ int srbe_minimize(srbe_ctx *c, int nsteps, double a, double dmax, uint64_t seed)
 // ---- iterative solve and learned warm start ---------------------------------------------------
 int srbe_set_solver(srbe_ctx *c, int kind, double tol, int maxit, int warm) {
   return guarded(c, [&] {
-    SRBE_REQUIRE(kind == SRBE_SOLVER_DIRECT || kind == SRBE_SOLVER_PCG, SRBE_EINVAL, "unknown solver");
+    SRBE_REQUIRE(kind == SRBE_SOLVER_DIRECT || kind == SRBE_SOLVER_PCG || kind == SRBE_SOLVER_LATTICE, SRBE_EINVAL,
+                 "unknown solver");
     SRBE_REQUIRE(warm >= SRBE_WARM_ZERO && warm <= SRBE_WARM_MODEL, SRBE_EINVAL, "unknown warm start");
     SRBE_REQUIRE(tol > 0 && tol < 1 && maxit > 0, SRBE_EINVAL, "bad tolerance or iteration limit");
     SRBE_REQUIRE(c->have_ele, SRBE_ESTATE, "srbe_set_electrode must come first");
+    SRBE_REQUIRE(kind == SRBE_SOLVER_LATTICE || c->dense, SRBE_ESTATE,
+                 "this electrode has no dense A (more than 16,384 sites): only the lattice solver applies");
+    SRBE_REQUIRE(kind != SRBE_SOLVER_LATTICE || c->lat.spectral, SRBE_ESTATE,
+                 "the lattice solver needs a lattice electrode");
+    c->lat_solve = kind == SRBE_SOLVER_LATTICE;
     c->pcg.on = kind == SRBE_SOLVER_PCG;
     c->pcg.tol = tol;
     c->pcg.maxit = maxit;
@@ -1566,6 +1572,8 @@ int srbe_set_skin(srbe_ctx *c, double skin) {
 }
 
 double srbe_get_skin(const srbe_ctx *c) { return c ? c->nbr.skin : 0.0; }
+
+double srbe_get_alpha_A(const srbe_ctx *c) { return c ? c->alpha_A : 0.0; }
 
 }  // extern "C"
 

@@ -52,7 +52,8 @@ __device__ __forceinline__ int pmod(int a, int n) {
 //   kFwdY: columns (l, a):  Qh[l][b][a]  = sum_iy T[l][iy][a] w_ny^{b iy}
 //   kInvY: columns (l, a):  U[l][iy][a]  = sum_b  W[l][b][a] w_ny^{-b iy}
 //   kInvX: rows (l, iy):    bF[site(l, iy, ix)] = - Re sum_a U[l][iy][a] w_nx^{-a ix}
-enum { kFwdX = 0, kFwdY = 1, kInvY = 2, kInvX = 3 };
+//   kInvXp: as kInvX but + Re into a per-site array (the spectral solve's y)
+enum { kFwdX = 0, kFwdY = 1, kInvY = 2, kInvX = 3, kInvXp = 4 };
 constexpr int kLineWarps = 2;
 
 template <int MODE>
@@ -60,8 +61,8 @@ __global__ void __launch_bounds__(32 * kLineWarps)
 k_lat_line(LatDev L, const double *__restrict__ Q, const double2 *__restrict__ in, double2 *__restrict__ out,
            double *__restrict__ bF) {
   extern __shared__ double2 sm[];
-  constexpr bool along_x = (MODE == kFwdX || MODE == kInvX);
-  constexpr bool conj = (MODE == kInvY || MODE == kInvX);
+  constexpr bool along_x = (MODE == kFwdX || MODE == kInvX || MODE == kInvXp);
+  constexpr bool conj = (MODE == kInvY || MODE == kInvX || MODE == kInvXp);
   const int n = along_x ? L.nx : L.ny;
   const int64_t lines = along_x ? (int64_t)L.nl * L.ny : (int64_t)L.nl * L.nx;
   double2 *tw = sm;
@@ -75,7 +76,7 @@ k_lat_line(LatDev L, const double *__restrict__ Q, const double2 *__restrict__ i
       double2 x;
       if (MODE == kFwdX) {
         x = make_double2(Q[L.site[line * L.nx + t]], 0.0);
-      } else if (MODE == kInvX) {
+      } else if (MODE == kInvX || MODE == kInvXp) {
         x = in[line * L.nx + t];
       } else {
         const int64_t l = line / L.nx, a = line % L.nx;
@@ -105,6 +106,8 @@ k_lat_line(LatDev L, const double *__restrict__ Q, const double2 *__restrict__ i
       out[line * L.nx + s] = make_double2(re, im);
     } else if (MODE == kInvX) {
       bF[L.site[line * L.nx + s]] = -re;
+    } else if (MODE == kInvXp) {
+      bF[L.site[line * L.nx + s]] = re;
     } else {
       const int64_t l = line / L.nx, a = line % L.nx;
       out[(l * L.ny + s) * L.nx + a] = make_double2(re, im);
@@ -112,14 +115,17 @@ k_lat_line(LatDev L, const double *__restrict__ Q, const double2 *__restrict__ i
   }
 }
 
+// Q: real per-site input of kFwdX; dst: per-site output of kInvX / kInvXp
 template <int MODE>
-void launch_line(srbe_ctx *c, const LatDev &L, const double2 *in, double2 *out) {
-  constexpr bool along_x = (MODE == kFwdX || MODE == kInvX);
+void launch_line(srbe_ctx *c, const LatDev &L, const double2 *in, double2 *out, const double *Q = nullptr,
+                 double *dst = nullptr) {
+  constexpr bool along_x = (MODE == kFwdX || MODE == kInvX || MODE == kInvXp);
   const int n = along_x ? L.nx : L.ny;
   const int64_t lines = along_x ? (int64_t)L.nl * L.ny : (int64_t)L.nl * L.nx;
   const size_t smem = sizeof(double2) * (size_t)n * (1 + kLineWarps);
-  k_lat_line<MODE><<<blocks_for(lines, kLineWarps), 32 * kLineWarps, smem, c->stream>>>(L, c->Q.p, in, out,
-                                                                                        c->lat.bF.p);
+  k_lat_line<MODE><<<blocks_for(lines, kLineWarps), 32 * kLineWarps, smem, c->stream>>>(
+      L, Q ? Q : c->Q.p, in, out, dst ? dst : c->lat.bF.p);
+  c->launches++;
 }
 
 // E[k][l] = e^{i phi_l(k)}: one thread per (mode, layer), once per step (both paths use it)
@@ -329,7 +335,7 @@ void lattice_bfar(srbe_ctx *c) {
   k_lat_bin<<<blocks_for(bins * 32, 128), 128, 0, c->stream>>>(L, c->K, c->dm.p, c->coef.p, E, W);
   launch_line<kInvY>(c, L, W, U);
   launch_line<kInvX>(c, L, U, nullptr);
-  c->launches += 4;
+  c->launches += 2;
   c->mode_evals += (int64_t)c->K * L.nl;
   SRBE_CUDA(cudaGetLastError());
 }
@@ -346,8 +352,304 @@ void lattice_s2(srbe_ctx *c, double2 *S, const double2 *S1, int mslot) {
   k_lat_modes<<<blocks_for(c->K + 1, 64), 64, 0, c->stream>>>(L, c->K, c->dm.p, c->lat.Qh.p, c->lat.E.p, c->lat.Zl.p,
                                                                 S1, c->dc.p, S, c->coef.p, c->coef32.p, c->scal.p,
                                                                 mslot);
-  c->launches += 3;
+  c->launches += 1;
   c->mode_evals += (int64_t)c->K * L.nl;
+  SRBE_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------------------------------------
+// Spectral form of A for lattice electrodes (an evaluation order of Eqs. 9-10 and 18, exact up to
+// rounding).  Every term of A depends on two sites only through their layers and their lattice
+// offset (the slab term through the layers alone), so A is block-circulant over (ix, iy) with
+// nl x nl blocks: with Yhat = F+ y (the forward transform of the lattice lines) and F- the
+// transform back without normalisation, A y = F- (M Yhat) bin by bin, where
+//   M(bin) = sum over the modes k of A in the bin of c_k e^{-i (phi_l(k) - phi_l'(k))}
+//          + conj(F+ R_l restricted to layer l') / (nx ny),
+// R_l being the real-space, self and slab part of the row of A at the origin site of layer l.
+// Hence A^-1 rhs = F- (M^-1 F+ rhs) / (nx ny)^2 with one nl x nl inverse per bin: the
+// constant-potential solve costs two small transforms per step and no dense matrix.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+// R[l][j] = real-space images + self + slab term of A between the origin site of layer l and site j
+// (the same terms and cut-offs as the dense build of A)
+__global__ void k_lat_real_rows(LatDev L, int64_t ne, const double *__restrict__ ex, const double *__restrict__ ey,
+                                const double *__restrict__ ez, double Lx, double Ly, double alpha, double eta,
+                                double rcut, int nimx, int nimy, double self, double slab, double *__restrict__ R) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = blockIdx.y;
+  if (j >= ne) return;
+  const int64_t i = L.site[(int64_t)l * L.ny * L.nx];
+  double dx0 = ex[i] - ex[j], dy0 = ey[i] - ey[j];
+  const double dz = ez[i] - ez[j];
+  dx0 -= Lx * floor(dx0 / Lx + 0.5);
+  dy0 -= Ly * floor(dy0 / Ly + 0.5);
+  const double rc2 = rcut * rcut, eg = 1.4142135623730951 * eta;
+  double acc = 0.0;
+  for (int a = -nimx; a <= nimx; ++a)
+    for (int b = -nimy; b <= nimy; ++b) {
+      const double dx = dx0 + a * Lx, dy = dy0 + b * Ly;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 > 0.0 && r2 < rc2) {
+        const double r = sqrt(r2);
+        acc += (erfc(alpha * r) - erfc(r / eg)) / r;
+      }
+    }
+  if (i == j) acc += self;
+  acc = fma(slab * ez[i], ez[j], acc);
+  R[(int64_t)l * ne + j] = acc;
+}
+
+// M[bin][l][l'] = conj(Rhat_l[l'][bin]) / (nx ny): the transformed real-space row of origin layer l
+__global__ void k_lat_collect_real(LatDev L, int l, const double2 *__restrict__ Rh, double2 *__restrict__ M) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nb = (int64_t)L.nx * L.ny;
+  if (t >= nb * L.nl) return;
+  const int64_t bin = t % nb;
+  const int lp = (int)(t / nb);
+  const double2 v = Rh[(int64_t)lp * nb + bin];
+  const double inv = 1.0 / (double)nb;
+  M[(bin * L.nl + l) * L.nl + lp] = make_double2(v.x * inv, -v.y * inv);
+}
+
+// k-space part: thread per (bin, l, l'), the bin's entries (mode of the half lattice, +1 for the
+// mode's own bin, -1 for its mirror -k) in list order; half-lattice weights are doubled, so c_k = w / 2
+__global__ void k_lat_kspace_M(LatDev L, const int32_t *__restrict__ start, const int2 *__restrict__ ent,
+                               const int4 *__restrict__ modes, const double *__restrict__ w,
+                               const double2 *__restrict__ tab, double2 *__restrict__ M) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nb = (int64_t)L.nx * L.ny;
+  const int nl2 = L.nl * L.nl;
+  if (t >= nb * nl2) return;
+  const int64_t bin = t / nl2;
+  const int l = (int)((t % nl2) / L.nl), lp = (int)(t % L.nl);
+  double re = 0.0, im = 0.0;
+  for (int e = start[bin]; e < start[bin + 1]; ++e) {
+    const int2 en = ent[e];
+    const int4 m = modes[en.x];
+    // e^{-i s (phi_l - phi_l')} with the phases as exact 64-bit turns
+    const uint64_t d = phase64(m, L.lu[l], L.lu[L.nl + l], L.lu[2 * L.nl + l]) -
+                       phase64(m, L.lu[lp], L.lu[L.nl + lp], L.lu[2 * L.nl + lp]);
+    double cs, sn;
+    sincos_turns(d, tab, cs, sn);
+    const double c = 0.5 * w[en.x];
+    re = fma(c, cs, re);
+    im = fma(-c * (double)en.y, sn, im);
+  }
+  double2 *dst = M + bin * nl2 + l * L.nl + lp;
+  *dst = make_double2(dst->x + re, dst->y + im);
+}
+
+// per bin: Hermitian part of M, its Cholesky factor, and scale x M^-1 into Minv; a non-positive
+// pivot raises flag (A not positive definite)
+__global__ void k_lat_invert(LatDev L, const double2 *__restrict__ M, double2 *__restrict__ Minv, double scale,
+                             int *__restrict__ flag) {
+  const int64_t bin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin >= (int64_t)L.nx * L.ny) return;
+  const int n = L.nl;
+  double2 H[kLatMaxLayers][kLatMaxLayers], X[kLatMaxLayers][kLatMaxLayers];
+  const double2 *m = M + bin * n * n;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double2 a = m[i * n + j], b = m[j * n + i];
+      H[i][j] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    }
+  // H = C C^H, C lower triangular (overwrites the lower part of H)
+  for (int j = 0; j < n; ++j) {
+    double dj = H[j][j].x;
+    for (int k = 0; k < j; ++k) dj -= H[j][k].x * H[j][k].x + H[j][k].y * H[j][k].y;
+    if (!(dj > 0.0)) {
+      atomicExch(flag, 1);
+      return;
+    }
+    const double cjj = sqrt(dj);
+    H[j][j] = make_double2(cjj, 0.0);
+    for (int i = j + 1; i < n; ++i) {
+      double re = H[i][j].x, im = H[i][j].y;
+      for (int k = 0; k < j; ++k) {   // - C[i][k] conj(C[j][k])
+        re -= H[i][k].x * H[j][k].x + H[i][k].y * H[j][k].y;
+        im -= H[i][k].y * H[j][k].x - H[i][k].x * H[j][k].y;
+      }
+      H[i][j] = make_double2(re / cjj, im / cjj);
+    }
+  }
+  // columns of H^-1: solve C z = e_c, then C^H x = z
+  for (int c = 0; c < n; ++c) {
+    double2 z[kLatMaxLayers];
+    for (int i = 0; i < n; ++i) {
+      double re = (i == c) ? 1.0 : 0.0, im = 0.0;
+      for (int k = 0; k < i; ++k) {
+        re -= H[i][k].x * z[k].x - H[i][k].y * z[k].y;
+        im -= H[i][k].x * z[k].y + H[i][k].y * z[k].x;
+      }
+      z[i] = make_double2(re / H[i][i].x, im / H[i][i].x);
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double re = z[i].x, im = z[i].y;
+      for (int k = i + 1; k < n; ++k) {   // - conj(C[k][i]) x[k]
+        re -= H[k][i].x * X[k][c].x + H[k][i].y * X[k][c].y;
+        im -= H[k][i].x * X[k][c].y - H[k][i].y * X[k][c].x;
+      }
+      X[i][c] = make_double2(re / H[i][i].x, im / H[i][i].x);
+    }
+  }
+  double2 *o = Minv + bin * n * n;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) o[i * n + j] = make_double2(scale * X[i][j].x, scale * X[i][j].y);
+}
+
+// W[l][bin] = sum_l' B[bin][l][l'] Yh[l'][bin] (thread per (bin, l), layers in order)
+__global__ void k_lat_binmul(LatDev L, const double2 *__restrict__ B, const double2 *__restrict__ Yh,
+                             double2 *__restrict__ W) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nb = (int64_t)L.nx * L.ny;
+  if (t >= nb * L.nl) return;
+  const int64_t bin = t % nb;
+  const int l = (int)(t / nb);
+  const double2 *b = B + (bin * L.nl + l) * L.nl;
+  double re = 0.0, im = 0.0;
+  for (int lp = 0; lp < L.nl; ++lp) {
+    const double2 m = b[lp], y = Yh[(int64_t)lp * nb + bin];
+    re = fma(m.x, y.x, fma(-m.y, y.y, re));
+    im = fma(m.x, y.y, fma(m.y, y.x, im));
+  }
+  W[(int64_t)l * nb + bin] = make_double2(re, im);
+}
+
+__global__ void k_lat_rhs(int64_t ne, double dpsi, const double *__restrict__ d, const double *__restrict__ b,
+                          double *__restrict__ r) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < ne) r[j] = fma(dpsi, d[j], b[j]);
+}
+
+// one block: psi_bar = -(e^T y) / s (fixed-order sum), Q = y + psi_bar w_e (Eqs. 9-10)
+__global__ void __launch_bounds__(1024)
+k_lat_finish(int64_t ne, const double *__restrict__ y, const double *__restrict__ we, double s_e,
+             double *__restrict__ Q, float *__restrict__ Q32, double *__restrict__ scal) {
+  __shared__ double red[1024];
+  __shared__ double psi;
+  const int t = threadIdx.x;
+  double a = 0.0;
+  for (int64_t j = t; j < ne; j += 1024) a += y[j];
+  red[t] = a;
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (t < s) red[t] += red[t + s];
+    __syncthreads();
+  }
+  if (t == 0) {
+    psi = -red[0] / s_e;
+    scal[kScalPsi] = psi;
+  }
+  __syncthreads();
+  const double p = psi;
+  for (int64_t j = t; j < ne; j += 1024) {
+    const double q = fma(p, we[j], y[j]);
+    Q[j] = q;
+    Q32[j] = (float)q;
+  }
+}
+
+// y = F- (B F+ x), B = Minv (solve) or M (apply)
+void spectral_apply(srbe_ctx *c, const double2 *B, const double *x, double *y) {
+  const LatDev L = lat_dev(c);
+  const int64_t cells = (int64_t)L.nl * L.nx * L.ny;
+  launch_line<kFwdX>(c, L, nullptr, c->lat.T.p, x);
+  launch_line<kFwdY>(c, L, c->lat.T.p, c->lat.Qh.p);
+  k_lat_binmul<<<blocks_for(cells, 256), 256, 0, c->stream>>>(L, B, c->lat.Qh.p, c->lat.T.p);
+  launch_line<kInvY>(c, L, c->lat.T.p, c->lat.Qh.p);
+  launch_line<kInvXp>(c, L, c->lat.Qh.p, nullptr, nullptr, y);
+  c->launches++;
+  SRBE_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+void lattice_spectral_setup(srbe_ctx *c, const std::vector<int4> &modesA, const std::vector<double> &wA,
+                            double alpha_A, double rcut, int nimx, int nimy, double self, double slab) {
+  Lattice &Lt = c->lat;
+  Lt.spectral = false;
+  if (Lt.nl == 0) return;
+  const LatDev L = lat_dev(c);
+  const int64_t ne = c->ne, nb = (int64_t)L.nx * L.ny, nl = L.nl;
+  double2 *M = Lt.M.ensure((size_t)nb * nl * nl);
+  double2 *Minv = Lt.Minv.ensure((size_t)nb * nl * nl);
+  double *R = Lt.Rrow.ensure((size_t)nl * ne);
+  Lt.R.ensure(ne);
+  Lt.Y.ensure(ne);
+  // real-space rows at the layer origins, transformed layer by layer
+  k_lat_real_rows<<<dim3(blocks_for(ne, 128), (unsigned)nl), 128, 0, c->stream>>>(
+      L, ne, c->ex.p, c->ey.p, c->ez.p, c->L[0], c->L[1], alpha_A, c->eta, rcut, nimx, nimy, self, slab, R);
+  c->launches++;
+  for (int l = 0; l < nl; ++l) {
+    launch_line<kFwdX>(c, L, nullptr, Lt.T.p, R + (size_t)l * ne);
+    launch_line<kFwdY>(c, L, Lt.T.p, Lt.Qh.p);
+    k_lat_collect_real<<<blocks_for(nb * nl, 256), 256, 0, c->stream>>>(L, l, Lt.Qh.p, M);
+    c->launches++;
+  }
+  // k-space part: the half-lattice modes of A binned by (m_x mod nx, m_y mod ny), each also into
+  // its mirror's bin; entries kept in mode order
+  const int64_t KA = (int64_t)modesA.size();
+  std::vector<int32_t> start(nb + 1, 0);
+  auto pm = [](int a, int n) { return ((a % n) + n) % n; };
+  auto bin_of = [&](int mx, int my) { return (int64_t)pm(my, L.ny) * L.nx + pm(mx, L.nx); };
+  for (int64_t t = 0; t < KA; ++t) {
+    start[bin_of(modesA[t].x, modesA[t].y) + 1]++;
+    start[bin_of(-modesA[t].x, -modesA[t].y) + 1]++;
+  }
+  for (int64_t b = 0; b < nb; ++b) start[b + 1] += start[b];
+  std::vector<int2> ent((size_t)2 * KA);
+  std::vector<int32_t> fill(start.begin(), start.end() - 1);
+  for (int64_t t = 0; t < KA; ++t) {
+    ent[fill[bin_of(modesA[t].x, modesA[t].y)]++] = make_int2((int)t, 1);
+    ent[fill[bin_of(-modesA[t].x, -modesA[t].y)]++] = make_int2((int)t, -1);
+  }
+  DevBuf<int32_t> dstart;
+  DevBuf<int2> dent;
+  DevBuf<int4> dmodes;
+  DevBuf<double> dw;
+  dstart.ensure(nb + 1);
+  dent.ensure(std::max<int64_t>(2 * KA, 1));
+  dmodes.ensure(std::max<int64_t>(KA, 1));
+  dw.ensure(std::max<int64_t>(KA, 1));
+  SRBE_CUDA(cudaMemcpyAsync(dstart.p, start.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, c->stream));
+  if (KA > 0) {
+    SRBE_CUDA(cudaMemcpyAsync(dent.p, ent.data(), sizeof(int2) * 2 * KA, cudaMemcpyHostToDevice, c->stream));
+    SRBE_CUDA(cudaMemcpyAsync(dmodes.p, modesA.data(), sizeof(int4) * KA, cudaMemcpyHostToDevice, c->stream));
+    SRBE_CUDA(cudaMemcpyAsync(dw.p, wA.data(), sizeof(double) * KA, cudaMemcpyHostToDevice, c->stream));
+  }
+  k_lat_kspace_M<<<blocks_for(nb * nl * nl, 128), 128, 0, c->stream>>>(L, dstart.p, dent.p, dmodes.p, dw.p,
+                                                                       c->tab.p, M);
+  int *flag = c->flag.ensure(1);
+  SRBE_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  k_lat_invert<<<blocks_for(nb, 64), 64, 0, c->stream>>>(L, M, Minv, 1.0 / ((double)nb * (double)nb), flag);
+  c->launches += 2;
+  SRBE_CUDA(cudaGetLastError());
+  int hflag = 0;
+  SRBE_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  SRBE_REQUIRE(hflag == 0, SRBE_ENOTCONV, "A is not positive definite (a lattice block has a non-positive pivot)");
+  Lt.spectral = true;
+}
+
+void lattice_solve(srbe_ctx *c, const double *rhs, double *y) {
+  SRBE_REQUIRE(c->lat.spectral, SRBE_ESTATE, "no spectral form of A");
+  spectral_apply(c, c->lat.Minv.p, rhs, y);
+}
+
+void lattice_apply_A(srbe_ctx *c, const double *x, double *y) {
+  SRBE_REQUIRE(c->lat.spectral, SRBE_ESTATE, "no spectral form of A");
+  spectral_apply(c, c->lat.M.p, x, y);
+}
+
+// per step: y = A^-1 (dpsi d + b), then psi_bar and Q (Eqs. 9-10)
+void charge_update_lattice(srbe_ctx *c) {
+  const int64_t ne = c->ne;
+  k_lat_rhs<<<blocks_for(ne, 256), 256, 0, c->stream>>>(ne, c->dpsi, c->ed.p, c->bvec.p, c->lat.R.p);
+  c->launches++;
+  lattice_solve(c, c->lat.R.p, c->lat.Y.p);
+  k_lat_finish<<<1, 1024, 0, c->stream>>>(ne, c->lat.Y.p, c->we.p, c->s_e, c->Q.p, c->Q32.p, c->scal.p);
+  c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }
 

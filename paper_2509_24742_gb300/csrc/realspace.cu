@@ -263,22 +263,23 @@ __device__ __forceinline__ void pair_ie(double r2, double alpha, double eta, dou
 // erfc(x) for x >= 0 from Abramowitz & Stegun 7.1.26 (Hastings' rational approximation,
 // |error| <= 1.5e-7 absolute), written against exp(-x^2) so that the force term shares it.
 __device__ __forceinline__ float erfc_as(float x, float ex2) {
-  const float t = __frcp_rn(fmaf(0.3275911f, x, 1.0f));
+  // the approximation's own error (1.5e-7) dwarfs the 2-ulp error of the fast reciprocal
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
   const float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f),
                                       -0.284496736f), 0.254829592f);
   return poly * ex2;
 }
 
-__device__ __forceinline__ void pair_ii_f(float r2, float alpha, float &phi, float &mdphi_r) {
-  const float rinv = rsqrtf(r2);
+__device__ __forceinline__ void pair_ii_f(float r2, float alpha, float &phi, float &mdphi_r, float &rinv) {
+  rinv = rsqrtf(r2);
   const float r = r2 * rinv;
   const float ex = __expf(-alpha * alpha * r2);
   phi = erfc_as(alpha * r, ex) * rinv;
   mdphi_r = (phi + (float)kTwoOverSqrtPi * alpha * ex) * (rinv * rinv);
 }
 
-__device__ __forceinline__ void pair_ie_f(float r2, float alpha, float eta, float &phi, float &mdphi_r) {
-  const float rinv = rsqrtf(r2);
+__device__ __forceinline__ void pair_ie_f(float r2, float alpha, float eta, float &phi, float &mdphi_r, float &rinv) {
+  rinv = rsqrtf(r2);
   const float r = r2 * rinv;
   const float ex = __expf(-alpha * alpha * r2);
   float p = erfc_as(alpha * r, ex) * rinv, f = p + (float)kTwoOverSqrtPi * alpha * ex;
@@ -428,13 +429,13 @@ __device__ __forceinline__ void pair_ion_ion(const PairSite &S, const CellsDev &
     const float4 o = ions.pf[pp];
     const float dx = S.Xf - (o.x + (float)ix * S.Lxf), dy = S.Yf - (o.y + (float)iy * S.Lyf), dz = S.Zf - o.z;
     const float r2 = dx * dx + dy * dy + dz * dz;
-    float phi, md2;
-    pair_ii_f(r2, S.af, phi, md2);
+    float phi, md2, rinv;
+    pair_ii_f(r2, S.af, phi, md2, rinv);
     float fs = S.qke * o.w * md2;
     if (EN) A.eii += 0.5f * S.qf * o.w * phi;
     if (lj) {
       const float2 sg = md.lj32[S.ti * md.ntype + ions.ts[pp]];
-      const float ir2 = __frcp_rn(r2), sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
+      const float ir2 = rinv * rinv, sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
       fs += 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
       if (EN) A.elj += 2.f * sg.y * (sr6 * sr6 - sr6);
     }
@@ -474,13 +475,13 @@ __device__ __forceinline__ void pair_ion_ele(const PairSite &S, const CellsDev &
     const float dx = S.Xf - (o.x + (float)ix * S.Lxf), dy = S.Yf - (o.y + (float)iy * S.Lyf), dz = S.Zf - o.z;
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float Qj = Q32[eles.order[pe]];
-    float phi, md2;
-    pair_ie_f(r2, S.af, S.etaf, phi, md2);
+    float phi, md2, rinv;
+    pair_ie_f(r2, S.af, S.etaf, phi, md2, rinv);
     float fs = S.qke * Qj * md2;
     if (EN) A.eie += S.qf * Qj * phi;
     if (md.ntype) {
       const float2 sg = md.lj32[S.ti * md.ntype + (md.ntype - 1)];
-      const float ir2 = __frcp_rn(r2), sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
+      const float ir2 = rinv * rinv, sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
       fs += 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
       if (EN) A.elj += 4.f * sg.y * (sr6 * sr6 - sr6);
     }
@@ -560,6 +561,14 @@ __device__ __forceinline__ void compacted_pairs(const PairSite &S, const CellsDe
 __device__ __forceinline__ int list_index(int32_t e) { return e & 0xffffff; }
 __device__ __forceinline__ int list_ix(int32_t e) { return ((e >> 24) & 15) - 8; }
 __device__ __forceinline__ int list_iy(int32_t e) { return ((unsigned)e >> 28) - 8; }
+// image shifts of a list entry as floats without an int-to-float conversion: the 4-bit field ORed
+// into the mantissa of 2^23 gives 2^23 + (shift + 8) exactly
+__device__ __forceinline__ float list_fx(int32_t e) {
+  return __int_as_float(0x4B000000 | (((unsigned)e >> 24) & 15u)) - 8388616.0f;
+}
+__device__ __forceinline__ float list_fy(int32_t e) {
+  return __int_as_float(0x4B000000 | ((unsigned)e >> 28)) - 8388616.0f;
+}
 __device__ __forceinline__ int32_t list_entry(int idx, int ix, int iy) {
   return (int32_t)((unsigned)idx | ((unsigned)(ix + 8) << 24) | ((unsigned)(iy + 8) << 28));
 }
@@ -621,17 +630,17 @@ __device__ __forceinline__ void ii_list_f32(const PairSite &S, const CellsDev &i
     const float4 o1 = ions.pf[i1];
     const int m1 = mdon ? ions.ms[i1] : 0, t1 = mdon ? ions.ts[i1] : 0;
     // batch b
-    const float dx = S.Xf - (o0.x + (float)list_ix(e0) * S.Lxf);
-    const float dy = S.Yf - (o0.y + (float)list_iy(e0) * S.Lyf), dz = S.Zf - o0.z;
+    const float dx = S.Xf - fmaf(list_fx(e0), S.Lxf, o0.x);
+    const float dy = S.Yf - fmaf(list_fy(e0), S.Lyf, o0.y), dz = S.Zf - o0.z;
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (base + lane < count && r2 < cut2 && r2 > 0.f) {
-      float phi, md2;
-      pair_ii_f(r2, S.af, phi, md2);
+      float phi, md2, rinv;
+      pair_ii_f(r2, S.af, phi, md2, rinv);
       float fs = S.qke * o0.w * md2;
       if (EN) A.eii += 0.5f * S.qf * o0.w * phi;
       if (mdon && m0 != S.mi) {
         const float2 sg = ljs[S.ti * md.ntype + t0];
-        const float ir2 = __frcp_rn(r2), sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
+        const float ir2 = rinv * rinv, sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
         fs += 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
         if (EN) A.elj += 2.f * sg.y * (sr6 * sr6 - sr6);
       }
@@ -663,17 +672,17 @@ __device__ __forceinline__ void ie_list_f32(const PairSite &S, const CellsDev &e
     const int j1 = list_index(e1);
     const float4 o1 = eles.pf[j1];
     const int s1 = eles.order[j1];
-    const float dx = S.Xf - (o0.x + (float)list_ix(e0) * S.Lxf);
-    const float dy = S.Yf - (o0.y + (float)list_iy(e0) * S.Lyf), dz = S.Zf - o0.z;
+    const float dx = S.Xf - fmaf(list_fx(e0), S.Lxf, o0.x);
+    const float dy = S.Yf - fmaf(list_fy(e0), S.Lyf, o0.y), dz = S.Zf - o0.z;
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (base + lane < count && r2 < cut2 && r2 > 0.f) {
       const float Qj = __ldg(Q32 + s0);
-      float phi, md2;
-      pair_ie_f(r2, S.af, S.etaf, phi, md2);
+      float phi, md2, rinv;
+      pair_ie_f(r2, S.af, S.etaf, phi, md2, rinv);
       float fs = S.qke * Qj * md2;
       if (EN) A.eie += S.qf * Qj * phi;
       if (md.ntype) {
-        const float ir2 = __frcp_rn(r2), sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
+        const float ir2 = rinv * rinv, sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
         fs += 24.f * sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
         if (EN) A.elj += 4.f * sg.y * (sr6 * sr6 - sr6);
       }
@@ -750,8 +759,8 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
     if (F32) {
       const float4 o = ions.pf[pp];
       const float dx = S.Xf - (o.x + (float)ix * S.Lxf), dy = S.Yf - (o.y + (float)iy * S.Lyf), dz = S.Zf - o.z;
-      float phi, md;
-      pair_ie_f(dx * dx + dy * dy + dz * dz, S.af, S.etaf, phi, md);
+      float phi, md, rinv;
+      pair_ie_f(dx * dx + dy * dy + dz * dz, S.af, S.etaf, phi, md, rinv);
       fn.add(-o.w * phi);
     } else {
       const double dx = X - (ions.xs[pp] + ix * Lx), dy = Y - (ions.ys[pp] + iy * Ly), dz = Z - ions.zs[pp];

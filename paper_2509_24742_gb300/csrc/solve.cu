@@ -391,6 +391,32 @@ void build_A_and_inverse(srbe_ctx *c) {
         hw.push_back(2.0 * 4.0 * kPi / (c->V * k2) * g);
       }
   const int KA = (int)hm.size();
+  const double rcut0 = xr / aA;
+  const int nimx0 = (int)std::ceil(rcut0 / Lx) + 1, nimy0 = (int)std::ceil(rcut0 / Ly) + 1;
+  const double self0 = 2.0 * (1.0 / (std::sqrt(2.0 * kPi) * c->eta) - aA / std::sqrt(kPi));
+  // lattice electrodes: the block-circulant (spectral) form of the same A, built from A's rows at
+  // the layer origins and its binned modes; beyond kDenseMaxSites it is the only form of A
+  lattice_spectral_setup(c, hm, hw, aA, rcut0, nimx0, nimy0, self0, 4.0 * kPi / c->V);
+  c->dense = ne <= kDenseMaxSites;
+  if (!c->dense) {
+    SRBE_REQUIRE(c->lat.spectral, SRBE_EINVAL,
+                 "more than 16,384 electrode sites are supported only for lattice electrodes (dense A would not fit)");
+    std::vector<double> ones(ne, 1.0), hwe(ne), hd(ne);
+    double *we = c->we.ensure(ne);
+    SRBE_CUDA(cudaMemcpyAsync(c->lat.R.p, ones.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, c->stream));
+    lattice_solve(c, c->lat.R.p, we);
+    SRBE_CUDA(cudaMemcpyAsync(hwe.data(), we, sizeof(double) * ne, cudaMemcpyDeviceToHost, c->stream));
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    for (int64_t j = 0; j < ne; ++j) hd[j] = c->hside[j] ? 0.5 : -0.5;
+    double s = 0.0;
+    for (int64_t j = 0; j < ne; ++j) s += hwe[j];
+    SRBE_REQUIRE(s > 0.0, SRBE_ENOTCONV, "e^T A^-1 e is not positive");
+    c->s_e = s;
+    c->wd = host_dot(hwe, hd);
+    c->bsplit.ensure(ne);
+    c->lat_solve = true;
+    return;
+  }
   DevBuf<int4> dmA;
   DevBuf<double> dw, Ct, St, rowp, colp;
   dmA.ensure(KA);
@@ -466,6 +492,8 @@ void build_A_and_inverse(srbe_ctx *c) {
   c->launches += 4;
   SRBE_CUDA(cudaGetLastError());
   SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  // the spectral solve is the default where it beats the dense matrix-vector product
+  c->lat_solve = c->lat.spectral && ne >= kLatSolveMinSites;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -663,6 +691,10 @@ void pcg_prepare(srbe_ctx *c) {
 }
 
 void charge_update(srbe_ctx *c) {
+  if (c->lat_solve) {
+    charge_update_lattice(c);
+    return;
+  }
   if (c->pcg.on) {
     if (c->pcg.warm == 0) {
       SRBE_CUDA(cudaMemsetAsync(c->pcg.y.p, 0, sizeof(double) * c->ne, c->stream));
@@ -735,9 +767,30 @@ __global__ void k_cp_residual_sum(int64_t n, const double *__restrict__ rr, doub
   }
 }
 
+// the same residual from a precomputed A Q (spectral form of A, no dense matrix)
+__global__ void k_cp_residual_vec(int64_t n, const double *__restrict__ AQ, const double *__restrict__ d,
+                                  const double *__restrict__ b, double dpsi, const double *__restrict__ scal,
+                                  double *__restrict__ rr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double rhs = fma(dpsi, d[i], b[i]);
+  const double r = AQ[i] - rhs - scal[kScalPsi];
+  rr[2 * i] = r * r;
+  rr[2 * i + 1] = rhs * rhs;
+}
+
 void charge_residual(srbe_ctx *c, double *out_dev) {
   const int64_t n = c->ne;
   double *rr = c->resid.ensure((size_t)2 * std::max<int64_t>(n, 1));
+  if (!c->dense) {
+    double *aq = c->lat.Y.p;
+    lattice_apply_A(c, c->Q.p, aq);
+    k_cp_residual_vec<<<blocks_for(n, 256), 256, 0, c->stream>>>(n, aq, c->ed.p, c->bvec.p, c->dpsi, c->scal.p, rr);
+    k_cp_residual_sum<<<1, 256, 0, c->stream>>>(n, rr, out_dev);
+    c->launches += 2;
+    SRBE_CUDA(cudaGetLastError());
+    return;
+  }
   k_cp_residual_rows<<<blocks_for(n * 32, 256), 256, 0, c->stream>>>(n, c->Amat.p, c->Q.p, c->ed.p, c->bvec.p,
                                                                       c->dpsi, c->scal.p, rr);
   k_cp_residual_sum<<<1, 256, 0, c->stream>>>(n, rr, out_dev);

@@ -17,6 +17,8 @@ namespace srbe {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kBoltz = 0.0083144626;     // kJ mol^-1 K^-1
 constexpr int64_t kMaxModes = 32 * 65535;   // modes per list: 32-mode tiles on a grid's y dimension
+constexpr int64_t kDenseMaxSites = 16384;    // dense A and its inverse (3 x n^2 x 8 B) only up to here
+constexpr int64_t kLatSolveMinSites = 8192;  // lattice electrodes from here solve through the spectral form
 constexpr int kTabBits = 10;                  // sin/cos table of 1024 entries per turn
 constexpr int kTab = 1 << kTabBits;
 constexpr int kGatherThreads = 256;           // gather kernels: one warp per particle
@@ -153,6 +155,12 @@ struct Lattice {
   DevBuf<double2> T, Qh;                       // [nl][ny][nx] transform scratch
   DevBuf<double> bF;                           // far part of b per site
   DevBuf<double2> E;                           // per-step e^{i phi_l(k)} [K][nl]
+  // spectral form of A: A is block-circulant over the lattice, A y = sum_bins w^{-bin.i} M(bin) Yhat(bin)
+  // with nl x nl Hermitian blocks M per bin (a, b); Minv holds M^-1 / (nx ny)^2 for the exact solve
+  bool spectral = false;
+  DevBuf<double2> M, Minv;                     // [ny][nx][nl][nl]
+  DevBuf<double> R, Y;                         // per-site scratch (right-hand side, solution)
+  DevBuf<double> Rrow;                         // [nl][ne] real-space rows of A at the layer origins
   int mode = 1;                                // 0 never, 1 when it pays (N_ele K large), 2 always
   int64_t min_work = 4000000;                  // N_ele x K from which mode 1 takes the lattice path
   bool active(int64_t ne, int K) const {
@@ -259,6 +267,8 @@ struct srbe_ctx {
   cudaEvent_t coop_chain = nullptr;
 
   srbe::Lattice lat;                           // lattice electrode path (Eqs. 15, 24 separated per layer)
+  bool dense = true;                           // dense A / projected inverse exist
+  bool lat_solve = false;                      // charge update through the spectral form of A
 
   // Langevin thermostat (Eq. 39): collision rate (1/ps, 0 = off), temperature (K), noise seed
   double lang_gamma = 0.0, lang_T = 0.0;
@@ -383,6 +393,11 @@ void lattice_setup(srbe_ctx *c, const std::vector<double> &x, const std::vector<
                    const std::vector<double> &z);
 void lattice_bfar(srbe_ctx *c);
 void lattice_s2(srbe_ctx *c, double2 *S, const double2 *S1, int mslot);
+void lattice_spectral_setup(srbe_ctx *c, const std::vector<int4> &modesA, const std::vector<double> &wA,
+                            double alpha_A, double rcut, int nimx, int nimy, double self, double slab);
+void lattice_solve(srbe_ctx *c, const double *rhs, double *y);
+void lattice_apply_A(srbe_ctx *c, const double *x, double *y);
+void charge_update_lattice(srbe_ctx *c);
 void coop_before(srbe_ctx *c);
 void coop_after(srbe_ctx *c);
 cudaEvent_t device_coop_chain();

@@ -14,7 +14,7 @@ from . import build as _build
 
 SRBE_OK, SRBE_EINVAL, SRBE_ENOMEM, SRBE_ECUDA, SRBE_ESTATE, SRBE_ENOTCONV, SRBE_ETIMEOUT = range(7)
 FP64, MIXED = 0, 1
-DIRECT, PCG = 0, 1
+DIRECT, PCG, LATTICE = 0, 1, 2
 WARM_ZERO, WARM_PREVIOUS, WARM_MODEL = 0, 1, 2
 N_DESC = 80
 METROPOLIS, EXACT = 0, 1
@@ -85,6 +85,7 @@ EXPORTS = {
     "srbe_lattice_info": ([_vp, _ip], _int),
     "srbe_set_skin": ([_vp, _dbl], _int),
     "srbe_get_skin": ([_vp], _dbl),
+    "srbe_get_alpha_A": ([_vp], _dbl),
     "srbe_autotune_skin": ([_vp, _int, _u64, _dp, _int, _dp], _int),
     "srbe_batch_create": ([_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _int),
     "srbe_batch_destroy": ([_vp], _int),
@@ -175,6 +176,10 @@ class Context:
 
     def set_A_params(self, alpha_A=0.0, tol=0.0):
         self._check(self.lib.srbe_set_A_params(self.h, float(alpha_A), float(tol)))
+
+    def alpha_A(self):
+        """The Ewald parameter A was built with."""
+        return self.lib.srbe_get_alpha_A(self.h)
 
     def set_electrode(self, R, side):
         R = _d(R).reshape(-1, 3)

@@ -168,7 +168,8 @@ def test_md_steps_match_oracle(orc, thermostat):
 @pytest.mark.parametrize("precision,solver,thermo,lattice", [(srbe.FP64, srbe.DIRECT, 0.0, 0),
                                                              (srbe.MIXED, srbe.DIRECT, 5.0, 0),
                                                              (srbe.MIXED, srbe.PCG, 0.0, 0),
-                                                             (srbe.FP64, srbe.DIRECT, 5.0, 2)])
+                                                             (srbe.FP64, srbe.DIRECT, 5.0, 2),
+                                                             (srbe.MIXED, srbe.LATTICE, 5.0, 2)])
 def test_graph_replay_is_bitwise_the_ordinary_path(precision, solver, thermo, lattice):
     """srbe_step replaying its captured CUDA graphs gives bitwise the trajectory of the ordinary
     launch path, across several calls, a read-back in between and a state change that recaptures."""
@@ -182,6 +183,8 @@ def test_graph_replay_is_bitwise_the_ordinary_path(precision, solver, thermo, la
             ctx.set_lattice(lattice)
             if solver == srbe.PCG:
                 ctx.set_solver(srbe.PCG, tol=1e-10, maxit=500, warm=srbe.WARM_PREVIOUS)
+            elif solver == srbe.LATTICE:
+                ctx.set_solver(srbe.LATTICE)
             ctx.step(3, 91)
             r1, v1 = ctx.get_positions(velocities=True)
             ctx.step(5, 91)
