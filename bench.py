@@ -357,13 +357,15 @@ def e2e_arm(ctx, slab, stream, flush, steps):
 
 # ---------------------------------------------------------------------------------------------- precision form
 def prec_arm(args):
-    """The 100k-particle slab (12,288 electrode sites, P = 500, 2 V): MD steps/s of the mixed form
-    and of the plain FP64 path, their errors and FP64 charge residuals, and the phase split."""
+    """The 100k-particle slab (12,288 electrode sites, P = 500, 2 V) or the 1.2 M-particle slab
+    (98,304 sites, P = 1000): MD steps/s of the mixed form and of the plain FP64 path, their errors
+    and FP64 charge residuals, and the phase split."""
     import torch
     from paper_2509_24742_gb300 import srbe, workloads
     torch.cuda.set_device(0)
     t0 = time.time()
-    slab = workloads.precision_100k()
+    big = args.workload == "large1m"
+    slab = workloads.large_1m() if big else workloads.precision_100k()
     stream = torch.cuda.Stream()
     ctx = srbe.from_slab(slab, precision=srbe.MIXED, md=True)
     t_setup = time.time() - t0
@@ -380,9 +382,10 @@ def prec_arm(args):
     rms_q = float(np.sqrt(((Q32 - Q64) ** 2).mean() / (Q64 ** 2).mean()))
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     out = {}
-    for name, prec, steps in (("mixed", srbe.MIXED, args.steps), ("fp64", srbe.FP64, max(3, min(args.steps, 30)))):
+    n_fp64 = 2 if big else max(3, min(args.steps, 30))
+    for name, prec, steps in (("mixed", srbe.MIXED, args.steps), ("fp64", srbe.FP64, n_fp64)):
         ctx.set_precision(prec)
-        ctx.step(args.warmup, SEED)
+        ctx.step(args.warmup if name == "mixed" else 1, SEED)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for i in range(steps):
@@ -393,22 +396,26 @@ def prec_arm(args):
                 flush.zero_()
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev)
+        n_tr = max(2, min(steps, 20))
         ctx.set_profiling(True)
-        ctx.step(max(3, min(steps, 20)), SEED)
+        ctx.step(n_tr, SEED)
         ph = ctx.phase_times()
         ctx.set_profiling(False)
-        n_tr = max(3, min(steps, 20))
         out[name] = {"steps_per_s": steps / (ms * 1e-3), "ms_per_step": ms / steps,
                      "phases_ms_per_step": {p: round(v[0] / n_tr, 5) for p, v in ph.items() if v[1]}}
     _, v = ctx.get_positions(velocities=True)
     T_end = float((slab.mass[:, None] * v ** 2).sum() / (3 * slab.n_ion * KB))
     lat = ctx.lattice_info()
     ctx.close()
-    return {"metric": "SRBE MD steps/sec on 1 GB300, precision form, 100k-particle slab",
+    wl_name = ("large1m_P1000: 24x24x60 nm, 98,304 electrode + 1,100,000 ion sites, P=1000, M=2, alpha 1.2, "
+               "rc 2.5, 2 V, dt=2 fs, spectral lattice solve" if big else
+               "prec100k_P500: 8x8x32 nm, 12,288 electrode + 87,712 ion sites, P=500, M=4, alpha 1.87, rc 1.6, "
+               "2 V, dt=2 fs")
+    return {"metric": "SRBE MD steps/sec on 1 GB300, %s" % ("1.2M-particle slab" if big else
+                                                          "precision form, 100k-particle slab"),
             "value": out["mixed"]["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "prec100k_P500: 8x8x32 nm, 12,288 electrode + 87,712 ion sites, P=500, M=4, "
-                                   "2 V, dt=2 fs", "l2": "flushed between timed steps (256 MB write)",
+            "config": {"workload": wl_name, "l2": "flushed between timed steps (256 MB write)",
                        "lattice_electrode": lat},
             "accuracy": {"rms_force_err_vs_fp64_gpu": rms_f, "rms_charge_err_vs_fp64_gpu": rms_q,
                          "fp64_charge_residual_mixed": res32, "fp64_charge_residual_fp64": res64},
@@ -601,7 +608,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="md11072", choices=["md11072", "batch64", "prec100k", "solve6144"])
+    ap.add_argument("--workload", default="md11072",
+                    choices=["md11072", "batch64", "prec100k", "solve6144", "large1m"])
     ap.add_argument("--replicas", type=int, default=64)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -616,7 +624,7 @@ def main():
     if args.workload == "batch64":
         print(json.dumps(batch_arm(args)))
         return
-    if args.workload == "prec100k":
+    if args.workload in ("prec100k", "large1m"):
         print(json.dumps(prec_arm(args)))
         return
     if args.workload == "solve6144":
