@@ -92,6 +92,7 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
                double *__restrict__ mpart, SfFinish fin, int *__restrict__ done) {
   __shared__ uint64_t su[3][kSfThreads];
   __shared__ double sw[kSfThreads];
+  __shared__ float sw32[kSfThreads];          // the weights in FP32 (mixed form), converted once
   __shared__ double2 red[4][32];
   __shared__ double mred[kSfThreads];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -109,6 +110,7 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
       su[1][t] = to_turns64(y[i], invL.y);
       su[2][t] = to_turns64(z[i], invL.z);
       sw[t] = w[i];
+      if (F32) sw32[t] = (float)sw[t];
       if (blockIdx.y == 0) mz = fma(w[i], z[i], mz);
     }
     __syncthreads();
@@ -126,7 +128,7 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
                             (uint32_t)m.z * (uint32_t)(su[2][j] >> 32);
         float c, s;
         sincos_turns32(th, c, s);
-        const float wf = (float)sw[j];
+        const float wf = sw32[j];
         fre.add(wf * c);
         fim.add(wf * s);
       }

@@ -1193,9 +1193,9 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
         sincos_turns32((uint32_t)m.x * vx + (uint32_t)m.y * vy + (uint32_t)m.z * vz, cs, sn);
         const float2 cf = __ldg(&coefF32[k]);
         const float im = cf.x * cs - cf.y * sn;
-        ak0 = fmaf((float)m.x, im, ak0);
-        ak1 = fmaf((float)m.y, im, ak1);
-        ak2 = fmaf((float)m.z, im, ak2);
+        ak0 = fmaf(small_int_to_float(m.x), im, ak0);
+        ak1 = fmaf(small_int_to_float(m.y), im, ak1);
+        ak2 = fmaf(small_int_to_float(m.z), im, ak2);
       }
     }
     // ---- real space: Coulomb of Eq. 13 (Gaussian units) and LJ (kJ/mol/nm), compacted pairs

@@ -354,9 +354,18 @@ __device__ __forceinline__ void sincos_turns(uint64_t th, const double2 *__restr
 
 // FP32 form: phase in turns from 32-bit fixed point (top half), reduced to [-pi, pi).
 __device__ __forceinline__ uint32_t to_turns32(double x, double invL) { return (uint32_t)(to_turns64(x, invL) >> 32); }
+// small integer (|v| < 2^22) to float without a conversion instruction: added to the mantissa of
+// 1.5 x 2^23, where the float spacing is 1, then the offset removed (exact)
+__device__ __forceinline__ float small_int_to_float(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+
+// FP32 sin/cos of a 32-bit phase in turns: the top 23 bits (a signed value below 2^22 in
+// magnitude, so converted exactly without a conversion instruction) times 2 pi / 2^23; the 7.5e-7
+// rad step is below __sincosf's own error on [-pi, pi)
 __device__ __forceinline__ void sincos_turns32(uint32_t th, float &c, float &s) {
-  constexpr float kTurn32 = (float)(2.0 * kPi / 4294967296.0);     // 2 pi / 2^32
-  const float a = (float)(int32_t)th * kTurn32;
+  constexpr float kTurn23 = (float)(2.0 * kPi / 8388608.0);         // 2 pi / 2^23
+  const float a = small_int_to_float((int32_t)th >> 9) * kTurn23;
   __sincosf(a, &s, &c);
 }
 
