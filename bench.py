@@ -160,14 +160,22 @@ def committed_traffic(kernel, precision):
     return None
 
 
+def solve_bytes(ne, precision):
+    """Bytes one charge update must move: the projected inverse (n x n, as (hi, lo) FP32 pairs in
+    the mixed form, FP64 otherwise: 8 bytes an entry either way) plus the vectors (b, q_d, w_e in,
+    Q and its FP32 copy out)."""
+    return ne * ne * 8 + 6 * 8 * ne
+
+
 def roofline(phase, ms_per_launch, slab, K, n_ii, n_ie, precision, pk):
     """Roofline of the dominant phase: algorithmic work per launch / its event-timed duration."""
     t = ms_per_launch * 1e-3
     if phase == "solve":
-        byts = slab.n_ele ** 2 * 8 + 4 * slab.n_ele * 8     # FP64 projected inverse + vectors
+        byts = solve_bytes(slab.n_ele, precision)
         ach = byts / t / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
-                "peak_source": pk["hbm_source"], "algorithmic_bytes": byts, "kernel": "k_gemv_rows"}
+                "peak_source": pk["hbm_source"], "algorithmic_bytes": byts,
+                "kernel": "k_charges_split" if precision == "mixed" else "k_charges_fp64"}
     if phase == "forces":
         flops = slab.n_ion * K * FLOP_MODE + (2 * n_ii + n_ie) * FLOP_PAIR
         kern = "k_ion_forces"
@@ -437,7 +445,7 @@ def solve_arm(args):
     ne = slab.n_ele
     out = {}
     with srbe.from_slab(slab, precision=srbe.MIXED) as ctx:
-        for name, prec, mbytes in (("mixed", srbe.MIXED, 8), ("fp64", srbe.FP64, 8)):
+        for name, prec in (("mixed", srbe.MIXED), ("fp64", srbe.FP64)):
             ctx.set_precision(prec)
             ctx.sample_k(SEED, 0)
             for _ in range(args.warmup):
@@ -449,7 +457,7 @@ def solve_arm(args):
             ph = ctx.phase_times()
             ctx.set_profiling(False)
             ms = ph["solve"][0] / ph["solve"][1]
-            byts = mbytes * ne * ne + 6 * 8 * ne    # (hi, lo) FP32 or FP64 matrix + the vectors
+            byts = solve_bytes(ne, name)
             ach = byts / (ms * 1e-3) / 1e9
             out[name] = {"ms_per_launch": ms, "algorithmic_bytes": byts,
                          "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",

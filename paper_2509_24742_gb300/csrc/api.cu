@@ -279,8 +279,10 @@ struct srbe::HostExt {
   bool forces_valid = false;
   // CUDA graphs of one MD step, one per pinned staging slot of the mode list (ping-pong)
   struct Slot {
-    int4 *hm = nullptr;
+    int4 *hm = nullptr;           // mapped pinned memory: the host writes, a captured step reads
     double *hw = nullptr;
+    const int4 *dhm = nullptr;    // the same buffers as device pointers
+    const double *dhw = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t done = nullptr;
   } slot[2];
@@ -529,13 +531,51 @@ void srbe_list_from_samples(srbe_ctx *c, const int32_t *samp, int P) {
 // per slot and replayed; the host fills the other slot while the GPU runs.
 void forces_pass(srbe_ctx *c, bool energies);
 
-void device_step(srbe_ctx *c, int slot) {
+// the captured step's mode list (K int4 + the step word) and weights, read from a mapped pinned slot
+__global__ void k_stage_modes(int K, const int4 *__restrict__ hm, const double *__restrict__ hw,
+                              int4 *__restrict__ dm, double *__restrict__ dc) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
+    dm[k] = hm[k];
+    if (k < K) dc[k] = hw[k];
+  }
+}
+
+// the same for every replica of a batch graph at once, one block per replica
+struct StageEntry {
+  const int4 *hm;
+  const double *hw;
+  int4 *dm;
+  double *dc;
+  int K;
+};
+__global__ void k_stage_many(const StageEntry *__restrict__ tab) {
+  const StageEntry s = tab[blockIdx.x];
+  for (int k = threadIdx.x; k <= s.K; k += blockDim.x) {
+    s.dm[k] = s.hm[k];
+    if (k < s.K) s.dc[k] = s.hw[k];
+  }
+}
+
+// one captured MD step of c; staged: the mode list is already on the device (batch graphs)
+void device_step(srbe_ctx *c, int slot, bool staged) {
   Extra *e = extra(c);
   const int K = c->K;
-  SRBE_CUDA(cudaMemcpyAsync(c->dm.p, e->slot[slot].hm, sizeof(int4) * (K + 1), cudaMemcpyHostToDevice, c->stream));
-  if (K > 0)
-    SRBE_CUDA(cudaMemcpyAsync(c->dc.p, e->slot[slot].hw, sizeof(double) * K, cudaMemcpyHostToDevice, c->stream));
+  SRBE_REQUIRE(c->dm.cap > (size_t)K && c->dc.cap >= (size_t)K && e->slot[slot].dhm, SRBE_ESTATE,
+               "mode buffers not reserved for a captured step");
+  if (!staged) {
+    // the mode list comes in through a kernel on the side stream that reads the pinned slot while
+    // the opening kick runs (nothing before S1 reads it; the opening kick has no thermostat)
+    SRBE_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+    SRBE_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    k_stage_modes<<<std::min(blocks_for((int64_t)K + 1, 256), 64u), 256, 0, c->side>>>(K, e->slot[slot].dhm,
+                                                                                       e->slot[slot].dhw, c->dm.p,
+                                                                                       c->dc.p);
+    c->launches++;
+    SRBE_CUDA(cudaGetLastError());
+    SRBE_CUDA(cudaEventRecord(c->ev_modes, c->side));
+  }
   integrate_kick_drift(c, 0.5 * c->dt, true);
+  if (!staged) SRBE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_modes, 0));
   forces_pass(c, false);
   integrate_kick_drift(c, 0.5 * c->dt, false);
 }
@@ -549,12 +589,20 @@ void ensure_slot_buffers(srbe_ctx *c) {
       if (sl.hw) cudaFreeHost(sl.hw);
       sl.hm = nullptr;
       sl.hw = nullptr;
+      sl.dhm = nullptr;
+      sl.dhw = nullptr;
     }
     e->slot_cap = 0;
   }
   for (auto &sl : e->slot) {
-    if (!sl.hm) SRBE_CUDA(cudaMallocHost((void **)&sl.hm, sizeof(int4) * (std::max(c->K, 1) + 1)));
-    if (!sl.hw) SRBE_CUDA(cudaMallocHost((void **)&sl.hw, sizeof(double) * std::max(c->K, 1)));
+    if (!sl.hm) {
+      SRBE_CUDA(cudaHostAlloc((void **)&sl.hm, sizeof(int4) * (std::max(c->K, 1) + 1), cudaHostAllocMapped));
+      SRBE_CUDA(cudaHostGetDevicePointer((void **)&sl.dhm, sl.hm, 0));
+    }
+    if (!sl.hw) {
+      SRBE_CUDA(cudaHostAlloc((void **)&sl.hw, sizeof(double) * std::max(c->K, 1), cudaHostAllocMapped));
+      SRBE_CUDA(cudaHostGetDevicePointer((void **)&sl.dhw, sl.hw, 0));
+    }
     if (!sl.done) {
       SRBE_CUDA(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
       SRBE_CUDA(cudaEventRecord(sl.done, c->stream));
@@ -585,7 +633,7 @@ void fill_slot(srbe_ctx *c, int slot) {
 // ever run at the same time.  kernels[r] receives the kernels one replay runs for context r.
 // Returns false (and leaves nothing captured) when capture is not possible.
 bool capture_graphs(srbe_ctx *const *ctxs, int n, cudaStream_t main, int width, const cudaStream_t *forks,
-                    cudaGraphExec_t out[2], int64_t *kernels) {
+                    cudaGraphExec_t out[2], int64_t *kernels, DevBuf<StageEntry> *stage_tabs) {
   std::vector<int64_t> launches0(n);
   for (int r = 0; r < n; ++r) launches0[r] = ctxs[r]->launches;
   std::vector<cudaStream_t> saved(n);
@@ -608,11 +656,34 @@ bool capture_graphs(srbe_ctx *const *ctxs, int n, cudaStream_t main, int width, 
   out[0] = out[1] = nullptr;
   for (int slot = 0; slot < 2 && ok; ++slot) {
     cudaGraph_t g = nullptr;
+    // with stage tables, every context's mode list of this slot comes in through one kernel at the
+    // head of the graph (its pointers are fixed while the graph lives)
+    if (stage_tabs) {
+      try {
+        std::vector<StageEntry> h(n);
+        for (int r = 0; r < n; ++r) {
+          srbe_ctx *c = ctxs[r];
+          const auto &sl = extra(c)->slot[slot];
+          SRBE_REQUIRE(sl.dhm && c->dm.cap > (size_t)c->K && c->dc.cap >= (size_t)c->K, SRBE_ESTATE,
+                       "mode buffers not reserved for a captured step");
+          h[r] = StageEntry{sl.dhm, sl.dhw, c->dm.p, c->dc.p, c->K};
+        }
+        StageEntry *d = stage_tabs[slot].ensure(n);
+        SRBE_CUDA(cudaMemcpy(d, h.data(), sizeof(StageEntry) * n, cudaMemcpyHostToDevice));
+      } catch (const Error &) {
+        ok = false;
+        break;
+      }
+    }
     if (cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       ok = false;
       break;
     }
     try {
+      if (stage_tabs) {
+        k_stage_many<<<n, 256, 0, main>>>(stage_tabs[slot].p);
+        SRBE_CUDA(cudaGetLastError());
+      }
       SRBE_CUDA(cudaEventRecord(chain, main));
       SRBE_CUDA(cudaEventRecord(fork_ev, main));
       for (int r = 0; r < n; ++r) {
@@ -625,8 +696,8 @@ bool capture_graphs(srbe_ctx *const *ctxs, int n, cudaStream_t main, int width, 
           c->stream = main;
         }
         const int64_t l0 = c->launches;
-        device_step(c, slot);
-        kernels[r] = c->launches - l0;
+        device_step(c, slot, stage_tabs != nullptr);
+        kernels[r] = c->launches - l0 + (stage_tabs && r == 0 ? 1 : 0);
         if (width > 0) {
           SRBE_CUDA(cudaEventRecord(join[r], c->stream));
           SRBE_CUDA(cudaStreamWaitEvent(main, join[r], 0));
@@ -815,6 +886,7 @@ int srbe_create(const double box[3], double alpha, double eta, double rc, int P,
     SRBE_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_modes, cudaEventDisableTiming));
     upload_table(c);
     c->scal.ensure(kScalCount);
     SRBE_CUDA(cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScalCount, c->stream));
@@ -838,6 +910,7 @@ int srbe_destroy(srbe_ctx *c) {
   if (c->stage_done) cudaEventDestroy(c->stage_done);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_modes) cudaEventDestroy(c->ev_modes);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   c->stream = nullptr;
@@ -1197,7 +1270,7 @@ int srbe_step(srbe_ctx *c, int nsteps, uint64_t seed0) {
       cudaGraphExec_t ex[2] = {nullptr, nullptr};
       srbe_ctx *one[1] = {c};
       if (!e->cap) SRBE_CUDA(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
-      if (capture_graphs(one, 1, e->cap, 0, nullptr, ex, &e->graph_kernels)) {
+      if (capture_graphs(one, 1, e->cap, 0, nullptr, ex, &e->graph_kernels, nullptr)) {
         e->slot[0].exec = ex[0];
         e->slot[1].exec = ex[1];
         e->graph_dirty = false;
@@ -1631,6 +1704,7 @@ struct srbe_batch {
   cudaEvent_t done[2] = {nullptr, nullptr};
   cudaEvent_t mark = nullptr;
   DevBuf<double> res;                // residual sums [n][2]
+  DevBuf<StageEntry> stage[2];       // per slot: where each replica's mode list comes from and goes
   double *h_res = nullptr;
   uint64_t t = 0;
   bool dirty = true;
@@ -1740,7 +1814,8 @@ void batch_capture(srbe_batch *b, const uint64_t *seeds) {
     b->forks.push_back(f);
   }
   b->kernels.assign(n, 0);
-  SRBE_REQUIRE(capture_graphs(b->ctx.data(), n, b->main, b->width, b->forks.data(), b->exec, b->kernels.data()),
+  SRBE_REQUIRE(capture_graphs(b->ctx.data(), n, b->main, b->width, b->forks.data(), b->exec, b->kernels.data(),
+                              b->stage),
                SRBE_ECUDA, "capture of the batch step failed");
   b->epoch.resize(n);
   for (int r = 0; r < n; ++r) {

@@ -187,6 +187,7 @@ struct srbe_ctx {
   bool own_stream = false;
   cudaStream_t side = nullptr;                 // neighbour-list work beside S1 (joined before b)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_modes = nullptr;              // a captured step's mode list staged (side stream)
   std::string err;
 
   bool have_ele = false, have_pos = false, have_modes = false, have_md = false;
