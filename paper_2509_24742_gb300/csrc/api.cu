@@ -529,7 +529,7 @@ void srbe_list_from_samples(srbe_ctx *c, const int32_t *samp, int P) {
 // The device half of a step (mode-list copy from a pinned slot, kick/drift, the force pass, kick) has
 // no host synchronisation and no allocation once the buffers are reserved, so it is captured once
 // per slot and replayed; the host fills the other slot while the GPU runs.
-void forces_pass(srbe_ctx *c, bool energies);
+void forces_pass(srbe_ctx *c, bool energies, bool after_drift = false);
 
 // the captured step's mode list (K int4 + the step word) and weights, read from a mapped pinned slot
 __global__ void k_stage_modes(int K, const int4 *__restrict__ hm, const double *__restrict__ hw,
@@ -576,7 +576,7 @@ void device_step(srbe_ctx *c, int slot, bool staged) {
   }
   integrate_kick_drift(c, 0.5 * c->dt, true);
   if (!staged) SRBE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_modes, 0));
-  forces_pass(c, false);
+  forces_pass(c, false, true);
   integrate_kick_drift(c, 0.5 * c->dt, false);
 }
 
@@ -730,7 +730,8 @@ void require_state(srbe_ctx *c, bool pos) {
   SRBE_REQUIRE(c->have_modes, SRBE_ESTATE, "no mode list: call srbe_sample_k, srbe_set_k or srbe_set_mode_list");
 }
 
-void charges_pass(srbe_ctx *c) {
+// after_drift: this step's drift has just written the ions' phase coordinates (c->iu)
+void charges_pass(srbe_ctx *c, bool after_drift) {
   reserve(c);
   // the neighbour refresh / rebuild (reads x, y, z; writes the sorted copies and lists) runs on the
   // context's side stream beside S1 (reads x, y, z, q) and joins before b, which needs both
@@ -749,7 +750,8 @@ void charges_pass(srbe_ctx *c) {
   c->stream = main;
   SRBE_CUDA(cudaEventRecord(c->ev_join, c->side));
   phase_begin(c, kPhS1);
-  structure_factor(c, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->S1.p, nullptr, kScalMion, 0);
+  structure_factor(c, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->S1.p, nullptr, kScalMion, 0,
+                   after_drift ? c->iu.p : nullptr);
   phase_end(c, kPhS1);
   SRBE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   phase_begin(c, kPhRhs);
@@ -760,11 +762,11 @@ void charges_pass(srbe_ctx *c) {
   phase_end(c, kPhSolve);
 }
 
-void forces_pass(srbe_ctx *c, bool energies) {
-  charges_pass(c);
+void forces_pass(srbe_ctx *c, bool energies, bool after_drift) {
+  charges_pass(c, after_drift);
   phase_begin(c, kPhS2);
   if (c->lat.active(c->ne, c->K)) lattice_s2(c, c->S2.p, c->S1.p, kScalMele);
-  else structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele, 1);
+  else structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele, 1, c->eu.p);
   phase_end(c, kPhS2);
   phase_begin(c, kPhForces);
   ion_forces(c, energies);
@@ -806,7 +808,7 @@ void eager_step(srbe_ctx *c, uint64_t seed0) {
   phase_begin(c, kPhIntegrate);
   integrate_kick_drift(c, 0.5 * c->dt, true);
   phase_end(c, kPhIntegrate);
-  forces_pass(c, false);
+  forces_pass(c, false, true);
   phase_begin(c, kPhIntegrate);
   integrate_kick_drift(c, 0.5 * c->dt, false);
   phase_end(c, kPhIntegrate);
@@ -1224,7 +1226,7 @@ int srbe_set_mode_list(srbe_ctx *c, const int32_t *m, const double *w, int K) {
 int srbe_solve_electrode_charges(srbe_ctx *c, double *Q, double *psi_bar, double *b) {
   return guarded(c, [&] {
     require_state(c, true);
-    charges_pass(c);
+    charges_pass(c, false);
     download_outputs(c, nullptr, Q, psi_bar, nullptr, b);
   });
 }

@@ -87,7 +87,8 @@ __device__ __forceinline__ void sf_finish(const SfFinish &f, int k, int lane) {
 template <bool F32>
 __global__ void __launch_bounds__(kSfThreads)
 k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-               const double *__restrict__ w, int K, const int4 *__restrict__ modes, double3 invL,
+               const uint64_t *__restrict__ u, const double *__restrict__ w, int K, const int4 *__restrict__ modes,
+               double3 invL,
                const double2 *__restrict__ tab, int64_t chunk, double2 *__restrict__ partial,
                double *__restrict__ mpart, SfFinish fin, int *__restrict__ done) {
   __shared__ uint64_t su[3][kSfThreads];
@@ -106,9 +107,15 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
     __syncthreads();
     const int64_t i = base + t;
     if (i < i1) {
-      su[0][t] = to_turns64(x[i], invL.x);
-      su[1][t] = to_turns64(y[i], invL.y);
-      su[2][t] = to_turns64(z[i], invL.z);
+      if (u) {
+        su[0][t] = u[i];
+        su[1][t] = u[n + i];
+        su[2][t] = u[2 * n + i];
+      } else {
+        su[0][t] = to_turns64(x[i], invL.x);
+        su[1][t] = to_turns64(y[i], invL.y);
+        su[2][t] = to_turns64(z[i], invL.z);
+      }
       sw[t] = w[i];
       if (F32) sw32[t] = (float)sw[t];
       if (blockIdx.y == 0) mz = fma(w[i], z[i], mz);
@@ -227,7 +234,7 @@ int64_t sfac_chunks(int64_t n, int K, int64_t *chunk) {
 }
 
 void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *w,
-                      double2 *S, const double2 *S_add, int mslot, int coef_mode) {
+                      double2 *S, const double2 *S_add, int mslot, int coef_mode, const uint64_t *u) {
   const int K = c->K;
   const int ktiles = std::max(1, (K + 31) / 32);
   int64_t chunk;
@@ -242,10 +249,10 @@ void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, 
     SRBE_REQUIRE(c->sfdone.cap >= (size_t)ktiles, SRBE_ESTATE, "tile counters not reserved for this size");
     dim3 grid((unsigned)nchunk, (unsigned)ktiles);
     if (c->precision == SRBE_MIXED)
-      k_sfac_partial<true><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, w, K, c->dm.p, invL, c->tab.p, chunk,
+      k_sfac_partial<true><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, u, w, K, c->dm.p, invL, c->tab.p, chunk,
                                                                c->partial.p, c->mpart.p, f, c->sfdone.p);
     else
-      k_sfac_partial<false><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, w, K, c->dm.p, invL, c->tab.p, chunk,
+      k_sfac_partial<false><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, u, w, K, c->dm.p, invL, c->tab.p, chunk,
                                                                 c->partial.p, c->mpart.p, f, c->sfdone.p);
     c->launches++;
     c->mode_evals += n * (int64_t)K;

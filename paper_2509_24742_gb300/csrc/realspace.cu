@@ -697,6 +697,30 @@ __device__ __forceinline__ void ie_list_f32(const PairSite &S, const CellsDev &e
   }
 }
 
+// FP32 pass over an electrode site's Verlet list (the mixed form's near part of b, Eq. 19): the
+// same three-stage pipeline as the ion passes, Kahan-compensated sum of -q_i phi_ie
+__device__ __forceinline__ void ei_list_f32(const PairSite &S, const CellsDev &ions, const int32_t *__restrict__ list,
+                                            int count, float cut2, int lane, KahanF32 &acc) {
+  auto entry = [&](int k) { return k < count ? __ldg(list + k) : 0; };
+  int32_t e0 = entry(lane), e1 = entry(32 + lane);
+  float4 o0 = ions.pf[list_index(e0)];
+  for (int base = 0; base < count; base += 32) {
+    const int32_t e2 = entry(base + 64 + lane);
+    const float4 o1 = ions.pf[list_index(e1)];
+    const float dx = S.Xf - fmaf(list_fx(e0), S.Lxf, o0.x);
+    const float dy = S.Yf - fmaf(list_fy(e0), S.Lyf, o0.y), dz = S.Zf - o0.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (base + lane < count && r2 < cut2 && r2 > 0.f) {
+      float phi, md2, rinv;
+      pair_ie_f(r2, S.af, S.etaf, phi, md2, rinv);
+      acc.add(-o0.w * phi);
+    }
+    e0 = e1;
+    e1 = e2;
+    o0 = o1;
+  }
+}
+
 // Verlet-list view handed to the gathers
 struct ListsDev {
   const int32_t *ii, *ie, *ei, *ii_n, *ie_n, *ei_n, *cell_s, *ecell;
@@ -773,7 +797,8 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
     }
   };
   const int nei = nl.ei_n[j];
-  if (nei <= nl.cap) compacted_list(S, ions, nl.ei + j * nl.cap, nei, cut2, wq[warp], lane, near_pair);
+  if (F32 && nei <= nl.cap) ei_list_f32(S, ions, nl.ei + j * nl.cap, nei, cut2, lane, fn);
+  else if (nei <= nl.cap) compacted_list(S, ions, nl.ei + j * nl.cap, nei, cut2, wq[warp], lane, near_pair);
   else compacted_pairs(S, ions, nl.ecell[j], false, cut2, wq[warp], lane, near_pair);
   if (F32) {
     // FP32 to the end of the warp sum: on this GPU every FP64 warp instruction is costly
@@ -885,9 +910,13 @@ __global__ void __launch_bounds__(256) k_nbr_refresh(NbrKernelArgs a) {
     const int64_t gsize = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = gtid; p < a.n; p += gsize) {
       const int32_t i = a.order[p];
+      // displacement since the build position, back across the periodic wrap (it is far below
+      // L / 2 unless the ion was wrapped, then within a skin of +-L): no FP64 division
       double dx = a.x[i] - a.xb[p], dy = a.y[i] - a.yb[p];
-      dx -= a.Lx * floor(dx / a.Lx + 0.5);
-      dy -= a.Ly * floor(dy / a.Ly + 0.5);
+      if (dx > 0.5 * a.Lx) dx -= a.Lx;
+      else if (dx < -0.5 * a.Lx) dx += a.Lx;
+      if (dy > 0.5 * a.Ly) dy -= a.Ly;
+      else if (dy < -0.5 * a.Ly) dy += a.Ly;
       const double X = a.xb[p] + dx, Y = a.yb[p] + dy, Z = a.z[i];
       a.xs[p] = X;
       a.ys[p] = Y;
@@ -1100,7 +1129,7 @@ void neighbor_update(srbe_ctx *c) {
   }
   const int want = (int)std::max<int64_t>(1, std::min<int64_t>((std::max<int64_t>(n, c->ne) * 32 + 255) / 256,
                                                                  (int64_t)blocks_per_sm * nsm));
-  k_nbr_refresh<<<blocks_for(std::max<int64_t>(n, 1), 256), 256, 0, c->stream>>>(a);
+  k_nbr_refresh<<<blocks_for(std::max<int64_t>(n, 1), 64), 64, 0, c->stream>>>(a);
   SRBE_CUDA(cudaGetLastError());
   void *args[] = {&a};
   coop_before(c);
@@ -1144,6 +1173,22 @@ void electrode_rhs(srbe_ctx *c) {
 
 // coefF[k] = (c_k Im S(k), c_k Re S(k)) with S = S1 + S2;
 // F_i = - q_i sum_k c_k k Im(S exp(-i k . r_i)) = - q_i sum_k k (cIm cos - cRe sin)   (Eq. 25)
+// the FP32 copies of the scalar parameters the mixed form needs (converted once on the host)
+struct ForceF32 {
+  float Lx, Ly, alpha, eta, rc, slab, kb;
+};
+
+// exact FP32 -> FP64 widening with integer instructions (FP64-pipe conversions are scarce on this
+// GPU): normal numbers re-biased, zeros kept; subnormal, infinite and NaN inputs take the conversion
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+  if (e - 1u < 254u)
+    return __longlong_as_double((long long)(((uint64_t)(u >> 31) << 63) | ((uint64_t)(e + 896u) << 52) |
+                                            ((uint64_t)(u & 0x7fffffu) << 29)));
+  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((uint64_t)(u >> 31) << 63));
+  return (double)f;
+}
+
 template <bool F32, bool EN>
 __global__ void __launch_bounds__(kGatherThreads)
 k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double *__restrict__ Q,
@@ -1151,17 +1196,20 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
              int K, const int4 *__restrict__ modes, const double2 *__restrict__ coefF,
              const float2 *__restrict__ coefF32, const double2 *__restrict__ tab,
              double3 invL, float3 kvf, double Lx, double Ly, double alpha, double eta, double rc, double slab,
-             const double *__restrict__ scal, MdDev md, const double *__restrict__ x_orig,
+             ForceF32 pf, const double *__restrict__ scal, MdDev md, const double *__restrict__ x_orig,
              const double *__restrict__ y_orig, const double *__restrict__ z_orig, double *__restrict__ F,
              double *__restrict__ epart) {
   __shared__ double red[kWarpsPerBlock][4];
   __shared__ int2 wq[kWarpsPerBlock][64];
   __shared__ float2 ljs[kMaxLjTypes * kMaxLjTypes];
+  __shared__ float s_mz;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   double e_ii = 0, e_ie = 0, e_lj = 0, e_b = 0;
-  if (F32 && md.ntype) {
+  if (F32) {
     for (int t = threadIdx.x; t < md.ntype * md.ntype; t += blockDim.x) ljs[t] = md.lj32[t];
+    // M_z (an FP64 sum over all charges) in FP32, once per block
+    if (threadIdx.x == 0) s_mz = (float)(scal[kScalMion] + scal[kScalMele]);
   }
   __syncthreads();
   if (p < ni) {
@@ -1203,10 +1251,10 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     S.X = X; S.Y = Y; S.Z = Z; S.qi = qi; S.Lx = Lx; S.Ly = Ly; S.alpha = alpha; S.eta = eta; S.rc2 = rc * rc;
     const float4 self = ions.pf[p];
     S.Xf = self.x; S.Yf = self.y; S.Zf = self.z; S.qf = self.w;
-    S.Lxf = (float)Lx; S.Lyf = (float)Ly; S.af = (float)alpha; S.etaf = (float)eta;
+    S.Lxf = pf.Lx; S.Lyf = pf.Ly; S.af = pf.alpha; S.etaf = pf.eta;
     S.qke = (float)kKe * self.w;
     S.ti = ti; S.mi = mi; S.p = p;
-    const float rcf = (float)rc;
+    const float rcf = F32 ? pf.rc : (float)rc;
     const float cut2 = F32 ? rcf * rcf : (rcf + kPrecheckMargin) * (rcf + kPrecheckMargin);
     PairAcc A;
     int2 *q = wq[warp];
@@ -1246,11 +1294,10 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
         elj = warp_sum_f(elj);
       }
       if (lane == 0) {
-        const float Mz = (float)(scal[kScalMion] + scal[kScalMele]);
-        float Fx = -qf * kvf.x * v[0], Fy = -qf * kvf.y * v[1], Fz = -qf * kvf.z * v[2] - (float)slab * qf * Mz;
+        float Fx = -qf * kvf.x * v[0], Fy = -qf * kvf.y * v[1], Fz = -qf * kvf.z * v[2] - pf.slab * qf * s_mz;
         float bx = 0.f, by = 0.f, bz = 0.f, eb = 0.f;
         if (md.ntype && md.bond_start) {
-          const float Lxf = (float)Lx, Lyf = (float)Ly, kbf = (float)md.kb;
+          const float Lxf = pf.Lx, Lyf = pf.Ly, kbf = pf.kb;
           for (int b = md.bond_start[i]; b < md.bond_start[i + 1]; ++b) {
             const float4 o = ions.pf[ions.inv[md.bond_j[b]]];
             float dx = Xf - o.x, dy = Yf - o.y, dz = Zf - o.z;
@@ -1266,9 +1313,9 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
           }
         }
         const float ke = (float)kKe;
-        F[i] = (double)(ke * Fx + v[3] + bx);
-        F[ni + i] = (double)(ke * Fy + v[4] + by);
-        F[2 * ni + i] = (double)(ke * Fz + v[5] + bz);
+        F[i] = widen_f32(ke * Fx + v[3] + bx);
+        F[ni + i] = widen_f32(ke * Fy + v[4] + by);
+        F[2 * ni + i] = widen_f32(ke * Fz + v[5] + bz);
         e_ii = eii;
         e_ie = eie;
         e_lj = elj;
@@ -1394,9 +1441,11 @@ void ion_forces(srbe_ctx *c, bool energies) {
     const bool mixed = c->precision == SRBE_MIXED;
     auto kern = mixed ? (energies ? k_ion_forces<true, true> : k_ion_forces<true, false>)
                       : (energies ? k_ion_forces<false, true> : k_ion_forces<false, false>);
+    const ForceF32 pf{(float)c->L[0], (float)c->L[1], (float)c->alpha, (float)c->eta,
+                      (float)c->rc,   (float)slab,   (float)md.kb};
     kern<<<nblk, kGatherThreads, 0, c->stream>>>(c->ni, ions, eles, lists_dev(c), c->Q.p, c->Q32.p, K, c->dm.p, coef,
                                                  c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta,
-                                                 c->rc, slab, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep);
+                                                 c->rc, slab, pf, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep);
     c->launches++;
     c->mode_evals += c->ni * (int64_t)K;
   }
@@ -1431,10 +1480,26 @@ struct Thermo {
   const int4 *step = nullptr;
 };
 
+// X - L floor(X / L), then once more if rounding left X at L.  A step moves a particle by far less
+// than L, so the usual case is one addition or subtraction of L (the same result as the floor form,
+// which runs only for X beyond [-L, 2L): FP64 division is costly on this GPU)
+__device__ __forceinline__ double wrap_periodic(double X, double L) {
+  if (X >= 0.0 && X < L) return X;
+  if (X >= -L && X < 0.0) {
+    X += L;
+  } else if (X >= L && X < 2.0 * L) {
+    X -= L;
+  } else {
+    X -= L * floor(X / L);
+  }
+  if (X >= L) X -= L;
+  return X;
+}
+
 __global__ void k_kick_drift(int64_t n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                              double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                              const double *__restrict__ F, const double *__restrict__ minv, double fac, double dt,
-                             int drift, double Lx, double Ly, Thermo th) {
+                             int drift, double Lx, double Ly, Thermo th, double3 invL, uint64_t *__restrict__ iu) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double w = fac * minv[i];
@@ -1444,7 +1509,7 @@ __global__ void k_kick_drift(int64_t n, double *__restrict__ x, double *__restri
     const uint64_t step = (uint64_t)(uint32_t)st.x | ((uint64_t)(uint32_t)st.y << 32);
     uint64_t wd[4];
     philox4x64_dev(step, (uint64_t)i, 0, 0, th.seed, 0x4C414E47ull, wd);
-    double g0, g1, g2;
+    double g0, g1, g2;   // sigma_i times three standard normals
     if (th.f32) {
       // the same words, their top 24 bits as FP32 uniforms in (0, 1): every FP64 instruction is
       // costly on this GPU and the noise needs no more than FP32
@@ -1456,9 +1521,11 @@ __global__ void k_kick_drift(int64_t n, double *__restrict__ x, double *__restri
       sincospif(2.f * u[1], &s0, &c0);
       sincospif(2.f * u[3], &s1, &c1v);
       (void)s1;
-      g0 = r0 * c0;
-      g1 = r0 * s0;
-      g2 = r1 * c1v;
+      // sigma in FP32 too, and the three noise terms formed before the FP64 update
+      const float sg = sqrtf((float)th.s2 * (float)minv[i]);
+      g0 = (double)(sg * (r0 * c0));
+      g1 = (double)(sg * (r0 * s0));
+      g2 = (double)(sg * (r1 * c1v));
     } else {
       double u[4];
 #pragma unroll
@@ -1468,27 +1535,28 @@ __global__ void k_kick_drift(int64_t n, double *__restrict__ x, double *__restri
       sincospi(2.0 * u[1], &s0, &c0);
       sincospi(2.0 * u[3], &s1, &c1v);
       (void)s1;
-      g0 = r0 * c0;
-      g1 = r0 * s0;
-      g2 = r1 * c1v;
+      const double sig = sqrt(th.s2 * minv[i]);
+      g0 = sig * (r0 * c0);
+      g1 = sig * (r0 * s0);
+      g2 = sig * (r1 * c1v);
     }
-    const double sig = sqrt(th.s2 * minv[i]);
-    a = fma(th.c1, a, sig * g0);
-    b = fma(th.c1, b, sig * g1);
-    c = fma(th.c1, c, sig * g2);
+    a = fma(th.c1, a, g0);
+    b = fma(th.c1, b, g1);
+    c = fma(th.c1, c, g2);
   }
   vx[i] = a;
   vy[i] = b;
   vz[i] = c;
   if (drift) {
-    double X = fma(dt, a, x[i]), Y = fma(dt, b, y[i]);
-    X -= Lx * floor(X / Lx);
-    Y -= Ly * floor(Y / Ly);
-    if (X >= Lx) X -= Lx;
-    if (Y >= Ly) Y -= Ly;
+    const double X = wrap_periodic(fma(dt, a, x[i]), Lx), Y = wrap_periodic(fma(dt, b, y[i]), Ly);
+    const double Z = fma(dt, c, z[i]);
     x[i] = X;
     y[i] = Y;
-    z[i] = fma(dt, c, z[i]);
+    z[i] = Z;
+    // the new positions' fixed-point phase coordinates, once per step for the ion structure factor
+    iu[i] = to_turns64(X, invL.x);
+    iu[n + i] = to_turns64(Y, invL.y);
+    iu[2 * n + i] = to_turns64(Z, invL.z);
   }
 }
 
@@ -1540,9 +1608,12 @@ void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift) {
     th.seed = c->lang_seed;
     th.step = c->dm.p + c->K;
   }
-  k_kick_drift<<<blocks_for(c->ni, 256), 256, 0, c->stream>>>(c->ni, c->x.p, c->y.p, c->z.p, c->vx.p, c->vy.p,
-                                                             c->vz.p, c->F.p, c->minv.p, fac_kick, c->dt,
-                                                             drift ? 1 : 0, c->L[0], c->L[1], th);
+  uint64_t *iu = drift ? c->iu.ensure((size_t)3 * c->ni) : nullptr;
+  const double3 invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
+  // 64-thread blocks: the FP64 arithmetic spreads over every SM even for a few thousand ions
+  k_kick_drift<<<blocks_for(c->ni, 64), 64, 0, c->stream>>>(c->ni, c->x.p, c->y.p, c->z.p, c->vx.p, c->vy.p,
+                                                           c->vz.p, c->F.p, c->minv.p, fac_kick, c->dt,
+                                                           drift ? 1 : 0, c->L[0], c->L[1], th, invL, iu);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }

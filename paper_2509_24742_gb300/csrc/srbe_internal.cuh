@@ -196,6 +196,7 @@ struct srbe_ctx {
   int64_t ne = 0;
   srbe::DevBuf<double> ex, ey, ez, ed;         // positions and d (-1/2 | +1/2)
   srbe::DevBuf<uint64_t> eu;                   // fixed-point phase coordinates [3][ne], site order
+  srbe::DevBuf<uint64_t> iu;                   // ion phase coordinates [3][ni] written by the drift of a step
   srbe::DevBuf<double> Bmat;                   // projected inverse J A^-1, ne x ne row-major
   srbe::DevBuf<float2> Bsplit;                 // its (hi, lo) FP32 split (mixed form)
   srbe::DevBuf<double> Amat;                   // A itself (kept for the refinement residual)
@@ -381,9 +382,10 @@ void build_run_table(srbe_ctx *c);
 void neighbor_update(srbe_ctx *c);
 void neighbor_force_rebuild(srbe_ctx *c);
 // coef_mode: -1 none, 0 writes (c Re S, c Im S) for the electrode right-hand side, 1 writes
-// (c Im S, c Re S) for the ion forces, into ctx->coef / coef32
+// (c Im S, c Re S) for the ion forces, into ctx->coef / coef32.  u: the particles' fixed-point phase
+// coordinates [3][n] if already known (else they come from x, y, z); z is read for M_z either way
 void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *w,
-                      double2 *S, const double2 *S_add, int mslot, int coef_mode);
+                      double2 *S, const double2 *S_add, int mslot, int coef_mode, const uint64_t *u = nullptr);
 void electrode_rhs(srbe_ctx *c);
 void charge_update(srbe_ctx *c);
 void pcg_prepare(srbe_ctx *c);
