@@ -179,8 +179,19 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
   // partials), then the four warp sums are added in warp order
   double2 acc = make_double2(0.0, 0.0);
   if (kidx < K) {
-#pragma unroll 4
-    for (int c = warp; c < fin.nchunk; c += 4) {
+    // eight loads in flight per thread before the adds (same order of additions)
+    int c = warp;
+    for (; c + 28 < fin.nchunk; c += 32) {
+      double2 p[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) p[u] = __ldcg(partial + (int64_t)(c + 4 * u) * K + kidx);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        acc.x += p[u].x;
+        acc.y += p[u].y;
+      }
+    }
+    for (; c < fin.nchunk; c += 4) {
       const double2 p = __ldcg(partial + (int64_t)c * K + kidx);
       acc.x += p.x;
       acc.y += p.y;

@@ -77,7 +77,8 @@ void build_run_table(srbe_ctx *c) {
             while (ox <= g.span[0]) {
               const int xx = cx + ox, ix = host_floor_div(xx, g.nc[0]), ccx = xx - ix * g.nc[0];
               const int run = std::min(g.span[0] - ox + 1, g.nc[0] - ccx);
-              runs.push_back(make_int4(rowbase + ccx, run, (ix + 512) | ((iy + 512) << 10), 0));
+              runs.push_back(make_int4(rowbase + ccx, run, (ix + 512) | ((iy + 512) << 10),
+                                       (yy - iy * g.nc[1]) | (zc << 16)));
               ox += run;
             }
           }
@@ -860,6 +861,7 @@ struct NbrKernelArgs {
   double Lx, Ly;
   double3 invL;
   float cut2, half_skin2;
+  float csf[3], z0f;     // cell edges and the grid's lower z in FP32 (stencil pruning)
   int *flag;
 };
 
@@ -870,28 +872,60 @@ __device__ __forceinline__ void warp_append(int32_t *list, int cap, int &count, 
   count += __popc(m);
 }
 
-// appends every particle of the runs of `cell` within sqrt(cut2) of (X, Y, Z) to list
+// appends every particle of the runs of `cell` within sqrt(cut2) of (X, Y, Z) to list.  The runs
+// and their particle ranges are fetched 32 at a time (lane = run) and broadcast, so that a list
+// costs one round of dependent loads for the whole stencil instead of one per run.
 __device__ __forceinline__ int build_list(const NbrKernelArgs &a, const int4 *runs, const int32_t *run_first, int cell,
                                           const int32_t *start, const float4 *pf, float X, float Y, float Z,
                                           int64_t self, int32_t *list, int lane) {
   int count = 0;
   const float Lxf = (float)a.Lx, Lyf = (float)a.Ly;
-  for (int r = run_first[cell]; r < run_first[cell + 1]; ++r) {
-    const int4 R = runs[r];
-    const int b0 = start[R.x], b1 = start[R.x + R.y];
-    if (b0 == b1) continue;
-    const int ix = image_x(R.z), iy = image_y(R.z);
-    const float sx = (float)ix * Lxf, sy = (float)iy * Lyf;
-    const bool zero_image = ix == 0 && iy == 0;
-    for (int base = b0; base < b1; base += 32) {
-      const int pp = base + lane;
-      bool in = false;
-      if (pp < b1 && !(zero_image && pp == self)) {
-        const float4 o = pf[pp];
-        const float dx = X - (o.x + sx), dy = Y - (o.y + sy), dz = Z - o.z;
-        in = dx * dx + dy * dy + dz * dz < a.cut2;
+  // stencil pruning: a run (one row of cells) whose box lies farther than the reach (plus a margin
+  // for FP32 rounding of the cell edges) in y and z is skipped, and its cells beyond the reach in x
+  // are trimmed; the end cells in z hold any particle beyond them, so they are open-ended
+  const float reach = sqrtf(a.cut2) + 1e-3f, reach2 = reach * reach;
+  const int rfirst = run_first[cell], nrun = run_first[cell + 1] - rfirst;
+  for (int rb = 0; rb < nrun; rb += 32) {
+    int mb0 = 0, mb1 = 0, mz = 0;
+    if (rb + lane < nrun) {
+      const int4 R = runs[rfirst + rb + lane];
+      const int ccy = R.w & 0xffff, zc = R.w >> 16;
+      const int ix = image_x(R.z), iy = image_y(R.z);
+      const float ylo = (float)ccy * a.csf[1] + (float)iy * Lyf, yhi = ylo + a.csf[1];
+      const float zlo = a.z0f + (float)zc * a.csf[2], zhi = zlo + a.csf[2];
+      const float dy = fmaxf(fmaxf(ylo - Y, Y - yhi), 0.f);
+      const float dz = fmaxf(fmaxf(zc > 0 ? zlo - Z : 0.f, zc < a.g.nc[2] - 1 ? Z - zhi : 0.f), 0.f);
+      const float d2 = dy * dy + dz * dz;
+      if (d2 < reach2) {
+        const float xr = sqrtf(reach2 - d2), xs = X - (float)ix * Lxf;
+        const int ccx0 = R.x - (zc * a.g.nc[1] + ccy) * a.g.nc[0];
+        const int klo = max(0, (int)floorf((xs - xr) / a.csf[0]) - ccx0);
+        const int khi = min(R.y - 1, (int)floorf((xs + xr) / a.csf[0]) - ccx0);
+        if (klo <= khi) {
+          mb0 = start[R.x + klo];
+          mb1 = start[R.x + khi + 1];
+          mz = R.z;
+        }
       }
-      warp_append(list, a.cap, count, in, list_entry(pp, ix, iy), lane);
+    }
+    const int nq = min(32, nrun - rb);
+    for (int q = 0; q < nq; ++q) {
+      const int b0 = __shfl_sync(0xffffffffu, mb0, q), b1 = __shfl_sync(0xffffffffu, mb1, q);
+      if (b0 == b1) continue;
+      const int code = __shfl_sync(0xffffffffu, mz, q);
+      const int ix = image_x(code), iy = image_y(code);
+      const float sx = (float)ix * Lxf, sy = (float)iy * Lyf;
+      const bool zero_image = ix == 0 && iy == 0;
+      for (int base = b0; base < b1; base += 32) {
+        const int pp = base + lane;
+        bool in = false;
+        if (pp < b1 && !(zero_image && pp == self)) {
+          const float4 o = pf[pp];
+          const float dx = X - (o.x + sx), dy = Y - (o.y + sy), dz = Z - o.z;
+          in = dx * dx + dy * dy + dz * dz < a.cut2;
+        }
+        warp_append(list, a.cap, count, in, list_entry(pp, ix, iy), lane);
+      }
     }
   }
   return count;
@@ -1030,24 +1064,27 @@ __global__ void __launch_bounds__(256) k_neighbor_update(NbrKernelArgs a) {
     a.cell_s[p] = a.cell[i];
   }
   grid.sync();
-  // ---- phase 7: ion lists (warp per ion)
-  for (int64_t p = gwarp; p < a.n; p += nwarps) {
-    const float4 me = a.pf[p];
-    const int cell = a.cell_s[p];
-    const int nii = build_list(a, a.runs, a.run_first, cell, a.start, a.pf, me.x, me.y, me.z, p,
-                               a.ii + p * a.cap, lane);
-    const int nie = build_list(a, a.runs, a.run_first, cell, a.eles.start, a.eles.pf, me.x, me.y, me.z, -1,
-                               a.ie + p * a.cap, lane);
-    if (lane == 0) {
-      a.ii_n[p] = nii;
-      a.ie_n[p] = nie;
+  // ---- phase 7: the ion lists (ion-ion and ion-electrode) and the electrode-ion lists as one pool
+  // of tasks, warp per task, so that no warp takes more than ceil(tasks / warps) of them
+  for (int64_t t = gwarp; t < a.n + a.ne; t += nwarps) {
+    if (t < a.n) {
+      const int64_t p = t;
+      const float4 me = a.pf[p];
+      const int cell = a.cell_s[p];
+      const int nii = build_list(a, a.runs, a.run_first, cell, a.start, a.pf, me.x, me.y, me.z, p,
+                                 a.ii + p * a.cap, lane);
+      const int nie = build_list(a, a.runs, a.run_first, cell, a.eles.start, a.eles.pf, me.x, me.y, me.z, -1,
+                                 a.ie + p * a.cap, lane);
+      if (lane == 0) {
+        a.ii_n[p] = nii;
+        a.ie_n[p] = nie;
+      }
+    } else {
+      const int64_t j = t - a.n;
+      const int nei = build_list(a, a.runs, a.run_first, a.ecell[j], a.start, a.pf, (float)a.ex[j], (float)a.ey[j],
+                                 (float)a.ez[j], -1, a.ei + j * a.cap, lane);
+      if (lane == 0) a.ei_n[j] = nei;
     }
-  }
-  // ---- phase 8: electrode-ion lists (warp per electrode site)
-  for (int64_t j = gwarp; j < a.ne; j += nwarps) {
-    const int nei = build_list(a, a.runs, a.run_first, a.ecell[j], a.start, a.pf, (float)a.ex[j], (float)a.ey[j],
-                               (float)a.ez[j], -1, a.ei + j * a.cap, lane);
-    if (lane == 0) a.ei_n[j] = nei;
   }
   grid.sync();
   if (gtid == 0) {
@@ -1115,6 +1152,8 @@ void neighbor_update(srbe_ctx *c) {
   a.Lx = c->L[0];
   a.Ly = c->L[1];
   a.invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
+  for (int d = 0; d < 3; ++d) a.csf[d] = (float)cl.g.cs[d];
+  a.z0f = (float)cl.g.z0;
   const float reach = (float)(c->rc + nb.skin) + (c->precision == SRBE_MIXED ? 0.f : kPrecheckMargin);
   a.cut2 = reach * reach;
   a.half_skin2 = (float)(0.25 * nb.skin * nb.skin);
