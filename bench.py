@@ -176,9 +176,17 @@ def roofline(phase, ms_per_launch, slab, K, n_ii, n_ie, precision, pk):
         return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
                 "peak_source": pk["hbm_source"], "algorithmic_bytes": byts,
                 "kernel": "k_charges_split" if precision == "mixed" else "k_charges_fp64"}
-    if phase == "forces":
+    if phase == "forces" and precision == "mixed":
+        # the mixed form splits the force pass: this phase is the k-space gather and the
+        # ion-electrode pairs; the ion-ion pairs are the "forces_ii" pass on the side stream
+        flops = slab.n_ion * K * FLOP_MODE + n_ie * FLOP_PAIR
+        kern = "k_ion_forces<1,0,2>"
+    elif phase == "forces_ii":
+        flops = 2 * n_ii * FLOP_PAIR
+        kern = "k_ion_forces<1,0,1>"
+    elif phase == "forces":
         flops = slab.n_ion * K * FLOP_MODE + (2 * n_ii + n_ie) * FLOP_PAIR
-        kern = "k_ion_forces"
+        kern = "k_ion_forces<0,0,0>"
     elif phase in ("S1", "S2"):
         n = slab.n_ion if phase == "S1" else slab.n_ele
         flops = n * K * FLOP_MODE

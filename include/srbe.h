@@ -166,18 +166,21 @@ int srbe_forces_dev(srbe_ctx *ctx, double *F_dev, double *Q_dev);
 int srbe_get_counters(const srbe_ctx *ctx, int64_t *kernel_launches, int64_t *mode_evals);
 
 /* Phase tracing (no counterpart in the paper; a measurement aid).  When on, every pass records a
- * CUDA event pair on the context's stream around each phase of Algorithm 1:
+ * CUDA event pair around each phase of Algorithm 1:
  *   0 mode-list upload, 1 cell lists, 2 S1 (ions), 3 b (electrode right-hand side),
- *   4 charge solve, 5 S2 (electrode), 6 ion forces, 7 integration, 8 energies.
- * srbe_get_phase_times synchronises the stream and returns, per phase, the summed device time
- * (ms) and the number of timed intervals since tracing was switched on (arrays of 9; either
- * may be NULL).  Switching tracing on resets the sums. */
+ *   4 charge solve, 5 S2 (electrode), 6 ion forces, 7 integration, 8 energies,
+ *   9 ion-ion forces (mixed form without energies: the ion-ion pairs and bonds run as their own
+ *     pass on the context's side stream, beside phases 3-5; phase 6 is then the rest).
+ * Phases 1 and 9 are timed on the side stream, the others on the context's stream.
+ * srbe_get_phase_times synchronises and returns, per phase, the summed device time (ms) and the
+ * number of timed intervals since tracing was switched on (arrays of 10; either may be NULL).
+ * Switching tracing on resets the sums. */
 int srbe_set_profiling(srbe_ctx *ctx, int on);
 
 /* CUDA graphs for srbe_step (no counterpart in the paper; launch-overhead removal).  With graphs on
  * (the default) and tracing off, srbe_step runs its first step after any state change the ordinary
- * way, then captures the device half of a step (mode-list copy from one of two pinned host slots,
- * kick/drift, the full force pass, kick) into one graph per slot and replays it; the host samples
+ * way, then captures the device half of a step (mode list read from one of two mapped pinned host
+ * slots, kick/drift, the full force pass, kick) into one graph per slot and replays it; the host samples
  * the next step's modes into the other slot while the GPU runs.  Results are bitwise those of the
  * ordinary path.  Every call other than srbe_step and the get/stat queries drops the graphs (they
  * are captured again on the next srbe_step).  If capture fails the context keeps stepping the

@@ -764,6 +764,20 @@ void charges_pass(srbe_ctx *c, bool after_drift) {
 
 void forces_pass(srbe_ctx *c, bool energies, bool after_drift) {
   charges_pass(c, after_drift);
+  if (ion_forces_split(c, energies)) {
+    // the ion-ion pairs on the side stream, behind the neighbour update, beside b / solve / S2
+    const cudaStream_t main = c->stream;
+    c->stream = c->side;
+    try {
+      phase_begin(c, kPhForcesII);
+      ion_forces_ii(c);
+      phase_end(c, kPhForcesII);
+    } catch (...) {
+      c->stream = main;
+      throw;
+    }
+    c->stream = main;
+  }
   phase_begin(c, kPhS2);
   if (c->lat.active(c->ne, c->K)) lattice_s2(c, c->S2.p, c->S1.p, kScalMele);
   else structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele, 1, c->eu.p);
@@ -889,6 +903,7 @@ int srbe_create(const double box[3], double alpha, double eta, double rc, int P,
     SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_modes, cudaEventDisableTiming));
+    SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_ii, cudaEventDisableTiming));
     upload_table(c);
     c->scal.ensure(kScalCount);
     SRBE_CUDA(cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScalCount, c->stream));
@@ -913,6 +928,7 @@ int srbe_destroy(srbe_ctx *c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_modes) cudaEventDestroy(c->ev_modes);
+  if (c->ev_ii) cudaEventDestroy(c->ev_ii);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   c->stream = nullptr;

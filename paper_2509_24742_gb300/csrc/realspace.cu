@@ -1228,7 +1228,10 @@ __device__ __forceinline__ double widen_f32(float f) {
   return (double)f;
 }
 
-template <bool F32, bool EN>
+// PART (mixed form without energies only): 0 the whole force; 1 the ion-ion pairs and bonds alone
+// into Fii (sorted order; they need neither Q nor S, so they run beside b, the solve and S2);
+// 2 everything else, plus Fii
+template <bool F32, bool EN, int PART>
 __global__ void __launch_bounds__(kGatherThreads)
 k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double *__restrict__ Q,
              const float *__restrict__ Q32,
@@ -1237,7 +1240,8 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
              double3 invL, float3 kvf, double Lx, double Ly, double alpha, double eta, double rc, double slab,
              ForceF32 pf, const double *__restrict__ scal, MdDev md, const double *__restrict__ x_orig,
              const double *__restrict__ y_orig, const double *__restrict__ z_orig, double *__restrict__ F,
-             double *__restrict__ epart) {
+             double *__restrict__ epart, float4 *__restrict__ Fii) {
+  static_assert(PART == 0 || (F32 && !EN), "the split force passes are the mixed form's, without energies");
   __shared__ double red[kWarpsPerBlock][4];
   __shared__ int2 wq[kWarpsPerBlock][64];
   __shared__ float2 ljs[kMaxLjTypes * kMaxLjTypes];
@@ -1248,7 +1252,7 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
   if (F32) {
     for (int t = threadIdx.x; t < md.ntype * md.ntype; t += blockDim.x) ljs[t] = md.lj32[t];
     // M_z (an FP64 sum over all charges) in FP32, once per block
-    if (threadIdx.x == 0) s_mz = (float)(scal[kScalMion] + scal[kScalMele]);
+    if (PART != 1 && threadIdx.x == 0) s_mz = (float)(scal[kScalMion] + scal[kScalMele]);
   }
   __syncthreads();
   if (p < ni) {
@@ -1261,7 +1265,9 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     // ---- k-space gather
     double fk[3] = {0, 0, 0};
     float ak0 = 0.f, ak1 = 0.f, ak2 = 0.f;
-    if (!F32) {
+    if (PART == 1) {
+      // no k-space part in the ion-ion pass
+    } else if (!F32) {
       for (int k = lane; k < K; k += 32) {
         const int4 m = __ldg(&modes[k]);
         double cs, sn;
@@ -1299,7 +1305,9 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     int2 *q = wq[warp];
     // Verlet lists; a particle whose list overflowed walks the stencil of its build cell instead
     const int nii = nl.ii_n[p], nie = nl.ie_n[p];
-    if (F32 && nii <= nl.cap)
+    if (PART == 2) {
+      // the ion-ion pairs came from the PART 1 pass
+    } else if (F32 && nii <= nl.cap)
       ii_list_f32<EN>(S, ions, md, ljs, nl.ii + p * nl.cap, nii, cut2, lane, A);
     else if (nii <= nl.cap)
       compacted_list(S, ions, nl.ii + p * nl.cap, nii, cut2, q, lane,
@@ -1307,7 +1315,9 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     else
       compacted_pairs(S, ions, nl.cell_s[p], true, cut2, q, lane,
                       [&](int2 e) { pair_ion_ion<F32, EN>(S, ions, md, e, A); });
-    if (F32 && nie <= nl.cap)
+    if (PART == 1) {
+      // the ion-electrode pairs wait for Q
+    } else if (F32 && nie <= nl.cap)
       ie_list_f32<EN>(S, eles, md, ljs, Q32, nl.ie + p * nl.cap, nie, cut2, lane, A);
     else if (nie <= nl.cap)
       compacted_list(S, eles, nl.ie + p * nl.cap, nie, cut2, q, lane,
@@ -1326,16 +1336,21 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
       // reduction over all charges) enters from FP64
       float v[6] = {ak0, ak1, ak2, A.f0, A.f1, A.f2};
 #pragma unroll
-      for (int d = 0; d < 6; ++d) v[d] = warp_sum_f(v[d]);
+      for (int d = (PART == 1 ? 3 : 0); d < 6; ++d) v[d] = warp_sum_f(v[d]);
       if (EN) {
         eii = warp_sum_f(eii);
         eie = warp_sum_f(eie);
         elj = warp_sum_f(elj);
       }
       if (lane == 0) {
-        float Fx = -qf * kvf.x * v[0], Fy = -qf * kvf.y * v[1], Fz = -qf * kvf.z * v[2] - pf.slab * qf * s_mz;
+        float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+        if (PART != 1) {
+          Fx = -qf * kvf.x * v[0];
+          Fy = -qf * kvf.y * v[1];
+          Fz = -qf * kvf.z * v[2] - pf.slab * qf * s_mz;
+        }
         float bx = 0.f, by = 0.f, bz = 0.f, eb = 0.f;
-        if (md.ntype && md.bond_start) {
+        if (PART != 2 && md.ntype && md.bond_start) {
           const float Lxf = pf.Lx, Lyf = pf.Ly, kbf = pf.kb;
           for (int b = md.bond_start[i]; b < md.bond_start[i + 1]; ++b) {
             const float4 o = ions.pf[ions.inv[md.bond_j[b]]];
@@ -1352,9 +1367,19 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
           }
         }
         const float ke = (float)kKe;
-        F[i] = widen_f32(ke * Fx + v[3] + bx);
-        F[ni + i] = widen_f32(ke * Fy + v[4] + by);
-        F[2 * ni + i] = widen_f32(ke * Fz + v[5] + bz);
+        if (PART == 1) {
+          Fii[p] = make_float4(v[3] + bx, v[4] + by, v[5] + bz, 0.f);
+        } else {
+          if (PART == 2) {
+            const float4 f = Fii[p];
+            bx = f.x;
+            by = f.y;
+            bz = f.z;
+          }
+          F[i] = widen_f32(ke * Fx + v[3] + bx);
+          F[ni + i] = widen_f32(ke * Fy + v[4] + by);
+          F[2 * ni + i] = widen_f32(ke * Fz + v[5] + bz);
+        }
         e_ii = eii;
         e_ie = eie;
         e_lj = elj;
@@ -1452,6 +1477,62 @@ __global__ void k_sum_partials(int nblk, int width, const double *__restrict__ p
   out[e] = s;
 }
 
+namespace {
+struct ForceLaunch {
+  MdDev md{};
+  double3 invL;
+  float3 kvf;
+  double slab;
+  unsigned nblk;
+  CellsDev ions, eles;
+  ForceF32 pf;
+};
+ForceLaunch force_launch(srbe_ctx *c) {
+  ForceLaunch f;
+  if (c->have_md) {
+    f.md.ntype = c->ntype;
+    f.md.lj = (const double2 *)c->lj.p;
+    f.md.lj32 = c->lj32.p;
+    f.md.bond_start = c->bond_start.p;
+    f.md.bond_j = c->bond_j.p;
+    f.md.bond_r0 = c->bond_r0.p;
+    f.md.kb = c->kb;
+  }
+  f.invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
+  f.kvf = make_float3((float)(2.0 * kPi / c->L[0]), (float)(2.0 * kPi / c->L[1]), (float)(2.0 * kPi / c->L[2]));
+  f.slab = 4.0 * kPi / c->V;
+  f.nblk = blocks_for(std::max<int64_t>(c->ni, 1), kWarpsPerBlock);
+  f.ions = cells_dev(c->icells, c->runtab);
+  f.eles = cells_dev(c->ecells, c->runtab);
+  if (!c->have_md) {
+    f.ions.ts = nullptr;
+    f.ions.ms = nullptr;
+  }
+  f.pf = ForceF32{(float)c->L[0], (float)c->L[1], (float)c->alpha, (float)c->eta,
+                  (float)c->rc,   (float)f.slab, (float)f.md.kb};
+  return f;
+}
+}  // namespace
+
+bool ion_forces_split(const srbe_ctx *c, bool energies) {
+  return c->precision == SRBE_MIXED && !energies && c->ni > 0;
+}
+
+// the mixed form's ion-ion pass (pairs and bonds: no Q, no S) on the side stream, right behind the
+// neighbour update there, so that it runs beside b, the charge solve and S2 on the main stream
+void ion_forces_ii(srbe_ctx *c) {
+  const ForceLaunch f = force_launch(c);
+  float4 *fii = c->fii.ensure((size_t)c->ni);
+  k_ion_forces<true, false, 1><<<f.nblk, kGatherThreads, 0, c->side>>>(
+      c->ni, f.ions, f.eles, lists_dev(c), c->Q.p, c->Q32.p, c->K, c->dm.p, c->coef.p, c->coef32.p, c->tab.p, f.invL,
+      f.kvf, c->L[0], c->L[1], c->alpha, c->eta, c->rc, f.slab, f.pf, c->scal.p, f.md, c->x.p, c->y.p, c->z.p,
+      c->F.p, nullptr, fii);
+  c->launches++;
+  SRBE_CUDA(cudaGetLastError());
+  SRBE_CUDA(cudaEventRecord(c->ev_ii, c->side));
+  c->fii_pending = true;
+}
+
 void ion_forces(srbe_ctx *c, bool energies) {
   const int K = c->K;
   double2 *coef = c->coef.p;   // written by the S2 reduction (S = S1 + S2)
@@ -1478,16 +1559,21 @@ void ion_forces(srbe_ctx *c, bool energies) {
   }
   if (c->ni > 0) {
     const bool mixed = c->precision == SRBE_MIXED;
-    auto kern = mixed ? (energies ? k_ion_forces<true, true> : k_ion_forces<true, false>)
-                      : (energies ? k_ion_forces<false, true> : k_ion_forces<false, false>);
+    const bool part2 = c->fii_pending && ion_forces_split(c, energies);
+    auto kern = part2 ? k_ion_forces<true, false, 2>
+                : mixed ? (energies ? k_ion_forces<true, true, 0> : k_ion_forces<true, false, 0>)
+                        : (energies ? k_ion_forces<false, true, 0> : k_ion_forces<false, false, 0>);
+    if (part2) SRBE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_ii, 0));
     const ForceF32 pf{(float)c->L[0], (float)c->L[1], (float)c->alpha, (float)c->eta,
                       (float)c->rc,   (float)slab,   (float)md.kb};
     kern<<<nblk, kGatherThreads, 0, c->stream>>>(c->ni, ions, eles, lists_dev(c), c->Q.p, c->Q32.p, K, c->dm.p, coef,
                                                  c->coef32.p, c->tab.p, invL, kvf, c->L[0], c->L[1], c->alpha, c->eta,
-                                                 c->rc, slab, pf, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep);
+                                                 c->rc, slab, pf, c->scal.p, md, c->x.p, c->y.p, c->z.p, c->F.p, ep,
+                                                 part2 ? c->fii.p : nullptr);
     c->launches++;
     c->mode_evals += c->ni * (int64_t)K;
   }
+  c->fii_pending = false;
   if (energies) {
     if (c->ni > 0) {
       k_sum_partials<<<1, 32, 0, c->stream>>>((int)nblk, 4, ep, c->scal.p + kScalEnergy);

@@ -188,6 +188,9 @@ struct srbe_ctx {
   cudaStream_t side = nullptr;                 // neighbour-list work beside S1 (joined before b)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_modes = nullptr;              // a captured step's mode list staged (side stream)
+  cudaEvent_t ev_ii = nullptr;                 // the mixed form's ion-ion force pass done (side stream)
+  bool fii_pending = false;                    // that pass was launched for the coming force pass
+  srbe::DevBuf<float4> fii;                    // its per-ion forces, sorted order
   std::string err;
 
   bool have_ele = false, have_pos = false, have_modes = false, have_md = false;
@@ -396,11 +399,15 @@ void mlp_forward(srbe_ctx *c, const float *D_dev, int64_t n, float *out_dev, dou
 double mlp_grad_step(srbe_ctx *c, const float *D_dev, const float *T_dev, const int32_t *rows_dev, int64_t n,
                      float *grad_dev, bool apply, float lr, float wd);
 void ion_forces(srbe_ctx *c, bool energies);
+bool ion_forces_split(const srbe_ctx *c, bool energies);
+void ion_forces_ii(srbe_ctx *c);
 void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift);
 void steepest_descent_move(srbe_ctx *c, double a, double dmax);
 void build_A_and_inverse(srbe_ctx *c);
 void energy_scalars(srbe_ctx *c);
-enum Phase { kPhUpload = 0, kPhCells, kPhS1, kPhRhs, kPhSolve, kPhS2, kPhForces, kPhIntegrate, kPhEnergy, kPhCount };
+enum Phase {
+  kPhUpload = 0, kPhCells, kPhS1, kPhRhs, kPhSolve, kPhS2, kPhForces, kPhIntegrate, kPhEnergy, kPhForcesII, kPhCount
+};
 void lattice_setup(srbe_ctx *c, const std::vector<double> &x, const std::vector<double> &y,
                    const std::vector<double> &z);
 void lattice_bfar(srbe_ctx *c);

@@ -96,7 +96,7 @@ EXPORTS = {
     "srbe_batch_step": ([_vp, _int, ctypes.POINTER(_u64), _dp], _int),
     "srbe_batch_autotune": ([_vp, _int, ctypes.POINTER(_u64), ctypes.POINTER(_int), _int, _dp], _int),
 }
-PHASES = ("upload", "cells", "S1", "rhs", "solve", "S2", "forces", "integrate", "energy")
+PHASES = ("upload", "cells", "S1", "rhs", "solve", "S2", "forces", "integrate", "energy", "forces_ii")
 
 
 def library_path():
