@@ -189,6 +189,17 @@ using namespace srbe;
 
 namespace {
 
+// Streams of the critical path (a context's own stream, the capture stream, batch forks) get the
+// highest priority, the side stream (lists, ion-ion forces) the lowest, so that where both have
+// blocks waiting the block scheduler serves b, the solve and S2 first.
+cudaStream_t make_stream(bool critical) {
+  int least = 0, greatest = 0;
+  SRBE_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  cudaStream_t s = nullptr;
+  SRBE_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, critical ? greatest : least));
+  return s;
+}
+
 int fail(srbe_ctx *c, const Error &e) {
   if (c) c->err = e.msg;
   return e.code;
@@ -895,11 +906,11 @@ int srbe_create(const double box[3], double alpha, double eta, double rc, int P,
   c->psi_right = psi_right;
   c->dpsi = (psi_right - psi_left) * kVolt;
   int rcode = guarded(c, [&] {
-    SRBE_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->stream = make_stream(true);
     c->own_stream = true;
     SRBE_CUDA(cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming));
     SRBE_CUDA(cudaEventRecord(c->stage_done, c->stream));
-    SRBE_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    c->side = make_stream(false);
     SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_modes, cudaEventDisableTiming));
@@ -948,7 +959,7 @@ int srbe_set_stream(srbe_ctx *c, void *stream) {
       c->stream = (cudaStream_t)stream;
       c->own_stream = false;
     } else if (!c->own_stream) {
-      SRBE_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->stream = make_stream(true);
       c->own_stream = true;
     }
     SRBE_CUDA(cudaEventRecord(c->stage_done, c->stream));
@@ -1287,7 +1298,7 @@ int srbe_step(srbe_ctx *c, int nsteps, uint64_t seed0) {
       ensure_slot_buffers(c);
       cudaGraphExec_t ex[2] = {nullptr, nullptr};
       srbe_ctx *one[1] = {c};
-      if (!e->cap) SRBE_CUDA(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
+      if (!e->cap) e->cap = make_stream(true);
       if (capture_graphs(one, 1, e->cap, 0, nullptr, ex, &e->graph_kernels, nullptr)) {
         e->slot[0].exec = ex[0];
         e->slot[1].exec = ex[1];
@@ -1828,7 +1839,7 @@ void batch_capture(srbe_batch *b, const uint64_t *seeds) {
   }
   while ((int)b->forks.size() < b->width) {
     cudaStream_t f = nullptr;
-    SRBE_CUDA(cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking));
+    f = make_stream(true);
     b->forks.push_back(f);
   }
   b->kernels.assign(n, 0);
@@ -1934,7 +1945,7 @@ int srbe_batch_create(int n, srbe_ctx *const *ctxs, srbe_batch **out) {
   b->ctx.assign(ctxs, ctxs + n);
   const int rc = batch_guarded(b, [&] {
     SRBE_CUDA(cudaGetDevice(&b->device));
-    SRBE_CUDA(cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking));
+    b->main = make_stream(true);
     for (auto &d : b->done) {
       SRBE_CUDA(cudaEventCreateWithFlags(&d, cudaEventDisableTiming));
       SRBE_CUDA(cudaEventRecord(d, b->main));

@@ -198,3 +198,15 @@ def test_graph_replay_is_bitwise_the_ordinary_path(precision, solver, thermo, la
     assert out[1][6][0] == 1 and out[1][6][1] > 5
     for a, b in zip(out[0][:6], out[1][:6]):
         assert np.array_equal(a, b)
+
+
+def test_split_force_pass_matches_single_pass():
+    """The mixed form without energies runs the ion-ion pairs and bonds as their own pass on the side
+    stream; with energies it runs one pass.  Same charges, same forces up to FP32 summation order."""
+    s = wl.md_11072()
+    with srbe.from_slab(s, precision=srbe.MIXED, md=True) as c:
+        c.sample_k(5, 1)
+        F_split, Q1, psi1 = c.forces()
+        F_one, Q2, psi2, _ = c.forces(energy=True)
+    assert np.array_equal(Q1, Q2) and psi1 == psi2
+    assert rel(F_split, F_one) < 1e-6, rel(F_split, F_one)
