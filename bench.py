@@ -349,10 +349,16 @@ def e2e_arm(ctx, slab, stream, flush, steps):
     q_h = torch.empty(n, dtype=torch.float64).pin_memory()
     F_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     Q_h = torch.empty(ne, dtype=torch.float64).pin_memory()
-    r_h.numpy()[:] = slab.r
     q_h.numpy()[:] = slab.q
     rn, qn, Fn, Qn = r_h.numpy(), q_h.numpy(), F_h.numpy(), Q_h.numpy()
+    # the positions an MD engine would hand in: the context's own trajectory, one frame per step
+    # (recorded untimed), so that the Verlet lists age and get rebuilt as they would in a run
+    traj = []
+    for i in range(steps + 3):
+        ctx.step(1, SEED)
+        traj.append(ctx.get_positions())
     for i in range(3):
+        rn[:] = traj[i]
         ctx.set_positions(rn, qn)
         ctx.sample_k(SEED, 10_000 + i)
         ctx.forces(out=(Fn, Qn))
@@ -360,6 +366,7 @@ def e2e_arm(ctx, slab, stream, flush, steps):
     for i in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        rn[:] = traj[3 + i]
         ctx.set_positions(rn, qn)
         ctx.sample_k(SEED, 20_000 + i)
         ctx.forces(out=(Fn, Qn))
@@ -368,7 +375,8 @@ def e2e_arm(ctx, slab, stream, flush, steps):
             flush.zero_()
     return {"value": steps / tot, "unit": UNIT, "h2d_bytes_per_step": int(rn.nbytes + qn.nbytes),
             "d2h_bytes_per_step": int(Fn.nbytes + Qn.nbytes),
-            "what": "host-pointer force provider: srbe_set_positions + srbe_sample_k + srbe_forces per step"}
+            "what": "host-pointer force provider: srbe_set_positions (next frame of an MD trajectory) + "
+                    "srbe_sample_k + srbe_forces per step"}
 
 
 # ---------------------------------------------------------------------------------------------- precision form

@@ -94,7 +94,10 @@ double srbe_get_alpha_A(const srbe_ctx *ctx);
 int srbe_set_electrode(srbe_ctx *ctx, int64_t n_ele, const double *R, const int8_t *side);
 
 /* Sets the n_ion electrolyte positions r [n_ion][3] (nm) and charges q (e).  n_ion may be 0.
- * Positions outside [0,L) in x or y are wrapped.  Errors: SRBE_EINVAL on non-finite input. */
+ * Positions outside [0,L) in x or y are wrapped.  With the same ion count and the same charges as
+ * the previous call (an MD engine handing in each step's positions) the Verlet lists are kept and
+ * rebuilt only once an ion has moved more than half the skin since their build; otherwise they are
+ * rebuilt at the next force evaluation.  Errors: SRBE_EINVAL on non-finite input. */
 int srbe_set_positions(srbe_ctx *ctx, int64_t n_ion, const double *r, const double *q);
 
 /* Copies the current ion positions and velocities out (either pointer may be NULL). */

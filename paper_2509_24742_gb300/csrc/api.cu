@@ -286,6 +286,7 @@ __global__ void k_interleave3(int64_t n, const double *__restrict__ x, const dou
 // per-context host state that the kernels never see
 struct srbe::HostExt {
   ModeSampler sampler;
+  std::vector<double> hq;  // the ion charges last handed to srbe_set_positions (host copy)
   DevBuf<double> aos;      // AoS staging for positions / forces
   bool forces_valid = false;
   // CUDA graphs of one MD step, one per pinned staging slot of the mode list (ping-pong)
@@ -1047,6 +1048,12 @@ int srbe_set_positions(srbe_ctx *c, int64_t n_ion, const double *r, const double
     SRBE_REQUIRE(finite_all(r, 3 * n_ion) && finite_all(q, n_ion), SRBE_EINVAL, "non-finite ion position or charge");
     if (c->have_md && n_ion != c->ni) c->have_md = false;
     if (n_ion != c->ni) c->nbr.cap = 0;
+    Extra *e = extra(c);
+    // the same ions with the same charges (an MD engine handing in each step's positions) keep their
+    // Verlet lists: the per-step refresh rebuilds them once some ion has moved more than half the
+    // skin since the last build.  Anything else (new count, new charges, first call) rebuilds.
+    const bool same_ions = c->have_pos && n_ion == c->ni && e->hq.size() == (size_t)n_ion &&
+                           std::equal(q, q + n_ion, e->hq.begin());
     c->ni = n_ion;
     const size_t n = (size_t)std::max<int64_t>(n_ion, 1);
     c->x.ensure(n);
@@ -1054,8 +1061,10 @@ int srbe_set_positions(srbe_ctx *c, int64_t n_ion, const double *r, const double
     c->z.ensure(n);
     c->q.ensure(n);
     c->F.ensure(3 * n);
-    neighbor_force_rebuild(c);
-    Extra *e = extra(c);
+    if (!same_ions) {
+      neighbor_force_rebuild(c);
+      e->hq.assign(q, q + n_ion);
+    }
     if (n_ion > 0) {
       double *aos = e->aos.ensure(3 * n);
       SRBE_CUDA(cudaMemcpyAsync(aos, r, sizeof(double) * 3 * n_ion, cudaMemcpyHostToDevice, c->stream));
@@ -1077,6 +1086,7 @@ int srbe_set_positions_dev(srbe_ctx *c, int64_t n_ion, const double *r_dev, cons
     if (n_ion != c->ni) c->nbr.cap = 0;
     c->ni = n_ion;
     neighbor_force_rebuild(c);
+    extra(c)->hq.clear();   // charges from device memory: the next host call rebuilds
     const size_t n = (size_t)std::max<int64_t>(n_ion, 1);
     c->x.ensure(n);
     c->y.ensure(n);
