@@ -1257,6 +1257,8 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
   __syncthreads();
   if (p < ni) {
     const int32_t i = ions.order[p];
+    // PART 2: the ion-ion pass's force for this ion, fetched now and used in the epilogue
+    const float4 fii_p = PART == 2 && lane == 0 ? Fii[p] : make_float4(0.f, 0.f, 0.f, 0.f);
     const double X = ions.xs[p], Y = ions.ys[p], Z = ions.zs[p], qi = ions.ws[p];
     const int ti = ions.ts ? ions.ts[p] : 0;
     const int mi = ions.ms ? ions.ms[p] : -1;
@@ -1371,10 +1373,9 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
           Fii[p] = make_float4(v[3] + bx, v[4] + by, v[5] + bz, 0.f);
         } else {
           if (PART == 2) {
-            const float4 f = Fii[p];
-            bx = f.x;
-            by = f.y;
-            bz = f.z;
+            bx = fii_p.x;
+            by = fii_p.y;
+            bz = fii_p.z;
           }
           F[i] = widen_f32(ke * Fx + v[3] + bx);
           F[ni + i] = widen_f32(ke * Fy + v[4] + by);

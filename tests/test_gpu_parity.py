@@ -210,3 +210,28 @@ def test_split_force_pass_matches_single_pass():
         F_one, Q2, psi2, _ = c.forces(energy=True)
     assert np.array_equal(Q1, Q2) and psi1 == psi2
     assert rel(F_split, F_one) < 1e-6, rel(F_split, F_one)
+
+
+@pytest.mark.parametrize("move", ["within_skin", "beyond_skin"])
+def test_set_positions_reuses_lists_only_while_valid(orc, slab784, move):
+    """srbe_set_positions with the same ions and charges keeps the Verlet lists; the per-step
+    half-skin test rebuilds them when needed.  Either way the forces equal a fresh context's."""
+    import copy
+    samples = orc.sample_metropolis(slab784.box, slab784.alpha, slab784.M, slab784.P, 3001, 2)
+    rng = np.random.default_rng(17)
+    r_new = slab784.r.copy()
+    if move == "within_skin":
+        r_new += rng.uniform(-0.004, 0.004, size=r_new.shape)
+    else:
+        r_new[:60, :2] += rng.uniform(-0.6, 0.6, size=(60, 2))
+    with gpu_ctx(slab784) as c:
+        c.set_k(samples)
+        c.forces()
+        c.set_positions(r_new, slab784.q)
+        F1, Q1, _ = c.forces()
+    s2 = copy.copy(slab784)
+    s2.r = r_new
+    with gpu_ctx(s2) as c2:
+        c2.set_k(samples)
+        F2, Q2, _ = c2.forces()
+    assert rel(F1, F2) < 1e-12 and rel(Q1, Q2) < 1e-12
