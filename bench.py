@@ -488,6 +488,44 @@ def solve_arm(args):
             "mixed": out["mixed"], "fp64": out["fp64"], "fp64_charge_residual": res}
 
 
+# ---------------------------------------------------------------------------------------------- charge noise
+def noise_arm(args):
+    """A synthetic analogue of the paper's Table 1 on the 11,072-site slab at its seeded packing:
+    over `steps` sampling seeds (the method's own Metropolis sampler), the standard deviation of the
+    left electrode's total charge and the per-site RMS deviation of the charges from their mean, for
+    M (deterministic low-|k_z| modes) in {0, 2, 4 = L_z / L_x, 8} and P in {50, 100, 200}; FP64."""
+    import copy
+    import torch
+    from paper_2509_24742_gb300 import srbe, workloads
+    torch.cuda.set_device(0)
+    base = workloads.md_11072()
+    left = base.side == 0
+    rows = []
+    t0 = time.perf_counter()
+    for M in (0, 2, 4, 8):
+        for P in (50, 100, 200):
+            s = copy.copy(base)
+            s.M, s.P = M, P
+            with srbe.from_slab(s) as ctx:
+                Qs = []
+                for i in range(args.steps):
+                    ctx.sample_k(SEED, i)
+                    Q, _, _ = ctx.solve_charges()
+                    Qs.append(Q)
+            Qs = np.array(Qs)
+            ql = Qs[:, left].sum(1)
+            dev = Qs - Qs.mean(0)
+            rows.append({"M": M, "P": P, "sd_left_total_e": float(ql.std(ddof=1)),
+                         "mean_left_total_e": float(ql.mean()),
+                         "rms_site_noise_rel": float(np.sqrt((dev ** 2).mean()) / np.sqrt((Qs.mean(0) ** 2).mean()))})
+    return {"metric": "SD of the electrode charge over sampling seeds vs M and P (synthetic Table 1 analogue)",
+            "value": None, "unit": "e", "n_gpus": 1, "steps": args.steps, "warmup": 0, "dtype": "f64",
+            "data": "synthetic", "higher_is_better": False,
+            "config": {"workload": "md11072_P200 slab (4x4x16 nm, 3072 electrode + 8000 ion sites), seeded packing, 1 V",
+                       "seeds": args.steps},
+            "table": rows, "wall_s": time.perf_counter() - t0}
+
+
 # ---------------------------------------------------------------------------------------------- batching form
 def batch_arm(args):
     """R uneven replicas: the mixed-precision batch (one graph launch per batch step, autotuned
@@ -645,7 +683,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="md11072",
-                    choices=["md11072", "batch64", "prec100k", "solve6144", "large1m"])
+                    choices=["md11072", "batch64", "prec100k", "solve6144", "large1m", "noise"])
     ap.add_argument("--replicas", type=int, default=64)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -665,6 +703,9 @@ def main():
         return
     if args.workload == "solve6144":
         print(json.dumps(solve_arm(args)))
+        return
+    if args.workload == "noise":
+        print(json.dumps(noise_arm(args)))
         return
     if world > 1:
         import torch
