@@ -277,8 +277,8 @@ int srbe_autotune_skin(srbe_ctx *ctx, int trial_steps, uint64_t seed, const doub
  * solver and mode count, each with its own seed and so its own k-sample lists) as one unit: each
  * batch step is ONE CUDA graph launch that runs Algorithm 1's step for every replica, the replicas
  * spread over `width` streams inside the graph so that small systems overlap on the GPU.  The host
- * samples every replica's next mode list (over a few host threads) into pinned slots while the GPU
- * runs the current step.  A replica's trajectory is bitwise the one srbe_step gives it with the same
+ * samples every replica's next mode list (over a few host threads) into mapped pinned slots while
+ * the GPU runs the current step; one kernel at the head of the graph reads them all.  A replica's trajectory is bitwise the one srbe_step gives it with the same
  * seed.  Cooperative kernels of different replicas are ordered one after another inside the graph
  * (two overlapping grid-wide barriers could starve each other of SMs).
  *   srbe_batch_create: ctxs are borrowed (the caller keeps and destroys them, after the batch);

@@ -538,9 +538,9 @@ void srbe_list_from_samples(srbe_ctx *c, const int32_t *samp, int P) {
 }
 
 // ---- CUDA graph of one MD step ------------------------------------------------------------------
-// The device half of a step (mode-list copy from a pinned slot, kick/drift, the force pass, kick) has
-// no host synchronisation and no allocation once the buffers are reserved, so it is captured once
-// per slot and replayed; the host fills the other slot while the GPU runs.
+// The device half of a step (mode list read from a mapped pinned slot, kick/drift, the force pass,
+// kick) has no host synchronisation and no allocation once the buffers are reserved, so it is
+// captured once per slot and replayed; the host fills the other slot while the GPU runs.
 void forces_pass(srbe_ctx *c, bool energies, bool after_drift = false);
 
 // the captured step's mode list (K int4 + the step word) and weights, read from a mapped pinned slot
