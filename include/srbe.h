@@ -121,6 +121,19 @@ int srbe_set_sampler(srbe_ctx *ctx, int kind, const int32_t *mmax);
  * (Eq. 27).  The same (seed, step) always gives the same list. */
 int srbe_sample_k(srbe_ctx *ctx, uint64_t seed, uint64_t step);
 
+/* The exact sampler (SRBE_SAMPLER_EXACT, inverse CDF per dimension of Eq. 26's P(k), rejection of
+ * I u {0}) on the device: one kernel draws the same Philox stream as the host sampler, takes the
+ * first P admissible tries in order and writes the modes and the Eq. 24-25 weights (G / P) 4 pi /
+ * (V k^2) with the host's operations in the host's order, so the list is bitwise the host's.  With
+ * it on, srbe_step's captured steps sample on the device (the host writes only the step and seed);
+ * the batch keeps host sampling.  srbe_set_device_sampler: on = 1 needs SRBE_SAMPLER_EXACT
+ * (SRBE_EINVAL otherwise); its tables follow srbe_set_sampler.  srbe_sample_k_device: like
+ * srbe_sample_k through the device kernel; copies the P sampled modes m [P][3] and their weights
+ * w [P] out (either may be NULL).  SRBE_ESTATE without the device sampler on; SRBE_ENOTCONV if fewer
+ * than P admissible modes came out of 2^20 tries. */
+int srbe_set_device_sampler(srbe_ctx *ctx, int on);
+int srbe_sample_k_device(srbe_ctx *ctx, uint64_t seed, uint64_t step, int32_t *m, double *w);
+
 /* Copies out the current sampled modes (m [P][3] integers, k = 2 pi m / L) and G. */
 int srbe_get_k(const srbe_ctx *ctx, int32_t *m, double *G);
 

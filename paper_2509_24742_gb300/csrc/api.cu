@@ -130,10 +130,8 @@ struct ModeSampler {
   int32_t support(int d) const {
     return box[d] > 0 ? box[d] : (int32_t)std::ceil(alpha * L[d] * std::sqrt(21.0 * std::log(10.0)) / kPi);
   }
-  // exact i.i.d. draws: inverse CDF per dimension, rejection of I u {0}
-  void exact(uint64_t seed, uint64_t step, int P, int32_t *out) const {
-    std::vector<double> cdf[3];
-    int32_t sup[3];
+  // the per-dimension cumulative distributions of the exact sampler (also the device sampler's)
+  void exact_tables(std::vector<double> cdf[3], int32_t sup[3]) const {
     for (int d = 0; d < 3; ++d) {
       sup[d] = support(d);
       cdf[d].resize(2 * sup[d] + 1);
@@ -145,6 +143,12 @@ struct ModeSampler {
       }
       for (double &v : cdf[d]) v /= acc;
     }
+  }
+  // exact i.i.d. draws: inverse CDF per dimension, rejection of I u {0}
+  void exact(uint64_t seed, uint64_t step, int P, int32_t *out) const {
+    std::vector<double> cdf[3];
+    int32_t sup[3];
+    exact_tables(cdf, sup);
     uint64_t tries = 0;
     for (int l = 0; l < P;) {
       const uint64_t c[4] = {tries++, step, 1, 0};
@@ -286,6 +290,12 @@ __global__ void k_interleave3(int64_t n, const double *__restrict__ x, const dou
 // per-context host state that the kernels never see
 struct srbe::HostExt {
   ModeSampler sampler;
+  // the exact sampler on the device: its tables (the host sampler's own cumulative distributions)
+  bool dev_sampler = false;
+  DevBuf<double> dev_cdf;
+  int32_t dev_sup[3] = {0, 0, 0};
+  DevBuf<int4> dev_step;   // step word for srbe_sample_k_device
+  DevBuf<int> dev_err;     // set when the device sampler ran out of tries
   std::vector<double> hq;  // the ion charges last handed to srbe_set_positions (host copy)
   DevBuf<double> aos;      // AoS staging for positions / forces
   bool forces_valid = false;
@@ -568,6 +578,130 @@ __global__ void k_stage_many(const StageEntry *__restrict__ tab) {
   }
 }
 
+// The exact i.i.d. sampler (inverse CDF per dimension, rejection of I u {0}) on the device, one block:
+// tries are numbered as on the host (Philox4x64-10, key (seed, 'SRBE' 2), counter (try, step, 1, 0)),
+// 256 per round, accepted ones placed in try order by a block scan, so the list is bitwise the host
+// sampler's; weights (G / P) 4 pi / (V k^2) with the host's operations in the host's order.
+constexpr int kSampleThreads = 256;
+constexpr int kSampleRounds = 1 << 12;     // 1M tries at most (a round accepts nearly all of its 256)
+struct DevSampleArgs {
+  const int4 *step_src;     // (step low, step high, seed low, seed high)
+  int P, M;
+  int32_t box[3], sup[3];
+  const double *cdf;        // the three tables back to back, 2 sup[d] + 1 entries each
+  double L[3], G, V;
+  int4 *dm;                 // modes: I at [0, M) (left as they are), samples at [M, M + P), step word at M + P
+  double *dc;               // weights, the same layout
+  int *err;
+};
+__device__ __forceinline__ int cdf_search(const double *cdf, int n, double u) {
+  // first index in [0, n - 1) with cdf >= u, else n - 1 (the host's lower_bound over [0, n - 1))
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cdf[mid] < u) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+__global__ void __launch_bounds__(kSampleThreads) k_sample_exact(DevSampleArgs a) {
+  __shared__ int scan[kSampleThreads];
+  __shared__ int s_count;
+  const int t = threadIdx.x;
+  const int4 sw = *a.step_src;
+  const uint64_t step = (uint64_t)(uint32_t)sw.x | ((uint64_t)(uint32_t)sw.y << 32);
+  const uint64_t seed = (uint64_t)(uint32_t)sw.z | ((uint64_t)(uint32_t)sw.w << 32);
+  if (t == 0) {
+    s_count = 0;
+    a.dm[a.M + a.P] = sw;   // the step word of the list (the thermostat reads its step half)
+  }
+  const double *cd[3] = {a.cdf, a.cdf + 2 * a.sup[0] + 1, a.cdf + 2 * a.sup[0] + 1 + 2 * a.sup[1] + 1};
+  __syncthreads();
+  for (int round = 0; round < kSampleRounds; ++round) {
+    uint64_t w[4];
+    philox4x64_dev((uint64_t)round * kSampleThreads + t, step, 1, 0, seed, 0x5352424500000002ull, w);
+    int32_t m[3];
+    bool ok = true;
+    for (int d = 0; d < 3; ++d) {
+      const double u = ((double)(w[d] >> 11) + 1.0) * 0x1.0p-53;
+      m[d] = cdf_search(cd[d], 2 * a.sup[d] + 1, u) - a.sup[d];
+      if (a.box[d] > 0 && abs(m[d]) > a.box[d]) ok = false;
+    }
+    if (m[0] == 0 && m[1] == 0 && abs(m[2]) <= a.M) ok = false;
+    // inclusive block scan of the accept flags (Hillis-Steele)
+    scan[t] = ok ? 1 : 0;
+    __syncthreads();
+    for (int off = 1; off < kSampleThreads; off <<= 1) {
+      const int v = t >= off ? scan[t - off] : 0;
+      __syncthreads();
+      scan[t] += v;
+      __syncthreads();
+    }
+    const int pos = s_count + scan[t] - (ok ? 1 : 0);
+    if (ok && pos < a.P) {
+      a.dm[a.M + pos] = make_int4(m[0], m[1], m[2], 0);
+      double k2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double kd = __ddiv_rn(__dmul_rn(2.0 * kPi, (double)m[d]), a.L[d]);
+        k2 = __dadd_rn(k2, __dmul_rn(kd, kd));
+      }
+      a.dc[a.M + pos] = __ddiv_rn(__dmul_rn(__dmul_rn(__ddiv_rn(a.G, (double)a.P), 4.0), kPi), __dmul_rn(a.V, k2));
+    }
+    __syncthreads();
+    if (t == 0) s_count += scan[kSampleThreads - 1];
+    __syncthreads();
+    if (s_count >= a.P) return;
+  }
+  if (t == 0) atomicExch(a.err, 1);
+}
+
+inline int4 sample_word(uint64_t step, uint64_t seed) {
+  return make_int4((int)(uint32_t)step, (int)(uint32_t)(step >> 32), (int)(uint32_t)seed, (int)(uint32_t)(seed >> 32));
+}
+
+DevSampleArgs dev_sample_args(srbe_ctx *c, const int4 *step_src) {
+  Extra *e = extra(c);
+  DevSampleArgs a;
+  a.step_src = step_src;
+  a.P = c->P;
+  a.M = c->M;
+  for (int d = 0; d < 3; ++d) {
+    a.box[d] = c->mmax[d];
+    a.sup[d] = e->dev_sup[d];
+    a.L[d] = c->L[d];
+  }
+  a.cdf = e->dev_cdf.p;
+  a.G = c->G;
+  a.V = c->V;
+  a.dm = c->dm.p;
+  a.dc = c->dc.p;
+  a.err = e->dev_err.p;
+  return a;
+}
+
+// the host sampler's cumulative distributions, uploaded for the device sampler
+void upload_sampler_tables(srbe_ctx *c) {
+  Extra *e = extra(c);
+  std::vector<double> cdf[3];
+  e->sampler.exact_tables(cdf, e->dev_sup);
+  std::vector<double> all;
+  for (auto &v : cdf) all.insert(all.end(), v.begin(), v.end());
+  double *d = e->dev_cdf.ensure(all.size());
+  SRBE_CUDA(cudaMemcpy(d, all.data(), sizeof(double) * all.size(), cudaMemcpyHostToDevice));
+  e->dev_step.ensure(1);
+  SRBE_CUDA(cudaMemset(e->dev_err.ensure(1), 0, sizeof(int)));
+}
+
+void check_dev_sampler(srbe_ctx *c) {
+  int h = 0;
+  SRBE_CUDA(cudaMemcpyAsync(&h, extra(c)->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  SRBE_CUDA(cudaStreamSynchronize(c->stream));
+  if (h) {
+    SRBE_CUDA(cudaMemset(extra(c)->dev_err.p, 0, sizeof(int)));
+    throw Error{SRBE_ENOTCONV, "device sampler: fewer than P admissible modes in 2^20 tries"};
+  }
+}
+
 // one captured MD step of c; staged: the mode list is already on the device (batch graphs)
 void device_step(srbe_ctx *c, int slot, bool staged) {
   Extra *e = extra(c);
@@ -576,12 +710,16 @@ void device_step(srbe_ctx *c, int slot, bool staged) {
                "mode buffers not reserved for a captured step");
   if (!staged) {
     // the mode list comes in through a kernel on the side stream that reads the pinned slot while
-    // the opening kick runs (nothing before S1 reads it; the opening kick has no thermostat)
+    // the opening kick runs (nothing before S1 reads it; the opening kick has no thermostat): the
+    // host's list, or with the device sampler only the slot's (step, seed) word
     SRBE_CUDA(cudaEventRecord(c->ev_fork, c->stream));
     SRBE_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    k_stage_modes<<<std::min(blocks_for((int64_t)K + 1, 256), 64u), 256, 0, c->side>>>(K, e->slot[slot].dhm,
-                                                                                       e->slot[slot].dhw, c->dm.p,
-                                                                                       c->dc.p);
+    if (e->dev_sampler)
+      k_sample_exact<<<1, kSampleThreads, 0, c->side>>>(dev_sample_args(c, e->slot[slot].dhm + K));
+    else
+      k_stage_modes<<<std::min(blocks_for((int64_t)K + 1, 256), 64u), 256, 0, c->side>>>(K, e->slot[slot].dhm,
+                                                                                         e->slot[slot].dhw, c->dm.p,
+                                                                                         c->dc.p);
     c->launches++;
     SRBE_CUDA(cudaGetLastError());
     SRBE_CUDA(cudaEventRecord(c->ev_modes, c->side));
@@ -1216,11 +1354,67 @@ int srbe_set_sampler(srbe_ctx *c, int kind, const int32_t *mmax) {
     Extra *e = extra(c);
     e->sampler.init(c->L, c->alpha, c->M, c->mmax);
     c->G = e->sampler.G();
+    if (e->dev_sampler) {
+      if (kind == SRBE_SAMPLER_EXACT) upload_sampler_tables(c);
+      else e->dev_sampler = false;
+    }
   });
 }
 
 int srbe_sample_k(srbe_ctx *c, uint64_t seed, uint64_t step) {
   return guarded(c, [&] { sample_into(c, seed, step); });
+}
+
+int srbe_set_device_sampler(srbe_ctx *c, int on) {
+  return guarded(c, [&] {
+    Extra *e = extra(c);
+    if (on) {
+      SRBE_REQUIRE(c->sampler == SRBE_SAMPLER_EXACT, SRBE_EINVAL,
+                   "the device sampler is the exact one: select SRBE_SAMPLER_EXACT first");
+      upload_sampler_tables(c);
+    }
+    e->dev_sampler = on != 0;
+  });
+}
+
+int srbe_sample_k_device(srbe_ctx *c, uint64_t seed, uint64_t step, int32_t *m, double *w) {
+  return guarded(c, [&] {
+    Extra *e = extra(c);
+    SRBE_REQUIRE(e->dev_sampler, SRBE_ESTATE, "device sampler not enabled (srbe_set_device_sampler)");
+    const int P = c->P, M = c->M;
+    // the list's layout (I, then P samples, then the step word) with zero samples for the kernel to
+    // overwrite
+    std::vector<int32_t> zero((size_t)3 * P, 0);
+    srbe_host_list(c, zero.data(), P);
+    upload_modes(c);
+    const int4 word = sample_word(step, seed);
+    SRBE_CUDA(cudaMemcpyAsync(e->dev_step.p, &word, sizeof(int4), cudaMemcpyHostToDevice, c->stream));
+    k_sample_exact<<<1, kSampleThreads, 0, c->stream>>>(dev_sample_args(c, e->dev_step.p));
+    c->launches++;
+    SRBE_CUDA(cudaGetLastError());
+    // the list's step word stays the MD step (the thermostat's), as after srbe_sample_k
+    const int4 md = step_word(c->md_step);
+    SRBE_CUDA(cudaMemcpyAsync(c->dm.p + c->K, &md, sizeof(int4), cudaMemcpyHostToDevice, c->stream));
+    std::vector<int4> hm4((size_t)std::max(P, 1));
+    std::vector<double> hw((size_t)std::max(P, 1));
+    if (P > 0) {
+      SRBE_CUDA(cudaMemcpyAsync(hm4.data(), c->dm.p + M, sizeof(int4) * P, cudaMemcpyDeviceToHost, c->stream));
+      SRBE_CUDA(cudaMemcpyAsync(hw.data(), c->dc.p + M, sizeof(double) * P, cudaMemcpyDeviceToHost, c->stream));
+    }
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    check_dev_sampler(c);
+    // the host copy of the list follows the device's
+    for (int l = 0; l < P; ++l) {
+      const int32_t v[3] = {hm4[l].x, hm4[l].y, hm4[l].z};
+      for (int d = 0; d < 3; ++d) {
+        c->hm[4 * (M + l) + d] = v[d];
+        c->hsamp[3 * l + d] = v[d];
+        if (m) m[3 * l + d] = v[d];
+      }
+      c->hc[M + l] = hw[l];
+      if (w) w[l] = hw[l];
+    }
+  });
 }
 
 int srbe_get_k(const srbe_ctx *cc, int32_t *m, double *G) {
@@ -1322,8 +1516,14 @@ int srbe_step(srbe_ctx *c, int nsteps, uint64_t seed0) {
       for (int s = 0; s < nsteps; ++s) {
         c->md_step++;
         const int slot = (int)(c->md_step & 1);
-        build_host_list(c, seed0, c->md_step);
-        fill_slot(c, slot);
+        if (e->dev_sampler) {
+          // the captured step samples its modes on the device from this word
+          SRBE_CUDA(cudaEventSynchronize(e->slot[slot].done));
+          e->slot[slot].hm[c->K] = sample_word(c->md_step, seed0);
+        } else {
+          build_host_list(c, seed0, c->md_step);
+          fill_slot(c, slot);
+        }
         coop_before(c);
         SRBE_CUDA(cudaGraphLaunch(e->slot[slot].exec, c->stream));
         coop_after(c);

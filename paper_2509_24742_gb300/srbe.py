@@ -53,6 +53,8 @@ EXPORTS = {
     "srbe_set_md": ([_vp, _dp, _dp, _int, _ip, _ip, _dp, _dp, _i64, _ip, _dp, _dbl, _dbl], _int),
     "srbe_set_sampler": ([_vp, _int, _ip], _int),
     "srbe_sample_k": ([_vp, _u64, _u64], _int),
+    "srbe_set_device_sampler": ([_vp, _int], _int),
+    "srbe_sample_k_device": ([_vp, _u64, _u64, _ip, _dp], _int),
     "srbe_get_k": ([_vp, _ip, _dp], _int),
     "srbe_set_k": ([_vp, _ip, _int], _int),
     "srbe_set_mode_list": ([_vp, _ip, _dp, _int], _int),
@@ -225,6 +227,16 @@ class Context:
     # --- modes
     def sample_k(self, seed, step=0):
         self._check(self.lib.srbe_sample_k(self.h, int(seed), int(step)))
+
+    def set_device_sampler(self, on=True):
+        self._check(self.lib.srbe_set_device_sampler(self.h, 1 if on else 0))
+
+    def sample_k_device(self, seed, step=0):
+        """The exact sampler's draw on the device: (m [P][3], w [P])."""
+        m = np.empty((self.P, 3), np.int32)
+        w = np.empty(self.P)
+        self._check(self.lib.srbe_sample_k_device(self.h, int(seed), int(step), _ptr(m, _ip), _ptr(w)))
+        return m, w
 
     def get_k(self):
         m = np.empty((self.P, 3), np.int32)
