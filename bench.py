@@ -14,11 +14,14 @@ library's stream and the per-phase device times come from the library's own even
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch64 [--replicas R] [--steps K] [--warmup W]
+  python bench.py --workload prec100k | large1m | solve6144 | noise [--steps K]
 
-The second form measures the batching form instead: R uneven replicas (default 64; 8k-57k
-particles, 1,536-6,144 electrode sites, 0-4 V, Lz/Lx 3-8, P 100-400, each with its own seed)
-stepped as one CUDA-graph launch per batch step, against the same replicas stepped one after
-another with the plain FP64 path.
+batch64 measures the batching form instead: R uneven replicas (default 64; 8k-57k particles,
+1,536-6,144 electrode sites, 0-4 V, Lz/Lx 3-8, P 100-400, each with its own seed) stepped as one
+CUDA-graph launch per batch step, against the same replicas stepped one after another with the
+plain FP64 path.  prec100k and large1m run the precision form on the 100k-particle and 1.2 M-particle
+slabs against FP64; solve6144 times the charge update alone against the HBM roofline; noise gives
+the electrode-charge standard deviation over sampling seeds against M and P.
 """
 from __future__ import annotations
 
