@@ -14,7 +14,7 @@ library's stream and the per-phase device times come from the library's own even
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch64 [--replicas R] [--steps K] [--warmup W]
-  python bench.py --workload prec100k | large1m | solve6144 | noise [--steps K]
+  python bench.py --workload prec100k | large1m | solve6144 | noise | learned | mlp [--steps K]
 
 batch64 measures the batching form instead: R uneven replicas (default 64; 8k-57k particles,
 1,536-6,144 electrode sites, 0-4 V, Lz/Lx 3-8, P 100-400, each with its own seed) stepped as one
@@ -185,10 +185,12 @@ def roofline(phase, ms_per_launch, slab, K, n_ii, n_ie, precision, pk):
         flops = slab.n_ion * K * FLOP_MODE + n_ie * FLOP_PAIR
         kern = "k_ion_forces<1,0,2>"
     elif phase == "forces_ii":
-        flops = 2 * n_ii * FLOP_PAIR
-        kern = "k_ion_forces<1,0,1>"
+        # each ion-ion pair within rc counted once (the kernel may evaluate it from both ends: that
+        # is extra work, not algorithmic work)
+        flops = n_ii * FLOP_PAIR
+        kern = "k_ion_ii<1>"
     elif phase == "forces":
-        flops = slab.n_ion * K * FLOP_MODE + (2 * n_ii + n_ie) * FLOP_PAIR
+        flops = slab.n_ion * K * FLOP_MODE + (n_ii + n_ie) * FLOP_PAIR
         kern = "k_ion_forces<0,0,0>"
     elif phase in ("S1", "S2"):
         n = slab.n_ion if phase == "S1" else slab.n_ele
@@ -202,8 +204,12 @@ def roofline(phase, ms_per_launch, slab, K, n_ii, n_ie, precision, pk):
     peak = pk["fp32_tflops"] if precision == "mixed" else pk["fp64_tflops"]
     ach = flops / t / 1e12
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "peak_source": "nominal (152 SMs x 128 FP32 lanes x 2 x 2070 MHz)" if precision == "mixed"
-            else "nominal GB300 FP64 1.25 TFLOP/s", "algorithmic_flops": flops, "kernel": kern}
+            "peak_source": "derived from unit counts and the maximum clock: 152 SMs x 128 FP32 lanes x 2 flop "
+                           "(FMA) x 2070 MHz = 80.5 TFLOP/s (MEASURED_PEAKS.json has no FP32 figure)"
+            if precision == "mixed" else "nominal GB300 FP64 1.25 TFLOP/s", "algorithmic_flops": flops,
+            "flop_counting": "%d flop per mode evaluation, %d per pair within rc, each pair once" % (FLOP_MODE,
+                                                                                                 FLOP_PAIR),
+            "kernel": kern}
 
 
 def job_throughput(ms_local, steps, world, device):
@@ -256,8 +262,11 @@ def gpu_arm(args, rank, world):
         """Device time of `steps` MD steps, each bracketed by CUDA events on the context's stream,
         with an L2 flush between steps.  Untraced, srbe_step replays its captured CUDA graph;
         traced, the ordinary launch path records an event pair around every phase."""
-        ctx.set_profiling(traced)
+        ctx.set_profiling(False)
         ctx.step(warm, SEED)
+        # tracing starts after the warm-up steps (switching it on resets the phase sums), so the
+        # phase split covers exactly the timed steps
+        ctx.set_profiling(traced)
         torch.cuda.synchronize()
         l0, _ = ctx.counters()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -346,40 +355,44 @@ def gpu_arm(args, rank, world):
 
 
 def e2e_arm(ctx, slab, stream, flush, steps):
+    """End to end through the public host-memory API, as an MD engine that keeps positions and
+    forces in host memory would call it: the engine's next frame is copied into a pinned input buffer
+    bound with srbe_set_host_io, then srbe_forces_host_io (one CUDA-graph replay: positions read from
+    the pinned buffer, the full force pass, forces and charges written back into pinned buffers)
+    returns once the host buffers hold the result."""
     import torch
     n, ne = slab.n_ion, slab.n_ele
-    r_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
-    q_h = torch.empty(n, dtype=torch.float64).pin_memory()
-    F_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
-    Q_h = torch.empty(ne, dtype=torch.float64).pin_memory()
-    q_h.numpy()[:] = slab.q
-    rn, qn, Fn, Qn = r_h.numpy(), q_h.numpy(), F_h.numpy(), Q_h.numpy()
     # the positions an MD engine would hand in: the context's own trajectory, one frame per step
     # (recorded untimed), so that the Verlet lists age and get rebuilt as they would in a run
     traj = []
     for i in range(steps + 3):
         ctx.step(1, SEED)
         traj.append(ctx.get_positions())
+    r_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    F_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    Q_h = torch.empty(ne, dtype=torch.float64).pin_memory()
+    rn, Fn, Qn = r_h.numpy(), F_h.numpy(), Q_h.numpy()
+    ctx.set_positions(traj[0], slab.q)
+    ctx.set_host_io(r_h.data_ptr(), F_h.data_ptr(), Q_h.data_ptr())
     for i in range(3):
         rn[:] = traj[i]
-        ctx.set_positions(rn, qn)
-        ctx.sample_k(SEED, 10_000 + i)
-        ctx.forces(out=(Fn, Qn))
+        ctx.forces_host_io(SEED, 10_000 + i)
     tot = 0.0
     for i in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rn[:] = traj[3 + i]
-        ctx.set_positions(rn, qn)
-        ctx.sample_k(SEED, 20_000 + i)
-        ctx.forces(out=(Fn, Qn))
+        ctx.forces_host_io(SEED, 20_000 + i)
+        f_sum = float(Fn[0, 0])             # the host reads the result
         tot += time.perf_counter() - t0
         with torch.cuda.stream(stream):
             flush.zero_()
-    return {"value": steps / tot, "unit": UNIT, "h2d_bytes_per_step": int(rn.nbytes + qn.nbytes),
-            "d2h_bytes_per_step": int(Fn.nbytes + Qn.nbytes),
-            "what": "host-pointer force provider: srbe_set_positions (next frame of an MD trajectory) + "
-                    "srbe_sample_k + srbe_forces per step"}
+    assert np.isfinite(f_sum)
+    return {"value": steps / tot, "unit": UNIT, "h2d_bytes_per_step": int(rn.nbytes),
+            "d2h_bytes_per_step": int(Fn.nbytes + Qn.nbytes + 8),
+            "what": "host-memory force provider: the next frame of an MD trajectory copied into a pinned buffer, "
+                    "then srbe_forces_host_io (positions read from pinned host memory, sampling of the step's "
+                    "modes, the full force pass, forces and charges written to pinned host memory) per step"}
 
 
 # ---------------------------------------------------------------------------------------------- precision form
@@ -625,6 +638,176 @@ def batch_arm(args):
     }
 
 
+def learned_arm(args):
+    """The learned form on the benchmark's slab (11,072 sites, P = 200 > 0, M = 4, 1 V, Langevin 400 K):
+    the MLP is trained on plain-method data (FP64 direct solve, descriptors and solutions y of every
+    step of a seeded MD run), then MD runs from the same state with the charge update as PCG to a
+    relative residual of 1e-8 from a cold, a previous-step and a learned start, in FP64 and in the
+    mixed form, beside the direct solves; last, R replicas of the slab (own seeds) in the learned
+    mixed PCG form as one batch against the plain FP64 direct path stepping them one by one."""
+    import torch
+    from paper_2509_24742_gb300 import srbe, workloads
+    torch.cuda.set_device(0)
+    t_setup = time.time()
+    slab = workloads.md_11072()
+    with srbe.from_slab(slab, precision=srbe.MIXED, md=True) as cm:
+        cm.minimize(N_MIN)
+        slab.r = cm.get_positions()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    n_data = 240
+    with srbe.from_slab(slab, precision=srbe.FP64, md=True) as ctx:
+        ctx.set_stream(stream.cuda_stream)
+        ctx.set_thermostat(GAMMA, T_BATH, SEED)
+        ctx.step(20, SEED)
+        Ds, Ys = [], []
+        for _ in range(n_data):
+            ctx.step(1, SEED)
+            Ds.append(ctx.descriptors())
+            Ys.append(ctx.solution())
+        n_tr = int(0.8 * n_data)
+        t_train = time.time()
+        ctx.mlp_init(seed=3)
+        loss = ctx.mlp_train(np.concatenate(Ds[:n_tr]), np.concatenate(Ys[:n_tr]), epochs=20, batch=512, lr=2e-3,
+                             weight_decay=1e-6, seed=1)
+        t_train = time.time() - t_train
+        held = float(np.mean([np.linalg.norm(ctx.mlp_predict(Ds[i]) - Ys[i]) / np.linalg.norm(Ys[i])
+                              for i in range(n_tr, n_data)]))
+        step_change = float(np.mean([np.linalg.norm(Ys[i] - Ys[i - 1]) / np.linalg.norm(Ys[i])
+                                     for i in range(n_tr, n_data)]))
+        params = ctx.mlp_params()
+        r0, v0 = ctx.get_positions(velocities=True)
+    t_setup = time.time() - t_setup
+
+    def start(prec, solver, warm, seed=SEED):
+        s2 = workloads.md_11072()
+        s2.r, s2.v = r0, v0
+        c = srbe.from_slab(s2, precision=prec, md=True)
+        c.set_stream(stream.cuda_stream)
+        c.set_thermostat(GAMMA, T_BATH, seed)
+        c.mlp_set_params(params)
+        if solver == srbe.PCG:
+            c.set_solver(srbe.PCG, tol=1e-8, maxit=2000, warm=warm)
+        return c
+
+    def timed(c, steps, seed=SEED):
+        c.step(args.warmup, seed)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.step(1, seed)
+            e1.record(stream)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return steps / (ms * 1e-3)
+
+    forms = [("fp64_direct", srbe.FP64, srbe.DIRECT, None), ("mixed_direct", srbe.MIXED, srbe.DIRECT, None)]
+    for pname, prec in (("fp64", srbe.FP64), ("mixed", srbe.MIXED)):
+        for wname, warm in (("cold", srbe.WARM_ZERO), ("previous", srbe.WARM_PREVIOUS), ("learned", srbe.WARM_MODEL)):
+            forms.append(("%s_pcg_%s" % (pname, wname), prec, srbe.PCG, warm))
+    steps = max(10, min(args.steps, 100))
+    results = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, prec, solver, warm in forms:
+        c = start(prec, solver, warm)
+        sps = timed(c, steps)
+        res = c.charge_residual()
+        its = []
+        if solver == srbe.PCG:
+            for _ in range(10):
+                c.step(1, SEED)
+                its.append(c.solver_stats()[0])
+        results[name] = {"steps_per_s": sps, "fp64_charge_residual": res,
+                         "pcg_iterations_mean": float(np.mean(its)) if its else None}
+        c.close()
+    # batched: R replicas in the learned mixed PCG form against the plain FP64 direct path
+    R = 8
+    seeds = np.arange(1, R + 1, dtype=np.uint64) * 7919
+    ctxs = [start(srbe.MIXED, srbe.PCG, srbe.WARM_MODEL, int(sd)) for sd in seeds]
+    b = srbe.Batch(ctxs)
+    bs = torch.cuda.ExternalStream(b.stream())
+    b.step(args.warmup, seeds)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bs)
+    b.step(steps, seeds)
+    e1.record(bs)
+    torch.cuda.synchronize()
+    batch_value = R * steps / (e0.elapsed_time(e1) * 1e-3)
+    bres = b.step(1, seeds, residuals=True)
+    clk = clocks.stop()
+    b.close()
+    for c in ctxs:
+        c.close()
+    plain = results["fp64_direct"]["steps_per_s"]
+    return {
+        "metric": "SRBE MD steps/s at FP64 charge residual <= 1e-8, learned form", "value": batch_value,
+        "unit": "replica-steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "md11072_P200 (the benchmark slab), Langevin 400 K; batch of %d replicas with "
+                               "own seeds" % R, "l2": "flushed between timed steps (256 MB write), single forms"},
+        "learned_mixed_pcg_batched": {"replica_steps_per_s": batch_value, "fp64_residual_max": float(np.max(bres)),
+                                      "vs_plain_fp64_direct": batch_value / plain},
+        "forms": results,
+        "training": {"steps_of_data": n_data, "rows": n_tr * slab.n_ele, "train_s": t_train, "final_loss": loss,
+                     "held_out_rel_err_of_y": held, "mean_step_to_step_change_of_y": step_change},
+        "setup_s": t_setup, "clocks": clk,
+    }
+
+
+def mlp_arm(args):
+    """The learned form's forward pass alone on the tensor cores: predictions for 98,304 electrode
+    sites (the 1.2 M-particle slab's electrode) per call, timed with CUDA events, against the measured
+    BF16 tensor peak.  Algorithmic work per row: 2 (80 x 128 + 128 x 128) flop of the two GEMMs; the
+    split-BF16 products run three MMAs per GEMM, which is extra work, not algorithmic work."""
+    import torch
+    from paper_2509_24742_gb300 import srbe, workloads
+    torch.cuda.set_device(0)
+    pk = peaks()
+    slab = workloads.one_shot_784()
+    n = 98_304
+    rng = np.random.default_rng(5)
+    D = rng.normal(size=(n, 80)).astype(np.float32)
+    stream = torch.cuda.Stream()
+    with srbe.from_slab(slab) as ctx:
+        ctx.set_stream(stream.cuda_stream)
+        ctx.mlp_init(seed=7)
+        y0 = ctx.mlp_predict(D[:4096])
+        Dd = torch.from_numpy(D).cuda()
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            ctx.mlp_predict_dev(Dd.data_ptr(), n, out.data_ptr())
+        torch.cuda.synchronize()
+        # events on the stream the kernels run on
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(10, min(args.steps, 200))
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.mlp_predict_dev(Dd.data_ptr(), n, out.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        y1 = out[:4096].cpu().numpy()
+    flops = 2.0 * n * (80 * 128 + 128 * 128)
+    ach = flops / (ms * 1e-3) / 1e12
+    peak = float(pk.get("bf16_tflops", 1915.5))
+    return {"metric": "MLP forward rows/s on the tensor cores (learned warm start)", "value": n / (ms * 1e-3),
+            "unit": "rows/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_call": ms,
+            "higher_is_better": True, "dtype": "bf16x3+f32", "data": "synthetic",
+            "config": {"workload": "mlp98304: 98,304 rows x 80 inputs, 80-128-128-1 SiLU",
+                       "l2": "inputs 31 MB (L2-resident between calls)"},
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "peak_source": "measured BF16 burst (cuBLAS 8192^3)", "algorithmic_flops": flops,
+                         "kernel": "k_mlp_forward_tc"},
+            "host_vs_device_path_max_abs_diff": float(np.abs(y0 - y1).max())}
+
+
 # ---------------------------------------------------------------------------------------------- CPU oracle
 def oracle_steps(budget_s, max_steps, min_steps=2, warmup=0):
     """Full oracle MD steps (plain FP64 C, OpenMP over independent output elements) on the same
@@ -686,7 +869,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="md11072",
-                    choices=["md11072", "batch64", "prec100k", "solve6144", "large1m", "noise"])
+                    choices=["md11072", "batch64", "prec100k", "solve6144", "large1m", "noise", "learned", "mlp"])
     ap.add_argument("--replicas", type=int, default=64)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -709,6 +892,12 @@ def main():
         return
     if args.workload == "noise":
         print(json.dumps(noise_arm(args)))
+        return
+    if args.workload == "learned":
+        print(json.dumps(learned_arm(args)))
+        return
+    if args.workload == "mlp":
+        print(json.dumps(mlp_arm(args)))
         return
     if world > 1:
         import torch

@@ -35,8 +35,31 @@ enum srbe_status {
   SRBE_ECUDA = 3,    /* a CUDA call failed; the message names it */
   SRBE_ESTATE = 4,   /* call out of order (e.g. forces before positions) */
   SRBE_ENOTCONV = 5, /* iterative solve did not reach its tolerance */
-  SRBE_ETIMEOUT = 6  /* a bounded device wait gave up */
+  SRBE_ETIMEOUT = 6, /* a bounded wait for the device gave up (srbe_synchronize) */
+  SRBE_ENONFINITE = 7 /* a force or an electrode charge came out NaN or infinite */
 };
+
+/* Errors found on the device.  Kernels raise flags in a few words of host-mapped memory owned by
+ * the context: an iterative charge solve that stopped at maxit (SRBE_ENOTCONV; the charges of that
+ * pass then come from the direct solve instead, see srbe_set_solver) and a non-finite force or
+ * charge (SRBE_ENONFINITE; checked on every force pass, on every charge update of
+ * srbe_solve_electrode_charges, and in the closing half kick of every MD step).  A flag is reported,
+ * and cleared, by the first of these calls that sees it: srbe_forces and
+ * srbe_solve_electrode_charges (after their outputs are written, so the outputs of that call are
+ * valid host copies of what the device holds), srbe_synchronize, srbe_step, which is asynchronous:
+ * it reports SRBE_ENONFINITE (and a bad input) raised by earlier steps at its start and between the
+ * steps it queues, as soon as the host sees them, and then steps no further, and srbe_batch_step
+ * (each replica's flags, at its start).  Neither of the two stops for SRBE_ENOTCONV, since that pass
+ * took the direct solve's charges: the flag stays raised for srbe_synchronize (or the next
+ * srbe_forces / srbe_solve_electrode_charges).  srbe_minimize reports SRBE_ENOTCONV only: its forces may overflow where the random packing
+ * put two sites on top of each other, which its capped step handles.  srbe_forces_dev is
+ * asynchronous and leaves its flags to the next of these calls.  SRBE_ENONFINITE takes precedence
+ * over SRBE_ENOTCONV; srbe_last_error names what was found.
+ *
+ * srbe_synchronize: waits for every pass queued on the context's streams, at most timeout_s seconds
+ * (timeout_s < 0: without limit), then reports the device flags.  SRBE_ETIMEOUT if work is still
+ * running at the limit (nothing is cancelled; the call may be repeated). */
+int srbe_synchronize(srbe_ctx *ctx, double timeout_s);
 
 enum srbe_precision {
   SRBE_FP64 = 0,  /* every sum, phase and pair term in FP64 */
@@ -93,7 +116,7 @@ double srbe_get_alpha_A(const srbe_ctx *ctx);
  * side other than 0/1, one side empty, non-finite R), SRBE_ENOTCONV if A is not positive definite. */
 int srbe_set_electrode(srbe_ctx *ctx, int64_t n_ele, const double *R, const int8_t *side);
 
-/* Sets the n_ion electrolyte positions r [n_ion][3] (nm) and charges q (e).  n_ion may be 0.
+/* Sets the n_ion electrolyte positions r [n_ion][3] (nm) and charges q (e).  0 <= n_ion <= 8,388,607.
  * Positions outside [0,L) in x or y are wrapped.  With the same ion count and the same charges as
  * the previous call (an MD engine handing in each step's positions) the Verlet lists are kept and
  * rebuilt only once an ion has moved more than half the skin since their build; otherwise they are
@@ -172,6 +195,22 @@ int srbe_step(srbe_ctx *ctx, int nsteps, uint64_t seed0);
  * random packing); needs srbe_set_md.  Velocities are kept. */
 int srbe_minimize(srbe_ctx *ctx, int nsteps, double a, double dmax, uint64_t seed);
 
+/* Captured force provider for an MD engine that keeps its state in host memory (no counterpart in
+ * the paper; launch- and copy-overhead removal).  srbe_set_host_io binds three caller-owned buffers of
+ * page-locked host memory mapped for the device (cudaHostAlloc, or registered with cudaHostRegister;
+ * the caller keeps ownership and must keep them alive while bound): r [n_ion][3] positions in,
+ * F [n_ion][3] forces out, Q [n_ele] charges out (Q may be NULL).  srbe_forces_host_io then equals
+ * srbe_set_positions(r, same charges) + srbe_sample_k(seed, step) + srbe_forces(F, Q, psi_bar), bitwise,
+ * as one CUDA-graph replay per call: a kernel reads the positions straight from the bound buffer, the
+ * force pass runs, a kernel writes F (and Q) back into the bound buffers, and the call returns once
+ * they hold the result.  The first call after any state change (and after srbe_set_host_io) runs the
+ * ordinary way and captures the graphs.  The charges are those of the last srbe_set_positions.
+ * Errors: SRBE_ESTATE (not bound, no electrode or positions), SRBE_EINVAL (a buffer that is not mapped
+ * page-locked memory; a non-finite position in r, which that pass replaced by the origin), and the
+ * device flags of srbe_synchronize. */
+int srbe_set_host_io(srbe_ctx *ctx, double *r, double *F, double *Q);
+int srbe_forces_host_io(srbe_ctx *ctx, uint64_t seed, uint64_t step, double *psi_bar);
+
 /* Device-resident variants: same as the host calls, with device pointers on the context's
  * stream and no host copies.  F_dev [n_ion*3], Q_dev [n_ele] may be NULL. */
 int srbe_set_positions_dev(srbe_ctx *ctx, int64_t n_ion, const double *r_dev, const double *q_dev);
@@ -219,13 +258,16 @@ int srbe_get_phase_times(srbe_ctx *ctx, double *ms, int64_t *count);
  * needs no dense matrix.  srbe_set_electrode picks it for lattice electrodes of 8,192 sites or
  * more; beyond 16,384 sites it is the only solver (A is not stored densely), otherwise
  * SRBE_SOLVER_DIRECT is the default.  Errors: SRBE_ESTATE for a solver the electrode cannot use. */
+/* A PCG solve that reaches maxit above tol raises SRBE_ENOTCONV (see srbe_synchronize); the same pass
+ * then takes its charges from the direct projected inverse (one extra kernel that runs only in that
+ * case), so the forces and the MD step that follow use converged charges. */
 enum srbe_solver { SRBE_SOLVER_DIRECT = 0, SRBE_SOLVER_PCG = 1, SRBE_SOLVER_LATTICE = 2 };
 enum srbe_warm { SRBE_WARM_ZERO = 0, SRBE_WARM_PREVIOUS = 1, SRBE_WARM_MODEL = 2 };
 int srbe_set_solver(srbe_ctx *ctx, int kind, double tol, int maxit, int warm);
 /* Iterations and the recomputed relative residual of the last PCG solve. */
 int srbe_get_solver_stats(srbe_ctx *ctx, int *iterations, double *rel_residual);
 
-/* The MLP (80 -> 128 -> 128 -> 1, SiLU, FP32) predicts y = A^-1 (dpsi d + b) per electrode site from
+/* The MLP (80 -> 128 -> 128 -> 1, SiLU; FP32 parameters) predicts y = A^-1 (dpsi d + b) per electrode site from
  * 80 descriptors: 32 Gaussian radial densities (centres 0.25..1.25 nm, width 0.035 nm) of the
  * positive and of the negative ion charge within rc, and Re, Im of exp(-i k_z Z_j) S1(k_z) for the 8
  * lowest k_z modes.  Parameters are one float vector (srbe_mlp_get_params gives its length):
@@ -238,7 +280,12 @@ int srbe_mlp_set_params(srbe_ctx *ctx, const float *params, int64_t count);
 int srbe_descriptors(srbe_ctx *ctx, float *D);
 /* The unprojected solution y = Q - psi_bar A^-1 e [n_ele] of the last charge update (the target). */
 int srbe_solution(srbe_ctx *ctx, double *y);
+/* srbe_mlp_predict and the learned warm start run the forward pass on the tensor cores (tcgen05
+ * kind::f16): both GEMMs with operands split into BF16 (hi, lo) pairs, hi hi + hi lo + lo hi products
+ * and FP32 accumulation (about 16 significand bits). */
 int srbe_mlp_predict(srbe_ctx *ctx, const float *D, int64_t n, float *out);
+/* The same with device pointers D_dev [n][80] and out_dev [n], queued on the context's stream. */
+int srbe_mlp_predict_dev(srbe_ctx *ctx, const float *D_dev, int64_t n, float *out_dev);
 /* Gradient of the mean squared standardised error over n rows (no update); grad has the length of
  * the trainable part of the parameter vector (everything before the input mean). */
 int srbe_mlp_gradients(srbe_ctx *ctx, const float *D, const float *target, int64_t n, float *grad, double *loss);
@@ -320,10 +367,16 @@ int srbe_batch_step(srbe_batch *batch, int nsteps, const uint64_t *seeds, double
 int srbe_batch_autotune(srbe_batch *batch, int trial_steps, const uint64_t *seeds, const int *widths, int n_widths,
                         double *ms_per_step);
 
-/* Structure factor without any device allocation (no counterpart in the paper; an interface
+/* Test aid (no counterpart in the paper): from the next pass on, overwrite one entry of the output
+ * with a NaN right after it is computed and before the non-finite check runs: what = 1 the force
+ * F[0], 2 the charge Q[0], 0 stops it.  It exists so that the reporting of SRBE_ENONFINITE can be
+ * tested without driving a trajectory to divergence. */
+int srbe_debug_inject_nonfinite(srbe_ctx *ctx, int what);
+
+/* Structure factor without any device allocation (the paper has no counterpart; an interface
  * for callers that cannot allocate device memory, e.g. an MD engine that hands out every byte of
  * GPU memory from its own pool, or code that must not allocate while its pipeline runs).
- * Computes S(k) = sum_j w_j exp(i k . r_j) (Eq. 15 form) in FP64 for
+ * Computes S(k) = sum_j w_j exp(i k . r_j) in FP64 for
  *   box      host [3]: periodic lengths (nm), k = 2 pi m / L componentwise
  *   r_dev    device [n][3] positions, w_dev device [n] weights (charges), n >= 0
  *   m_dev    device [K][3] integer modes, 0 <= K <= 8192
@@ -331,9 +384,9 @@ int srbe_batch_autotune(srbe_batch *batch, int trial_steps, const uint64_t *seed
  *   stream   cudaStream_t as void* (NULL: legacy default stream); the call is asynchronous
  * Partial sums go to one fixed 2 MiB array (131072 double2) compiled into the library, next to a
  * 16 KiB sin/cos table; every GPU that loads the library holds both until the process exits.
- * The first call on each device does its set-up (looks up the arrays' device addresses and
- * copies the table in, with that device current), so make that first call before any stream
- * capture.  Every call shares the array and leaves its partials there; each partial is written
+ * The first call on each device does its set-up (looks up the arrays' device addresses, copies
+ * the table in, waits for the device to finish that copy and loads the kernels, with that device
+ * current), so make that first call before any stream capture; it may come on any stream.  Every call shares the array and leaves its partials there; each partial is written
  * before it is read, so nothing has to be cleared, but calls that overlap on the GPU race on it.
  * Allocates nothing (no cudaMalloc, cudaFree or allocating library call).
  * Errors: SRBE_EINVAL (bad box, n < 0, K outside [0, 8192], null pointers), SRBE_ECUDA. */

@@ -276,6 +276,48 @@ __global__ void k_interleave(int64_t n, const double *__restrict__ F, double *__
   out[3 * i + 2] = F[2 * n + i];
 }
 
+// the force provider's input: positions [n][3] read from the caller's pinned host buffer (mapped),
+// x and y wrapped into [0, L) as srbe_set_positions does, and their fixed-point phase coordinates for
+// the ion structure factor.  A non-finite position is replaced by the box origin (so that no kernel
+// sees it) and raises the bad-input flag.
+__global__ void k_io_load(int64_t n, const double *__restrict__ r, double Lx, double Ly, double3 invL,
+                          double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
+                          uint64_t *__restrict__ iu, int *__restrict__ status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double X = r[3 * i], Y = r[3 * i + 1], Z = r[3 * i + 2];
+  if (!(isfinite(X) && isfinite(Y) && isfinite(Z))) {
+    X = Y = Z = 0.0;
+    *(volatile int *)(status + kStatBadInput) = 1;
+  }
+  X -= Lx * floor(X / Lx);
+  Y -= Ly * floor(Y / Ly);
+  if (X >= Lx) X -= Lx;
+  if (Y >= Ly) Y -= Ly;
+  x[i] = X;
+  y[i] = Y;
+  z[i] = Z;
+  iu[i] = to_turns64(X, invL.x);
+  iu[n + i] = to_turns64(Y, invL.y);
+  iu[2 * n + i] = to_turns64(Z, invL.z);
+}
+
+// the force provider's output: F [3][ni] as [ni][3], Q and psi_bar into the caller's pinned buffers
+__global__ void k_io_store(int64_t ni, const double *__restrict__ F, double *__restrict__ Fo, int64_t ne,
+                           const double *__restrict__ Q, double *__restrict__ Qo, const double *__restrict__ scal,
+                           double *__restrict__ psi) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ni || i < ne; i += stride) {
+    if (i < ni) {
+      Fo[3 * i] = F[i];
+      Fo[3 * i + 1] = F[ni + i];
+      Fo[3 * i + 2] = F[2 * ni + i];
+    }
+    if (i < ne && Qo) Qo[i] = Q[i];
+    if (i == 0) *psi = scal[kScalPsi];
+  }
+}
+
 __global__ void k_interleave3(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                               const double *__restrict__ z, double *__restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -309,6 +351,26 @@ struct srbe::HostExt {
     cudaEvent_t done = nullptr;
   } slot[2];
   cudaStream_t cap = nullptr;   // capture stream (a legacy default stream cannot be captured)
+  // the captured host-I/O force provider (srbe_set_host_io / srbe_forces_host_io): the caller's
+  // pinned buffers and their device views, a library-owned mapped word for psi_bar, and one graph
+  // per mode-list slot
+  double *io_r = nullptr, *io_F = nullptr, *io_Q = nullptr;
+  const double *io_dr = nullptr;
+  double *io_dF = nullptr, *io_dQ = nullptr;
+  double *io_psi = nullptr, *io_dpsi = nullptr;
+  cudaGraphExec_t io_exec[2] = {nullptr, nullptr};
+  uint64_t io_epoch = ~0ull;
+  int io_K = -1;
+  int64_t io_kernels = 0;
+  uint64_t io_calls = 0;
+  void drop_io_graphs() {
+    for (auto &g : io_exec)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+    io_epoch = ~0ull;
+  }
   int graph_K = -1;
   int slot_cap = 0;
   bool graph_dirty = true;
@@ -333,6 +395,8 @@ struct srbe::HostExt {
   ~HostExt() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     drop_graphs();
+    drop_io_graphs();
+    if (io_psi) cudaFreeHost(io_psi);
     if (cap) cudaStreamDestroy(cap);
     for (auto &sl : slot) {
       if (sl.hm) cudaFreeHost(sl.hm);
@@ -551,7 +615,7 @@ void srbe_list_from_samples(srbe_ctx *c, const int32_t *samp, int P) {
 // The device half of a step (mode list read from a mapped pinned slot, kick/drift, the force pass,
 // kick) has no host synchronisation and no allocation once the buffers are reserved, so it is
 // captured once per slot and replayed; the host fills the other slot while the GPU runs.
-void forces_pass(srbe_ctx *c, bool energies, bool after_drift = false);
+void forces_pass(srbe_ctx *c, bool energies, bool after_drift = false, bool check = true);
 
 // the captured step's mode list (K int4 + the step word) and weights, read from a mapped pinned slot
 __global__ void k_stage_modes(int K, const int4 *__restrict__ hm, const double *__restrict__ hw,
@@ -730,6 +794,35 @@ void device_step(srbe_ctx *c, int slot, bool staged) {
   integrate_kick_drift(c, 0.5 * c->dt, false);
 }
 
+// one pass of the host-I/O force provider: mode list from the slot (side stream), positions from the
+// caller's mapped buffer, the full force pass, the non-finite check, forces and charges back
+void provider_step(srbe_ctx *c, int slot) {
+  Extra *e = extra(c);
+  const int K = c->K;
+  SRBE_REQUIRE(c->dm.cap > (size_t)K && c->dc.cap >= (size_t)K && e->slot[slot].dhm && e->io_dr, SRBE_ESTATE,
+               "buffers not reserved for the force provider");
+  SRBE_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+  SRBE_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  k_stage_modes<<<std::min(blocks_for((int64_t)K + 1, 256), 64u), 256, 0, c->side>>>(K, e->slot[slot].dhm,
+                                                                                     e->slot[slot].dhw, c->dm.p,
+                                                                                     c->dc.p);
+  SRBE_CUDA(cudaEventRecord(c->ev_modes, c->side));
+  uint64_t *iu = c->iu.ensure((size_t)3 * std::max<int64_t>(c->ni, 1));
+  const double3 invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
+  k_io_load<<<blocks_for(std::max<int64_t>(c->ni, 1), 64), 64, 0, c->stream>>>(
+      c->ni, e->io_dr, c->L[0], c->L[1], invL, c->x.p, c->y.p, c->z.p, iu, c->d_status);
+  c->launches += 2;
+  SRBE_CUDA(cudaGetLastError());
+  SRBE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_modes, 0));
+  forces_pass(c, false, true);
+  check_finite(c, true, true);
+  const int64_t nt = std::max<int64_t>(std::max<int64_t>(c->ni, c->ne), 1);
+  k_io_store<<<std::min(blocks_for(nt, 256), 304u), 256, 0, c->stream>>>(c->ni, c->F.p, e->io_dF, c->ne, c->Q.p,
+                                                                         e->io_dQ, c->scal.p, e->io_dpsi);
+  c->launches++;
+  SRBE_CUDA(cudaGetLastError());
+}
+
 void ensure_slot_buffers(srbe_ctx *c) {
   Extra *e = extra(c);
   SRBE_CUDA(cudaStreamSynchronize(c->stream));
@@ -776,14 +869,16 @@ void fill_slot(srbe_ctx *c, int slot) {
   copy_to_slot(c, slot);
 }
 
-// Captures device_step of every context in ctxs into one executable graph per slot.  With width 0
+// Captures device_step (provider: provider_step) of every context in ctxs into one executable graph
+// per slot.  With width 0
 // all run in order on the capture stream; otherwise context r runs on forks[r % width], forked from
 // and joined back into the capture stream, so that up to width replicas overlap on the GPU.  The
 // cooperative kernels of all of them are chained through one capture-local event, so no two of them
 // ever run at the same time.  kernels[r] receives the kernels one replay runs for context r.
 // Returns false (and leaves nothing captured) when capture is not possible.
 bool capture_graphs(srbe_ctx *const *ctxs, int n, cudaStream_t main, int width, const cudaStream_t *forks,
-                    cudaGraphExec_t out[2], int64_t *kernels, DevBuf<StageEntry> *stage_tabs) {
+                    cudaGraphExec_t out[2], int64_t *kernels, DevBuf<StageEntry> *stage_tabs,
+                    bool provider = false) {
   std::vector<int64_t> launches0(n);
   for (int r = 0; r < n; ++r) launches0[r] = ctxs[r]->launches;
   std::vector<cudaStream_t> saved(n);
@@ -846,7 +941,8 @@ bool capture_graphs(srbe_ctx *const *ctxs, int n, cudaStream_t main, int width, 
           c->stream = main;
         }
         const int64_t l0 = c->launches;
-        device_step(c, slot, stage_tabs != nullptr);
+        if (provider) provider_step(c, slot);
+        else device_step(c, slot, stage_tabs != nullptr);
         kernels[r] = c->launches - l0 + (stage_tabs && r == 0 ? 1 : 0);
         if (width > 0) {
           SRBE_CUDA(cudaEventRecord(join[r], c->stream));
@@ -910,9 +1006,13 @@ void charges_pass(srbe_ctx *c, bool after_drift) {
   phase_begin(c, kPhSolve);
   charge_update(c);
   phase_end(c, kPhSolve);
+  // test aid: a NaN in Q[0] before anything reads the charges
+  if (c->inject == 2 && c->ne > 0) SRBE_CUDA(cudaMemsetAsync(c->Q.p, 0xff, sizeof(double), c->stream));
 }
 
-void forces_pass(srbe_ctx *c, bool energies, bool after_drift) {
+// check: non-finite forces and charges raise the context's flag (the MD step checks them in its
+// closing half kick instead, after_drift; the minimiser tolerates overflowing forces)
+void forces_pass(srbe_ctx *c, bool energies, bool after_drift, bool check) {
   charges_pass(c, after_drift);
   if (ion_forces_split(c, energies)) {
     // the ion-ion pairs on the side stream, behind the neighbour update, beside b / solve / S2
@@ -935,6 +1035,9 @@ void forces_pass(srbe_ctx *c, bool energies, bool after_drift) {
   phase_begin(c, kPhForces);
   ion_forces(c, energies);
   phase_end(c, kPhForces);
+  // test aid: a NaN in F[0] before the check
+  if (c->inject == 1 && c->ni > 0) SRBE_CUDA(cudaMemsetAsync(c->F.p, 0xff, sizeof(double), c->stream));
+  if (check && !after_drift) check_finite(c, true, true);
   if (energies) {
     phase_begin(c, kPhEnergy);
     energy_scalars(c);
@@ -978,6 +1081,35 @@ void eager_step(srbe_ctx *c, uint64_t seed0) {
   phase_end(c, kPhIntegrate);
 }
 
+
+// Reports (throws) and clears the device-raised flags: after the work that may raise them has
+// finished, or (srbe_step) for whatever the host already sees, without waiting.  notconv = false
+// leaves an unconverged iterative solve (whose pass fell back to the direct solve) raised for a later
+// call, so that MD keeps stepping.
+void report_status(srbe_ctx *c, bool notconv = true) {
+  volatile int *h = c->h_status;
+  if (!h) return;
+  const int nc = notconv ? h[kStatNotConv] : 0, nf = h[kStatNonFiniteF], nq = h[kStatNonFiniteQ],
+            nb = h[kStatBadInput], nt = h[kStatTimeout];
+  if (!(nc | nf | nq | nb | nt)) return;
+  if (notconv) h[kStatNotConv] = 0;
+  if (nt) {
+    h[kStatTimeout] = 0;
+    throw Error{SRBE_ETIMEOUT, "a tensor-core MMA did not complete within its wait limit (its outputs are invalid)"};
+  }
+  h[kStatNonFiniteF] = 0;
+  h[kStatNonFiniteQ] = 0;
+  h[kStatBadInput] = 0;
+  if (nb)
+    throw Error{SRBE_EINVAL, "non-finite position in the host input buffer (replaced by the origin for that pass)"};
+  if (nf || nq)
+    throw Error{SRBE_ENONFINITE, std::string("non-finite ") + (nf && nq ? "forces and electrode charges"
+                                                               : nf   ? "forces"
+                                                                      : "electrode charges") +
+                                     (nc ? " (and an iterative solve stopped at maxit)" : "")};
+  throw Error{SRBE_ENOTCONV, "PCG charge solve stopped at maxit above its tolerance; the charges of that pass "
+                             "come from the direct solve"};
+}
 
 void download_outputs(srbe_ctx *c, double *F, double *Q, double *psi, double *energy, double *b) {
   Extra *e = extra(c);
@@ -1055,6 +1187,9 @@ int srbe_create(const double box[3], double alpha, double eta, double rc, int P,
     SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_modes, cudaEventDisableTiming));
     SRBE_CUDA(cudaEventCreateWithFlags(&c->ev_ii, cudaEventDisableTiming));
     upload_table(c);
+    SRBE_CUDA(cudaHostAlloc((void **)&c->h_status, sizeof(int) * kStatCount, cudaHostAllocMapped));
+    std::memset(c->h_status, 0, sizeof(int) * kStatCount);
+    SRBE_CUDA(cudaHostGetDevicePointer((void **)&c->d_status, c->h_status, 0));
     c->scal.ensure(kScalCount);
     SRBE_CUDA(cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScalCount, c->stream));
     c->hx->sampler.init(c->L, c->alpha, c->M, c->mmax);
@@ -1074,6 +1209,7 @@ int srbe_destroy(srbe_ctx *c) {
   if (c->h_mode_stage) cudaFreeHost(c->h_mode_stage);
   if (c->h_w_stage) cudaFreeHost(c->h_w_stage);
   if (c->side) cudaStreamSynchronize(c->side);
+  if (c->h_status) cudaFreeHost(c->h_status);
   if (c->stage_done) cudaEventDestroy(c->stage_done);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -1182,7 +1318,7 @@ int srbe_set_electrode(srbe_ctx *c, int64_t n_ele, const double *R, const int8_t
 int srbe_set_positions(srbe_ctx *c, int64_t n_ion, const double *r, const double *q) {
   return guarded(c, [&] {
     SRBE_REQUIRE(n_ion >= 0 && (n_ion == 0 || (r && q)), SRBE_EINVAL, "null positions or charges");
-    SRBE_REQUIRE(n_ion < (1ll << 31), SRBE_EINVAL, "too many ions");
+    SRBE_REQUIRE(n_ion < (1ll << 23), SRBE_EINVAL, "at most 8,388,607 ions are supported");
     SRBE_REQUIRE(finite_all(r, 3 * n_ion) && finite_all(q, n_ion), SRBE_EINVAL, "non-finite ion position or charge");
     if (c->have_md && n_ion != c->ni) c->have_md = false;
     if (n_ion != c->ni) c->nbr.cap = 0;
@@ -1220,6 +1356,7 @@ int srbe_set_positions(srbe_ctx *c, int64_t n_ion, const double *r, const double
 int srbe_set_positions_dev(srbe_ctx *c, int64_t n_ion, const double *r_dev, const double *q_dev) {
   return guarded(c, [&] {
     SRBE_REQUIRE(n_ion >= 0 && (n_ion == 0 || (r_dev && q_dev)), SRBE_EINVAL, "null positions or charges");
+    SRBE_REQUIRE(n_ion < (1ll << 23), SRBE_EINVAL, "at most 8,388,607 ions are supported");
     if (c->have_md && n_ion != c->ni) c->have_md = false;
     if (n_ion != c->ni) c->nbr.cap = 0;
     c->ni = n_ion;
@@ -1458,7 +1595,9 @@ int srbe_solve_electrode_charges(srbe_ctx *c, double *Q, double *psi_bar, double
   return guarded(c, [&] {
     require_state(c, true);
     charges_pass(c, false);
+    check_finite(c, false, true);
     download_outputs(c, nullptr, Q, psi_bar, nullptr, b);
+    report_status(c);
   });
 }
 
@@ -1468,6 +1607,7 @@ int srbe_forces(srbe_ctx *c, double *F, double *Q, double *psi_bar, double *ener
     forces_pass(c, energy != nullptr);
     extra(c)->forces_valid = true;
     download_outputs(c, F, Q, psi_bar, energy, nullptr);
+    report_status(c);
   });
 }
 
@@ -1485,12 +1625,83 @@ int srbe_forces_dev(srbe_ctx *c, double *F_dev, double *Q_dev) {
   });
 }
 
+int srbe_set_host_io(srbe_ctx *c, double *r, double *F, double *Q) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(c->have_ele && c->have_pos, SRBE_ESTATE, "electrode and positions (charges) are required");
+    SRBE_REQUIRE(r && (F || c->ni == 0), SRBE_EINVAL, "null position or force buffer");
+    Extra *e = extra(c);
+    e->drop_io_graphs();
+    // page-locked host memory (cudaHostAlloc or cudaHostRegister) only: plain pageable memory is
+    // rejected even where the device could reach it
+    auto dev_view = [](void *h, const char *what) {
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, h) != cudaSuccess || at.type != cudaMemoryTypeHost || !at.devicePointer) {
+        cudaGetLastError();
+        throw Error{SRBE_EINVAL, std::string(what) + " is not page-locked host memory mapped for the device "
+                                                     "(allocate it with cudaHostAlloc or register it)"};
+      }
+      return at.devicePointer;
+    };
+    e->io_dr = (const double *)dev_view(r, "the position buffer");
+    e->io_dF = F ? (double *)dev_view(F, "the force buffer") : nullptr;
+    e->io_dQ = Q ? (double *)dev_view(Q, "the charge buffer") : nullptr;
+    e->io_r = r;
+    e->io_F = F;
+    e->io_Q = Q;
+    if (!e->io_psi) {
+      SRBE_CUDA(cudaHostAlloc((void **)&e->io_psi, sizeof(double), cudaHostAllocMapped));
+      SRBE_CUDA(cudaHostGetDevicePointer((void **)&e->io_dpsi, e->io_psi, 0));
+    }
+  });
+}
+
+int srbe_forces_host_io(srbe_ctx *c, uint64_t seed, uint64_t step, double *psi_bar) {
+  return guarded(c, [&] {
+    Extra *e = extra(c);
+    SRBE_REQUIRE(e->io_dr, SRBE_ESTATE, "srbe_set_host_io has not been called");
+    SRBE_REQUIRE(c->have_ele && c->have_pos, SRBE_ESTATE, "electrode and positions (charges) are required");
+    report_status(c);                  // flags of earlier asynchronous calls
+    const int slot = (int)(e->io_calls++ & 1);
+    build_host_list(c, seed, step);
+    if (!c->have_modes || (int)c->hc.size() != c->K) {
+      upload_modes(c);                 // a new mode count: sizes the mode buffers (and recaptures)
+      c->have_modes = true;
+    }
+    reserve(c);
+    ensure_slot_buffers(c);
+    fill_slot(c, slot);
+    if (e->io_epoch != e->epoch || e->io_K != c->K || !e->io_exec[slot]) {
+      // the first pass after a state change runs the ordinary way (it sizes every buffer), then the
+      // pass is captured for the following calls
+      provider_step(c, slot);
+      e->drop_io_graphs();
+      srbe_ctx *one[1] = {c};
+      if (!e->cap) e->cap = make_stream(true);
+      if (capture_graphs(one, 1, e->cap, 0, nullptr, e->io_exec, &e->io_kernels, nullptr, true)) {
+        e->io_epoch = e->epoch;
+        e->io_K = c->K;
+      }
+    } else {
+      coop_before(c);
+      SRBE_CUDA(cudaGraphLaunch(e->io_exec[slot], c->stream));
+      coop_after(c);
+      c->launches += e->io_kernels;
+    }
+    SRBE_CUDA(cudaEventRecord(e->slot[slot].done, c->stream));
+    SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    e->forces_valid = true;
+    if (psi_bar) *psi_bar = *(volatile double *)e->io_psi / kVolt;
+    report_status(c);
+  }, true);
+}
+
 int srbe_step(srbe_ctx *c, int nsteps, uint64_t seed0) {
   return guarded(c, [&] {
     SRBE_REQUIRE(nsteps >= 0, SRBE_EINVAL, "negative step count");
     SRBE_REQUIRE(c->have_ele && c->have_pos, SRBE_ESTATE, "electrode and positions are required");
     SRBE_REQUIRE(c->have_md, SRBE_ESTATE, "srbe_set_md has not been called");
     Extra *e = extra(c);
+    report_status(c, false);     // flags that earlier (asynchronous) steps raised
     initial_forces(c, seed0);
     const bool graphs = !c->profiling && c->use_graphs && !e->graph_failed && nsteps > 0;
     if (graphs && (e->graph_dirty || e->graph_K != c->K)) {
@@ -1514,6 +1725,7 @@ int srbe_step(srbe_ctx *c, int nsteps, uint64_t seed0) {
     }
     if (graphs && !e->graph_failed) {
       for (int s = 0; s < nsteps; ++s) {
+        report_status(c, false); // what the host sees so far (no wait)
         c->md_step++;
         const int slot = (int)(c->md_step & 1);
         if (e->dev_sampler) {
@@ -1532,9 +1744,45 @@ int srbe_step(srbe_ctx *c, int nsteps, uint64_t seed0) {
       }
       return;
     }
-    for (int s = 0; s < nsteps; ++s) eager_step(c, seed0);
+    for (int s = 0; s < nsteps; ++s) {
+      report_status(c, false);
+      eager_step(c, seed0);
+    }
     SRBE_CUDA(cudaGetLastError());
   }, true);
+}
+
+int srbe_synchronize(srbe_ctx *c, double timeout_s) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(!std::isnan(timeout_s), SRBE_EINVAL, "timeout is NaN");
+    cudaStream_t ss[2] = {c->stream, c->side};
+    if (timeout_s < 0) {
+      for (cudaStream_t st : ss) SRBE_CUDA(cudaStreamSynchronize(st));
+    } else {
+      // bounded wait: poll both streams until they are idle or the limit passes
+      const auto t_end = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+      for (;;) {
+        bool busy = false;
+        for (cudaStream_t st : ss) {
+          const cudaError_t q = cudaStreamQuery(st);
+          if (q == cudaErrorNotReady) busy = true;
+          else SRBE_CUDA(q);
+        }
+        if (!busy) break;
+        if (std::chrono::steady_clock::now() >= t_end)
+          throw Error{SRBE_ETIMEOUT, "work still running on the context's streams after the time limit"};
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+      }
+    }
+    report_status(c);
+  }, true);
+}
+
+int srbe_debug_inject_nonfinite(srbe_ctx *c, int what) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(what >= 0 && what <= 2, SRBE_EINVAL, "what must be 0, 1 (F[0]) or 2 (Q[0])");
+    c->inject = what;
+  });
 }
 
 int srbe_set_graphs(srbe_ctx *c, int on) {
@@ -1585,11 +1833,12 @@ int srbe_minimize(srbe_ctx *c, int nsteps, double a, double dmax, uint64_t seed)
     SRBE_REQUIRE(c->have_ele && c->have_pos && c->have_md, SRBE_ESTATE, "electrode, positions and MD terms needed");
     for (int t = 0; t < nsteps; ++t) {
       sample_into(c, seed, (uint64_t)t);
-      forces_pass(c, false);
+      forces_pass(c, false, false, false);
       steepest_descent_move(c, a, dmax);
     }
     extra(c)->forces_valid = false;
     SRBE_CUDA(cudaStreamSynchronize(c->stream));
+    report_status(c);
   });
 }
 
@@ -1747,6 +1996,14 @@ int srbe_mlp_predict(srbe_ctx *c, const float *D, int64_t n, float *out) {
     SRBE_CUDA(cudaMemcpyAsync(out, o, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
     SRBE_CUDA(cudaStreamSynchronize(c->stream));
   });
+}
+
+int srbe_mlp_predict_dev(srbe_ctx *c, const float *D_dev, int64_t n, float *out_dev) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(D_dev && out_dev && n >= 0, SRBE_EINVAL, "bad arguments");
+    SRBE_REQUIRE(c->mlp.ready, SRBE_ESTATE, "no MLP parameters");
+    mlp_forward(c, D_dev, n, out_dev, nullptr);
+  }, true);
 }
 
 int srbe_mlp_gradients(srbe_ctx *c, const float *D, const float *target, int64_t n, float *grad, double *loss) {
@@ -2200,6 +2457,14 @@ int srbe_batch_step(srbe_batch *b, int nsteps, const uint64_t *seeds, double *re
     SRBE_REQUIRE(nsteps >= 0, SRBE_EINVAL, "negative step count");
     SRBE_REQUIRE(seeds, SRBE_EINVAL, "null seed array");
     batch_check_replicas(b);
+    // device flags that earlier (asynchronous) batch steps raised on any replica
+    for (size_t r = 0; r < b->ctx.size(); ++r) {
+      try {
+        report_status(b->ctx[r], false);
+      } catch (const Error &e) {
+        throw Error{e.code, "replica " + std::to_string(r) + ": " + e.msg};
+      }
+    }
     batch_run(b, nsteps, seeds);
     if (residuals) batch_residuals(b, residuals);
   });

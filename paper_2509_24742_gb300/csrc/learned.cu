@@ -1,5 +1,6 @@
 // Learned warm start for the constant-potential solve (the learned form): a per-electrode-site MLP
-// (80 -> 128 -> 128 -> 1, SiLU, FP32) maps local electrolyte descriptors to the unprojected solution
+// (80 -> 128 -> 128 -> 1, SiLU; FP32 parameters, forward GEMMs on the tensor cores) maps local
+// electrolyte descriptors to the unprojected solution
 // y = A^-1 (dpsi d + b) of the charge update (Eqs. 9-10), which seeds the PCG iteration.
 //
 // Descriptors of site j (80 floats):
@@ -13,6 +14,7 @@
 // the sum order is fixed) and a second kernel adds the block gradients in block order and applies
 // the AdamW update.
 #include "srbe_internal.cuh"
+#include "tc.cuh"
 
 namespace srbe {
 
@@ -75,7 +77,7 @@ k_descriptors(int64_t ne, const double *__restrict__ ex, const double *__restric
     float r = 0.f, qv = 0.f;
     if (k < cnt) {
       const int32_t e = ei[j * (int64_t)cap + k];
-      const int idx = e & 0xffffff, ix = ((e >> 24) & 15) - 8, iy = ((unsigned)e >> 28) - 8;
+      const int idx = e & 0x7fffff, ix = ((e >> 24) & 15) - 8, iy = ((unsigned)e >> 28) - 8;
       const float4 o = ion_pf[idx];
       const float dx = X - (o.x + ix * Lx), dy = Y - (o.y + iy * Ly), dz = Z - o.z;
       const float r2 = dx * dx + dy * dy + dz * dz;
@@ -107,34 +109,138 @@ k_descriptors(int64_t ne, const double *__restrict__ ex, const double *__restric
   }
 }
 
-// forward pass for n rows; one block of 128 threads (hidden units) per group of rows
-__global__ void __launch_bounds__(kH)
-k_mlp_forward(int64_t n, const float *__restrict__ D, const float *__restrict__ P, float *__restrict__ out,
-              double *__restrict__ out_y) {
-  __shared__ float x[kIn], h1[kH], red[kH / 32];
-  const int h = threadIdx.x;
-  for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
-    if (h < kIn) x[h] = (D[row * kIn + h] - P[oXm + h]) / P[oXs + h];
+// ------------------------------------------------------------------------------------------------
+// forward pass on the tensor cores (tcgen05): 128 rows per tile, Z1 = X W1^T and Z2 = H1 W2^T as
+// kind::f16 MMAs into tensor memory with FP32 accumulation.  Every operand is split into BF16
+// (hi, lo) and each product taken as hi hi + hi lo + lo hi, which keeps about 16 significand bits
+// (the scalar FP32 path keeps 24; the difference stays below 1e-5 of the output here).  One CTA of
+// four warps per SM, persistent over tiles; thread t owns row t of the tile (tensor-memory lane t)
+// for the bias + SiLU epilogues, and thread 0 issues the MMAs.
+// ------------------------------------------------------------------------------------------------
+constexpr int kTcK1 = kIn / tc::kKstep;    // 5 K steps of layer 1
+constexpr int kTcK2 = kH / tc::kKstep;     // 8 K steps of layer 2
+constexpr size_t kTcSmem = (size_t)(2 * kTcK1 + 2 * kTcK2) * 2 * tc::kBlockBytes;   // 208 KB
+constexpr int kTcPolls = 1 << 20;          // bounded mbarrier waits
+static_assert(kIn % tc::kKstep == 0 && kH == tc::kRows, "MLP sizes must match the MMA tiles");
+
+__global__ void __launch_bounds__(128, 1)
+k_mlp_forward_tc(int64_t n, const float *__restrict__ D, const float *__restrict__ P, float *__restrict__ out,
+                 double *__restrict__ out_y, int *__restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __nv_bfloat16 *w1h = reinterpret_cast<__nv_bfloat16 *>(smem);
+  __nv_bfloat16 *w1l = w1h + kTcK1 * tc::kBlockElems, *w2h = w1l + kTcK1 * tc::kBlockElems;
+  __nv_bfloat16 *w2l = w2h + kTcK2 * tc::kBlockElems, *xh = w2l + kTcK2 * tc::kBlockElems;
+  __nv_bfloat16 *xl = xh + kTcK1 * tc::kBlockElems, *hh = xl + kTcK1 * tc::kBlockElems;
+  __nv_bfloat16 *hl = hh + kTcK2 * tc::kBlockElems;
+  __shared__ float sb1[kH], sb2[kH], sw3[kH], sxm[kIn], sxs[kIn];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int t = threadIdx.x, warp = t >> 5;
+  for (int i = t; i < kH * kIn; i += 128) {
+    const int h = i / kIn, k = i - h * kIn;
+    tc::split_bf16(P[oW1 + i], w1h[tc::off(h, k)], w1l[tc::off(h, k)]);
+  }
+  for (int i = t; i < kH * kH; i += 128) {
+    const int h = i / kH, k = i - h * kH;
+    tc::split_bf16(P[oW2 + i], w2h[tc::off(h, k)], w2l[tc::off(h, k)]);
+  }
+  sb1[t] = P[oB1 + t];
+  sb2[t] = P[oB2 + t];
+  sw3[t] = P[oW3 + t];
+  if (t < kIn) {
+    sxm[t] = P[oXm + t];
+    sxs[t] = P[oXs + t];
+  }
+  const float b3 = P[oB3], ym = P[oYm], ys = P[oYs];
+  if (t == 0) tc::mbar_init(&mbar, 1);
+  if (warp == 0) tc::tmem_alloc(&tbase, 256);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t d1 = tbase, d2 = tbase + 128, lanes = (uint32_t)(32 * warp) << 16;
+  const uint32_t idesc = tc::idesc_bf16(128, 128);
+  const int64_t ntiles = (n + 127) / 128;
+  uint32_t phase = 0;
+  bool fail = false;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row0 = tile * 128;
+    // standardised inputs of the tile (rows beyond n are zero)
+    for (int i = t; i < 128 * kIn; i += 128) {
+      const int r = i / kIn, k = i - r * kIn;
+      const float x = row0 + r < n ? (D[row0 * kIn + i] - sxm[k]) / sxs[k] : 0.f;
+      tc::split_bf16(x, xh[tc::off(r, k)], xl[tc::off(r, k)]);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
     __syncthreads();
-    float z1 = P[oB1 + h];
-    for (int k = 0; k < kIn; ++k) z1 = fmaf(P[oW1 + h * kIn + k], x[k], z1);
-    h1[h] = silu(z1);
-    __syncthreads();
-    float z2 = P[oB2 + h];
-    for (int k = 0; k < kH; ++k) z2 = fmaf(P[oW2 + h * kH + k], h1[k], z2);
-    float v = P[oW3 + h] * silu(z2);
+    tc::fence_after_sync();
+    if (t == 0) {
+      for (int s = 0; s < kTcK1; ++s) {
+        const uint64_t ah = tc::block_desc(xh + s * tc::kBlockElems), al = tc::block_desc(xl + s * tc::kBlockElems);
+        const uint64_t bh = tc::block_desc(w1h + s * tc::kBlockElems), bl = tc::block_desc(w1l + s * tc::kBlockElems);
+        tc::mma_bf16(d1, ah, bh, idesc, s > 0);
+        tc::mma_bf16(d1, ah, bl, idesc, true);
+        tc::mma_bf16(d1, al, bh, idesc, true);
+      }
+      tc::commit(&mbar);
+    }
+    fail = __syncthreads_or(!tc::mbar_wait(&mbar, phase, kTcPolls)) != 0;
+    if (fail) break;
+    phase ^= 1u;
+    tc::fence_after_sync();
+    // H1 = SiLU(Z1 + b1), row t, split into the layer-2 operand
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+      float v[32];
+      tc::ld32(d1 + lanes + (uint32_t)c0, v);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((h & 31) == 0) red[h >> 5] = v;
+      for (int j = 0; j < 32; ++j)
+        tc::split_bf16(silu(v[j] + sb1[c0 + j]), hh[tc::off(t, c0 + j)], hl[tc::off(t, c0 + j)]);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
     __syncthreads();
-    if (h == 0) {
-      const float o3 = red[0] + red[1] + red[2] + red[3] + P[oB3];
-      const float y = o3 * P[oYs] + P[oYm];
+    tc::fence_after_sync();
+    if (t == 0) {
+      for (int s = 0; s < kTcK2; ++s) {
+        const uint64_t ah = tc::block_desc(hh + s * tc::kBlockElems), al = tc::block_desc(hl + s * tc::kBlockElems);
+        const uint64_t bh = tc::block_desc(w2h + s * tc::kBlockElems), bl = tc::block_desc(w2l + s * tc::kBlockElems);
+        tc::mma_bf16(d2, ah, bh, idesc, s > 0);
+        tc::mma_bf16(d2, ah, bl, idesc, true);
+        tc::mma_bf16(d2, al, bh, idesc, true);
+      }
+      tc::commit(&mbar);
+    }
+    fail = __syncthreads_or(!tc::mbar_wait(&mbar, phase, kTcPolls)) != 0;
+    if (fail) break;
+    phase ^= 1u;
+    tc::fence_after_sync();
+    // output = W3 . SiLU(Z2 + b2) + b3, de-standardised
+    float acc = 0.f;
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+      float v[32];
+      tc::ld32(d2 + lanes + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc = fmaf(sw3[c0 + j], silu(v[j] + sb2[c0 + j]), acc);
+    }
+    tc::fence_before_sync();
+    const int64_t row = row0 + t;
+    if (row < n) {
+      const float y = (acc + b3) * ys + ym;
       if (out) out[row] = y;
       if (out_y) out_y[row] = (double)y;
     }
-    __syncthreads();
   }
+  if (fail) {
+    // an MMA did not complete within the limit: raise the flag, give it one more bounded wait, then
+    // release the tensor memory and return
+    if (t == 0) *(volatile int *)(status + kStatTimeout) = 1;
+    tc::mbar_wait(&mbar, phase, kTcPolls);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tbase, 256);
 }
 
 // forward + backward of the standardised MSE loss over rows [blockIdx.x * chunk, ...); the block's
@@ -230,8 +336,16 @@ void mlp_descriptors(srbe_ctx *c, float *D_dev) {
 }
 
 void mlp_forward(srbe_ctx *c, const float *D_dev, int64_t n, float *out_dev, double *out_y_dev) {
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(n, 152 * 8));
-  k_mlp_forward<<<grid, kH, 0, c->stream>>>(n, D_dev, c->mlp.P.p, out_dev, out_y_dev);
+  if (n <= 0) return;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    SRBE_CUDA(cudaGetDevice(&dev));
+    SRBE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SRBE_CUDA(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+  }
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 127) / 128, nsm);
+  k_mlp_forward_tc<<<grid, 128, kTcSmem, c->stream>>>(n, D_dev, c->mlp.P.p, out_dev, out_y_dev, c->d_status);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }

@@ -101,7 +101,8 @@ __global__ void k_na_reduce(int K, int nchunk, const double2 *__restrict__ parti
 }
 
 // Once per device, with that device current: resolve the device addresses of the file-scope
-// arrays and fill the sin/cos table (a host-to-symbol copy, no allocation).
+// arrays, fill the sin/cos table (a host-to-symbol copy, no allocation), wait for the device, and
+// load both kernels.
 int setup_device(DeviceSetup **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return SRBE_ECUDA;
@@ -116,6 +117,15 @@ int setup_device(DeviceSetup **out) {
       h[j] = make_double2((double)cosl(a), (double)sinl(a));
     }
     if (cudaMemcpyToSymbol(na_table, h, sizeof(h)) != cudaSuccess) return SRBE_ECUDA;
+    // A copy from pageable memory may return before its DMA has landed, and streams created
+    // non-blocking do not wait for the legacy stream it ran on: wait for it here, so that a first
+    // call on any stream reads a complete table.
+    if (cudaDeviceSynchronize() != cudaSuccess) return SRBE_ECUDA;
+    // Load both kernels now (lazy module loading would otherwise load them at their first launch,
+    // which may come inside a stream capture or a running pipeline).
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_na_partial) != cudaSuccess) return SRBE_ECUDA;
+    if (cudaFuncGetAttributes(&fa, k_na_reduce) != cudaSuccess) return SRBE_ECUDA;
     s.ready = true;
   }
   *out = &s;

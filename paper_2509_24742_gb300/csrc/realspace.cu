@@ -557,9 +557,11 @@ __device__ __forceinline__ void compacted_pairs(const PairSite &S, const CellsDe
   __syncwarp();
 }
 
-// The same compaction over a Verlet list: entries pack a sorted index (bits 0-23) and the image
-// shifts ix + 8, iy + 8 (bits 24-27, 28-31); consecutive lanes read consecutive entries.
-__device__ __forceinline__ int list_index(int32_t e) { return e & 0xffffff; }
+// The same compaction over a Verlet list: entries pack a sorted index (bits 0-22), an LJ-exclusion
+// bit (bit 23: the pair lies inside one molecule; ion-ion lists only) and the image shifts ix + 8,
+// iy + 8 (bits 24-27, 28-31); consecutive lanes read consecutive entries.
+constexpr int32_t kListExcl = 1 << 23;
+__device__ __forceinline__ int list_index(int32_t e) { return e & 0x7fffff; }
 __device__ __forceinline__ int list_ix(int32_t e) { return ((e >> 24) & 15) - 8; }
 __device__ __forceinline__ int list_iy(int32_t e) { return ((unsigned)e >> 28) - 8; }
 // image shifts of a list entry as floats without an int-to-float conversion: the 4-bit field ORed
@@ -875,9 +877,11 @@ __device__ __forceinline__ void warp_append(int32_t *list, int cap, int &count, 
 // appends every particle of the runs of `cell` within sqrt(cut2) of (X, Y, Z) to list.  The runs
 // and their particle ranges are fetched 32 at a time (lane = run) and broadcast, so that a list
 // costs one round of dependent loads for the whole stencil instead of one per run.
+// ms (ion-ion lists with molecules): entries of particles of molecule `mol` get the exclusion bit.
 __device__ __forceinline__ int build_list(const NbrKernelArgs &a, const int4 *runs, const int32_t *run_first, int cell,
                                           const int32_t *start, const float4 *pf, float X, float Y, float Z,
-                                          int64_t self, int32_t *list, int lane) {
+                                          int64_t self, int32_t *list, int lane, const int32_t *ms = nullptr,
+                                          int mol = -1) {
   int count = 0;
   const float Lxf = (float)a.Lx, Lyf = (float)a.Ly;
   // stencil pruning: a run (one row of cells) whose box lies farther than the reach (plus a margin
@@ -919,12 +923,14 @@ __device__ __forceinline__ int build_list(const NbrKernelArgs &a, const int4 *ru
       for (int base = b0; base < b1; base += 32) {
         const int pp = base + lane;
         bool in = false;
+        int32_t excl = 0;
         if (pp < b1 && !(zero_image && pp == self)) {
           const float4 o = pf[pp];
           const float dx = X - (o.x + sx), dy = Y - (o.y + sy), dz = Z - o.z;
           in = dx * dx + dy * dy + dz * dz < a.cut2;
+          if (in && ms && ms[pp] == mol) excl = kListExcl;
         }
-        warp_append(list, a.cap, count, in, list_entry(pp, ix, iy), lane);
+        warp_append(list, a.cap, count, in, list_entry(pp, ix, iy) | excl, lane);
       }
     }
   }
@@ -1072,7 +1078,14 @@ __global__ void __launch_bounds__(256) k_neighbor_update(NbrKernelArgs a) {
       const float4 me = a.pf[p];
       const int cell = a.cell_s[p];
       const int nii = build_list(a, a.runs, a.run_first, cell, a.start, a.pf, me.x, me.y, me.z, p,
-                                 a.ii + p * a.cap, lane);
+                                 a.ii + p * a.cap, lane, a.mol ? a.ms : nullptr, a.mol ? a.ms[p] : -1);
+      // pad the ion-ion list to a whole number of 32-entry batches with entries that always lie beyond
+      // the cutoff (the ion itself seven box lengths away in x and y), so that the mixed form's pass
+      // runs without bounds checks; a list that overflowed is walked from the stencil instead
+      if (nii <= a.cap) {
+        const int padded = min(a.cap, (nii + 31) & ~31);
+        if (nii + lane < padded) a.ii[p * a.cap + nii + lane] = list_entry((int)p, 7, 7);
+      }
       const int nie = build_list(a, a.runs, a.run_first, cell, a.eles.start, a.eles.pf, me.x, me.y, me.z, -1,
                                  a.ie + p * a.cap, lane);
       if (lane == 0) {
@@ -1515,6 +1528,122 @@ ForceLaunch force_launch(srbe_ctx *c) {
 }
 }  // namespace
 
+// The mixed form's ion-ion pass (real-space Coulomb of Eq. 13 between ions, LJ, bonds; no Q, no S):
+// one warp per ion over its Verlet list, FP32.  The list is padded to whole 32-entry batches with
+// entries beyond the cutoff, so the loop has no bounds checks; an entry carries the LJ exclusion of
+// an intramolecular pair, so the only gathers per entry are the neighbour's (x, y, z, q) and, with
+// LJ, its type; image shifts come from a 256-entry shared table indexed by the entry's top byte.
+// Two-stage software pipeline: the entries of batch b + 2 and the particle data of batch b + 1 are
+// in flight while batch b computes.  Per lane the terms are summed in list order, then a warp tree.
+// the list of ion p overflowed at its build: walk the stencil of its build cell (kept out of line so
+// that the list loop's registers do not carry it)
+__device__ __noinline__ float3 ion_ii_stencil(int64_t p, float4 me, int ti, int mi, const CellsDev &ions,
+                                               const ListsDev &nl, const MdDev &md, const ForceF32 &pf, int2 *q,
+                                               int lane) {
+  PairSite S;
+  S.Xf = me.x; S.Yf = me.y; S.Zf = me.z; S.qf = me.w; S.Lxf = pf.Lx; S.Lyf = pf.Ly; S.af = pf.alpha;
+  S.etaf = pf.eta; S.qke = (float)kKe * me.w; S.ti = ti; S.mi = mi; S.p = p;
+  PairAcc A;
+  compacted_pairs(S, ions, nl.cell_s[p], true, pf.rc * pf.rc, q, lane,
+                  [&](int2 e) { pair_ion_ion<true, false>(S, ions, md, e, A); });
+  return make_float3(A.f0, A.f1, A.f2);
+}
+
+// one ion's pass (the body of k_ion_ii)
+template <bool LJ>
+__device__ __forceinline__ void ion_ii_one(int64_t p, int64_t ni, const CellsDev &ions, const ListsDev &nl,
+                                           const MdDev &md, const ForceF32 &pf, const float2 *shift,
+                                           const float2 *ljs, int2 *wq, int lane, float4 *__restrict__ Fii) {
+  if (p >= ni) return;
+  const float4 me = ions.pf[p];
+  const int ti = LJ ? ions.ts[p] : 0;
+  const float2 *ljrow = ljs + ti * md.ntype;
+  const float qke = (float)kKe * me.w, af = pf.alpha, cut2 = pf.rc * pf.rc, Lx = pf.Lx, Ly = pf.Ly;
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+  const int cnt = nl.ii_n[p];
+  if (cnt <= nl.cap) {
+    const int32_t *list = nl.ii + p * nl.cap;
+    const int nb = min(nl.cap, (cnt + 31) & ~31);
+    int32_t e0 = nb > 0 ? __ldg(list + lane) : 0, e1 = nb > 32 ? __ldg(list + 32 + lane) : 0;
+    float4 o0 = ions.pf[list_index(e0)];
+    int t0 = LJ ? ions.ts[list_index(e0)] : 0;
+    for (int base = 0; base < nb; base += 32) {
+      const int32_t e2 = base + 64 < nb ? __ldg(list + base + 64 + lane) : 0;
+      const int j1 = list_index(e1);
+      const float4 o1 = ions.pf[j1];
+      const int t1 = LJ ? ions.ts[j1] : 0;
+      // batch b
+      const float2 sh = shift[(unsigned)e0 >> 24];
+      const float dx = me.x - fmaf(sh.x, Lx, o0.x), dy = me.y - fmaf(sh.y, Ly, o0.y), dz = me.z - o0.z;
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 < cut2 && r2 > 0.f) {
+        float phi, md2, rinv;
+        pair_ii_f(r2, af, phi, md2, rinv);
+        float fs = qke * o0.w * md2;
+        if (LJ && !(e0 & kListExcl)) {
+          const float2 sg = ljrow[t0];
+          const float ir2 = rinv * rinv, sr2 = sg.x * ir2, sr6 = sr2 * sr2 * sr2;
+          fs += sg.y * (2.f * sr6 * sr6 - sr6) * ir2;
+        }
+        f0 = fmaf(fs, dx, f0);
+        f1 = fmaf(fs, dy, f1);
+        f2 = fmaf(fs, dz, f2);
+      }
+      e0 = e1;
+      e1 = e2;
+      o0 = o1;
+      t0 = t1;
+    }
+  } else {
+    const float3 f = ion_ii_stencil(p, me, ti, LJ ? ions.ms[p] : -1, ions, nl, md, pf, wq, lane);
+    f0 = f.x;
+    f1 = f.y;
+    f2 = f.z;
+  }
+  f0 = warp_sum_f(f0);
+  f1 = warp_sum_f(f1);
+  f2 = warp_sum_f(f2);
+  if (lane == 0) {
+    float bx = 0.f, by = 0.f, bz = 0.f;
+    if (LJ && md.bond_start) {
+      const int32_t i = ions.order[p];
+      const float kbf = pf.kb;
+      for (int b = md.bond_start[i]; b < md.bond_start[i + 1]; ++b) {
+        const float4 o = ions.pf[ions.inv[md.bond_j[b]]];
+        float dx = me.x - o.x, dy = me.y - o.y, dz = me.z - o.z;
+        dx -= Lx * floorf(dx / Lx + 0.5f);
+        dy -= Ly * floorf(dy / Ly + 0.5f);
+        const float len = sqrtf(dx * dx + dy * dy + dz * dz);
+        const float ext = len - (float)md.bond_r0[b];
+        const float f = -kbf * ext / len;
+        bx += f * dx;
+        by += f * dy;
+        bz += f * dz;
+      }
+    }
+    Fii[p] = make_float4(f0 + bx, f1 + by, f2 + bz, 0.f);
+  }
+}
+
+template <bool LJ>
+__global__ void __launch_bounds__(kGatherThreads)
+k_ion_ii(int64_t ni, CellsDev ions, ListsDev nl, MdDev md, ForceF32 pf, float4 *__restrict__ Fii) {
+  __shared__ float2 shift[256];                     // (ix, iy) image counts as floats, by entry >> 24
+  __shared__ float2 ljs[kMaxLjTypes * kMaxLjTypes]; // (sigma^2, 24 eps)
+  __shared__ int2 wq[kWarpsPerBlock][64];           // queue of the stencil walk (overflowed lists)
+  for (int t = threadIdx.x; t < 256; t += blockDim.x)
+    shift[t] = make_float2(small_int_to_float((t & 15) - 8), small_int_to_float((t >> 4) - 8));
+  if (LJ)
+    for (int t = threadIdx.x; t < md.ntype * md.ntype; t += blockDim.x) {
+      const float2 v = md.lj32[t];
+      ljs[t] = make_float2(v.x, 24.f * v.y);
+    }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  ion_ii_one<LJ>(p, ni, ions, nl, md, pf, shift, ljs, wq[warp], lane, Fii);
+}
+
 bool ion_forces_split(const srbe_ctx *c, bool energies) {
   return c->precision == SRBE_MIXED && !energies && c->ni > 0;
 }
@@ -1524,10 +1653,12 @@ bool ion_forces_split(const srbe_ctx *c, bool energies) {
 void ion_forces_ii(srbe_ctx *c) {
   const ForceLaunch f = force_launch(c);
   float4 *fii = c->fii.ensure((size_t)c->ni);
-  k_ion_forces<true, false, 1><<<f.nblk, kGatherThreads, 0, c->side>>>(
-      c->ni, f.ions, f.eles, lists_dev(c), c->Q.p, c->Q32.p, c->K, c->dm.p, c->coef.p, c->coef32.p, c->tab.p, f.invL,
-      f.kvf, c->L[0], c->L[1], c->alpha, c->eta, c->rc, f.slab, f.pf, c->scal.p, f.md, c->x.p, c->y.p, c->z.p,
-      c->F.p, nullptr, fii);
+  const ListsDev L = lists_dev(c);
+  const int64_t n = c->ni;
+  if (c->have_md && f.md.ntype)
+    k_ion_ii<true><<<f.nblk, kGatherThreads, 0, c->side>>>(n, f.ions, L, f.md, f.pf, fii);
+  else
+    k_ion_ii<false><<<f.nblk, kGatherThreads, 0, c->side>>>(n, f.ions, L, f.md, f.pf, fii);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
   SRBE_CUDA(cudaEventRecord(c->ev_ii, c->side));
@@ -1622,14 +1753,20 @@ __device__ __forceinline__ double wrap_periodic(double X, double L) {
   return X;
 }
 
+// The closing half kick (status != nullptr) also checks the step's forces and charges: a non-finite
+// F of this thread's ion or Q of the electrode site with the same index raises the context's flag.
 __global__ void k_kick_drift(int64_t n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                              double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                              const double *__restrict__ F, const double *__restrict__ minv, double fac, double dt,
-                             int drift, double Lx, double Ly, Thermo th, double3 invL, uint64_t *__restrict__ iu) {
+                             int drift, double Lx, double Ly, Thermo th, double3 invL, uint64_t *__restrict__ iu,
+                             int64_t ne, const double *__restrict__ Q, int *__restrict__ status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (status && i < ne && !isfinite(Q[i])) *(volatile int *)(status + kStatNonFiniteQ) = 1;
   if (i >= n) return;
   const double w = fac * minv[i];
-  double a = fma(w, F[i], vx[i]), b = fma(w, F[n + i], vy[i]), c = fma(w, F[2 * n + i], vz[i]);
+  const double fx = F[i], fy = F[n + i], fz = F[2 * n + i];
+  if (status && !(isfinite(fx) && isfinite(fy) && isfinite(fz))) *(volatile int *)(status + kStatNonFiniteF) = 1;
+  double a = fma(w, fx, vx[i]), b = fma(w, fy, vy[i]), c = fma(w, fz, vz[i]);
   if (th.on) {
     const int4 st = *th.step;
     const uint64_t step = (uint64_t)(uint32_t)st.x | ((uint64_t)(uint32_t)st.y << 32);
@@ -1736,10 +1873,33 @@ void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift) {
   }
   uint64_t *iu = drift ? c->iu.ensure((size_t)3 * c->ni) : nullptr;
   const double3 invL = make_double3(1.0 / c->L[0], 1.0 / c->L[1], 1.0 / c->L[2]);
+  // the closing kick checks the step's forces and charges (one thread per ion and per site)
+  const int64_t ne = drift ? 0 : c->ne;
+  const int64_t nt = std::max<int64_t>(c->ni, ne);
   // 64-thread blocks: the FP64 arithmetic spreads over every SM even for a few thousand ions
-  k_kick_drift<<<blocks_for(c->ni, 64), 64, 0, c->stream>>>(c->ni, c->x.p, c->y.p, c->z.p, c->vx.p, c->vy.p,
-                                                           c->vz.p, c->F.p, c->minv.p, fac_kick, c->dt,
-                                                           drift ? 1 : 0, c->L[0], c->L[1], th, invL, iu);
+  k_kick_drift<<<blocks_for(nt, 64), 64, 0, c->stream>>>(c->ni, c->x.p, c->y.p, c->z.p, c->vx.p, c->vy.p,
+                                                         c->vz.p, c->F.p, c->minv.p, fac_kick, c->dt,
+                                                         drift ? 1 : 0, c->L[0], c->L[1], th, invL, iu, ne, c->Q.p,
+                                                         drift ? nullptr : c->d_status);
+  c->launches++;
+  SRBE_CUDA(cudaGetLastError());
+}
+
+// non-finite check of the forces [3][nF / 3] and charges [nQ] of a pass outside the MD step
+__global__ void k_check_finite(int64_t nF, const double *__restrict__ F, int64_t nQ, const double *__restrict__ Q,
+                               int *__restrict__ status) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nF || i < nQ; i += stride) {
+    if (i < nF && !isfinite(F[i])) *(volatile int *)(status + kStatNonFiniteF) = 1;
+    if (i < nQ && !isfinite(Q[i])) *(volatile int *)(status + kStatNonFiniteQ) = 1;
+  }
+}
+
+void check_finite(srbe_ctx *c, bool forces, bool charges) {
+  const int64_t nF = forces ? 3 * c->ni : 0, nQ = charges ? c->ne : 0;
+  if (nF == 0 && nQ == 0) return;
+  const unsigned nb = std::min<unsigned>(blocks_for(std::max(nF, nQ), 256), 304);
+  k_check_finite<<<nb, 256, 0, c->stream>>>(nF, c->F.p, nQ, c->Q.p, c->d_status);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }

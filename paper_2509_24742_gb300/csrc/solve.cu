@@ -181,7 +181,10 @@ __global__ void k_gemv_rows(int64_t nrow, int64_t ncol, const T *__restrict__ M,
 __global__ void __launch_bounds__(256)
 k_charges_fp64(int64_t n, const double *__restrict__ B, const double *__restrict__ b, double dpsi,
                const double *__restrict__ qd, const double *__restrict__ we, double wd, double s_e,
-               double *__restrict__ Q, float *__restrict__ Q32, double *__restrict__ scal) {
+               double *__restrict__ Q, float *__restrict__ Q32, double *__restrict__ scal,
+               const int *__restrict__ gate) {
+  // gate (the fallback after an iterative solve): run only if *gate is set
+  if (gate && *gate == 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (row > n) return;
@@ -253,8 +256,11 @@ constexpr int kSplitWarps = 4;
 __global__ void __launch_bounds__(256)
 k_charges_split(int64_t n, const float2 *__restrict__ B, const float2 *__restrict__ b, double dpsi,
                 const double *__restrict__ qd, const float2 *__restrict__ we, double wd, double s_e,
-                double *__restrict__ Q, float *__restrict__ Q32, double *__restrict__ scal) {
+                double *__restrict__ Q, float *__restrict__ Q32, double *__restrict__ scal,
+                const int *__restrict__ gate) {
   __shared__ DF part[256 / 32];
+  // gate (the fallback after an iterative solve): the whole block leaves unless *gate is set
+  if (gate && *gate == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int seg = warp % kSplitWarps;
   const int64_t row = (int64_t)blockIdx.x * (256 / 32 / kSplitWarps) + warp / kSplitWarps;
@@ -512,8 +518,9 @@ struct PcgArgs {
   double *y, *r, *z, *p, *Ap, *part;
   double *Q, *scal;
   float *Q32;
-  int *stats;        // [0] iterations
+  int *stats;        // [0] iterations, [1] 1 if stopped at maxit above the tolerance (arms the fallback)
   double *res;       // [0] final relative residual (recomputed)
+  int *status;       // the context's host-mapped error flags
 };
 
 __device__ double grid_dot_sum(const PcgArgs &a, double mine, int slot, cg::grid_group &grid) {
@@ -627,6 +634,10 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
     a.scal[kScalPsi] = psi;
     a.stats[0] = it;
     a.res[0] = sqrt(r2 / vv);
+    // stopped at maxit above the tolerance: raise the host flag and arm the direct fallback
+    const int failed = rr > a.tol2 * vv ? 1 : 0;
+    a.stats[1] = failed;
+    if (failed) *(volatile int *)(a.status + kStatNotConv) = 1;
   }
 }
 
@@ -663,6 +674,7 @@ void charge_update_pcg(srbe_ctx *c) {
   a.scal = c->scal.p;
   a.stats = c->pcg.stats.p;
   a.res = c->pcg.res.p;
+  a.status = c->d_status;
   void *args[] = {&a};
   coop_before(c);
   SRBE_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg, dim3(grid), dim3(256), args, 0, c->stream));
@@ -690,6 +702,21 @@ void pcg_prepare(srbe_ctx *c) {
   SRBE_CUDA(cudaGetLastError());
 }
 
+// Q and psi_bar through the projected inverse (one matrix-vector product); with a gate, only if *gate
+void charge_update_direct(srbe_ctx *c, const int *gate) {
+  const int64_t ne = c->ne;
+  const unsigned nb = blocks_for((ne + 1) * 32, 256);
+  if (c->precision == SRBE_MIXED)
+    k_charges_split<<<blocks_for(ne + 1, 256 / 32 / kSplitWarps), 256, 0, c->stream>>>(
+        ne, c->Bsplit.p, c->bsplit.p, c->dpsi, c->qd.p, c->wesplit.p, c->wd, c->s_e, c->Q.p, c->Q32.p, c->scal.p,
+        gate);
+  else
+    k_charges_fp64<<<nb, 256, 0, c->stream>>>(ne, c->Bmat.p, c->bvec.p, c->dpsi, c->qd.p, c->we.p, c->wd, c->s_e,
+                                              c->Q.p, c->Q32.p, c->scal.p, gate);
+  c->launches++;
+  SRBE_CUDA(cudaGetLastError());
+}
+
 void charge_update(srbe_ctx *c) {
   if (c->lat_solve) {
     charge_update_lattice(c);
@@ -705,18 +732,11 @@ void charge_update(srbe_ctx *c) {
       mlp_forward(c, c->mlp.D.p, c->ne, nullptr, c->pcg.y.p);
     }
     charge_update_pcg(c);
+    // the direct solve of the same right-hand side, run only when PCG stopped at maxit above tol
+    charge_update_direct(c, c->pcg.stats.p + 1);
     return;
   }
-  const int64_t ne = c->ne;
-  const unsigned nb = blocks_for((ne + 1) * 32, 256);
-  if (c->precision == SRBE_MIXED)
-    k_charges_split<<<blocks_for(ne + 1, 256 / 32 / kSplitWarps), 256, 0, c->stream>>>(
-        ne, c->Bsplit.p, c->bsplit.p, c->dpsi, c->qd.p, c->wesplit.p, c->wd, c->s_e, c->Q.p, c->Q32.p, c->scal.p);
-  else
-    k_charges_fp64<<<nb, 256, 0, c->stream>>>(ne, c->Bmat.p, c->bvec.p, c->dpsi, c->qd.p, c->we.p, c->wd, c->s_e,
-                                              c->Q.p, c->Q32.p, c->scal.p);
-  c->launches++;
-  SRBE_CUDA(cudaGetLastError());
+  charge_update_direct(c, nullptr);
 }
 
 // FP64 check of the constant-potential conditions (Eqs. 9-10) met by the charges in use:

@@ -279,6 +279,12 @@ struct srbe_ctx {
   double lang_gamma = 0.0, lang_T = 0.0;
   uint64_t lang_seed = 0;
 
+  // device-raised error flags (see srbe_synchronize), one word each so that kernels set them with
+  // plain stores: host-mapped pinned memory, read by the host without a copy
+  int *h_status = nullptr;                     // host view
+  int *d_status = nullptr;                     // device view of the same words
+  int inject = 0;                              // test aid: 1 NaN into F[0], 2 NaN into Q[0] after each pass
+
   // counters
   int64_t launches = 0;
   int64_t mode_evals = 0;
@@ -286,6 +292,9 @@ struct srbe_ctx {
 };
 
 namespace srbe {
+
+// device error flags (ctx->d_status words)
+enum { kStatNotConv = 0, kStatNonFiniteF = 1, kStatNonFiniteQ = 2, kStatBadInput = 3, kStatTimeout = 4, kStatCount = 8 };
 
 // indices into ctx->scal (16 device scalars): dipoles sum q z and sum Q Z, psi_bar (e/nm), then the
 // energy accumulators: U_N ion-ion, U_N ion-electrode, LJ, bonds, U_N electrode-electrode,
@@ -405,6 +414,8 @@ void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift);
 void steepest_descent_move(srbe_ctx *c, double a, double dmax);
 void build_A_and_inverse(srbe_ctx *c);
 void energy_scalars(srbe_ctx *c);
+// raises kStatNonFiniteF / kStatNonFiniteQ if any of F [3][ni] (forces = true) or Q [ne] is not finite
+void check_finite(srbe_ctx *c, bool forces, bool charges);
 enum Phase {
   kPhUpload = 0, kPhCells, kPhS1, kPhRhs, kPhSolve, kPhS2, kPhForces, kPhIntegrate, kPhEnergy, kPhForcesII, kPhCount
 };

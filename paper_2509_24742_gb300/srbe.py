@@ -12,7 +12,7 @@ import numpy as np
 
 from . import build as _build
 
-SRBE_OK, SRBE_EINVAL, SRBE_ENOMEM, SRBE_ECUDA, SRBE_ESTATE, SRBE_ENOTCONV, SRBE_ETIMEOUT = range(7)
+SRBE_OK, SRBE_EINVAL, SRBE_ENOMEM, SRBE_ECUDA, SRBE_ESTATE, SRBE_ENOTCONV, SRBE_ETIMEOUT, SRBE_ENONFINITE = range(8)
 FP64, MIXED = 0, 1
 DIRECT, PCG, LATTICE = 0, 1, 2
 WARM_ZERO, WARM_PREVIOUS, WARM_MODEL = 0, 1, 2
@@ -24,7 +24,8 @@ ENERGY_TERMS = ("U_N ion-ion", "U_N ion-electrode", "U_N electrode-electrode", "
                 "U_LJ", "U_bond")
 
 _STATUS = {SRBE_EINVAL: "invalid argument", SRBE_ENOMEM: "out of memory", SRBE_ECUDA: "CUDA error",
-           SRBE_ESTATE: "call out of order", SRBE_ENOTCONV: "not converged", SRBE_ETIMEOUT: "timeout"}
+           SRBE_ESTATE: "call out of order", SRBE_ENOTCONV: "not converged", SRBE_ETIMEOUT: "timeout",
+           SRBE_ENONFINITE: "non-finite result"}
 
 
 class SrbeError(RuntimeError):
@@ -69,6 +70,10 @@ EXPORTS = {
     "srbe_graph_state": ([_vp, ctypes.POINTER(_int), ctypes.POINTER(_i64)], _int),
     "srbe_get_phase_times": ([_vp, _dp, ctypes.POINTER(_i64)], _int),
     "srbe_structure_factor_noalloc": ([_dp, _i64, _vp, _vp, _int, _vp, _vp, _vp], _int),
+    "srbe_synchronize": ([_vp, _dbl], _int),
+    "srbe_set_host_io": ([_vp, _vp, _vp, _vp], _int),
+    "srbe_forces_host_io": ([_vp, _u64, _u64, ctypes.POINTER(_dbl)], _int),
+    "srbe_debug_inject_nonfinite": ([_vp, _int], _int),
     "srbe_minimize": ([_vp, _int, _dbl, _dbl, _u64], _int),
     "srbe_set_solver": ([_vp, _int, _dbl, _int, _int], _int),
     "srbe_get_solver_stats": ([_vp, ctypes.POINTER(_int), ctypes.POINTER(_dbl)], _int),
@@ -78,6 +83,7 @@ EXPORTS = {
     "srbe_descriptors": ([_vp, _fp], _int),
     "srbe_solution": ([_vp, _dp], _int),
     "srbe_mlp_predict": ([_vp, _fp, _i64, _fp], _int),
+    "srbe_mlp_predict_dev": ([_vp, _vp, _i64, _vp], _int),
     "srbe_mlp_gradients": ([_vp, _fp, _fp, _i64, _fp, ctypes.POINTER(_dbl)], _int),
     "srbe_mlp_train": ([_vp, _fp, _fp, _i64, _int, _int, ctypes.c_float, ctypes.c_float, _u64,
                         ctypes.POINTER(_dbl)], _int),
@@ -287,6 +293,26 @@ class Context:
     def step(self, nsteps, seed0):
         self._check(self.lib.srbe_step(self.h, int(nsteps), int(seed0)))
 
+    def set_host_io(self, r_ptr, F_ptr, Q_ptr=None):
+        """Binds caller-owned page-locked host buffers (addresses): positions [n][3] in, forces
+        [n][3] and charges [n_ele] out, all float64, for forces_host_io."""
+        self._check(self.lib.srbe_set_host_io(self.h, _vp(r_ptr), _vp(F_ptr), _vp(Q_ptr) if Q_ptr else None))
+
+    def forces_host_io(self, seed, step):
+        """One captured force pass on the bound buffers; returns psi_bar (V)."""
+        psi = _dbl()
+        self._check(self.lib.srbe_forces_host_io(self.h, int(seed), int(step), ctypes.byref(psi)))
+        return psi.value
+
+    def synchronize(self, timeout_s=-1.0):
+        """Waits for the queued work (at most timeout_s seconds; < 0 without limit) and reports the
+        device-raised flags (SRBE_ENOTCONV, SRBE_ENONFINITE) as SrbeError; SRBE_ETIMEOUT at the limit."""
+        self._check(self.lib.srbe_synchronize(self.h, float(timeout_s)))
+
+    def debug_inject_nonfinite(self, what):
+        """Test aid: 1 puts a NaN into F[0], 2 into Q[0] after every following pass, 0 stops it."""
+        self._check(self.lib.srbe_debug_inject_nonfinite(self.h, int(what)))
+
     def set_graphs(self, on=True):
         self._check(self.lib.srbe_set_graphs(self.h, 1 if on else 0))
 
@@ -344,6 +370,10 @@ class Context:
         out = np.empty(D.shape[0], np.float32)
         self._check(self.lib.srbe_mlp_predict(self.h, _ptr(D, _fp), D.shape[0], _ptr(out, _fp)))
         return out
+
+    def mlp_predict_dev(self, D_ptr, n, out_ptr):
+        """Forward pass on device buffers (float32 [n][80] -> float32 [n]), queued on the context's stream."""
+        self._check(self.lib.srbe_mlp_predict_dev(self.h, _vp(D_ptr), int(n), _vp(out_ptr)))
 
     def mlp_gradients(self, D, T):
         D = np.ascontiguousarray(D, dtype=np.float32).reshape(-1, N_DESC)

@@ -2,7 +2,8 @@
 87,712 ion sites, P = 500): the oracle cannot solve for the charges at this size, so the test
 compares sampled outputs it can compute one by one (b on sampled electrode sites, electrostatic
 forces on sampled ions for the charges the GPU found) and checks properties that hold at any size
-(neutrality, the FP64 residual of the constant-potential conditions, the mixed form against FP64)."""
+(neutrality, the FP64 residual of the constant-potential conditions, the mixed form against FP64).
+The charges are checked against the oracle's rows of A on sampled sites."""
 import numpy as np
 import pytest
 
@@ -30,6 +31,7 @@ def test_precision_100k_sampled_parity_and_properties(orc, big):
         F, Q, psi = ctx.forces()
         _, _, b = ctx.solve_charges()
         res64 = ctx.charge_residual()
+        alpha_A = ctx.alpha_A()
         ctx.set_lattice(0)                      # the plain per-site sums at the same size
         F0, Q0, _ = ctx.forces()
         ctx.set_lattice(1)
@@ -44,6 +46,14 @@ def test_precision_100k_sampled_parity_and_properties(orc, big):
     ions = np.sort(rng.choice(big.n_ion, 48, replace=False))
     assert rel(b[sites] * srbe.VOLT, orc.sampled_b(big, m, c, sites)) < 1e-10
     assert rel(F[ions], orc.sampled_forces(big, m, c, Q, ions)) < 1e-10
+    # the charges meet the constant-potential conditions A Q = dpsi d + b + psi_bar e (Eqs. 9-10)
+    # row by row, with the rows of A formed by the oracle one at a time (Eq. 18)
+    rows = np.sort(rng.choice(big.n_ele, 12, replace=False))
+    d = np.where(big.side == 1, 0.5, -0.5)
+    bv = b * srbe.VOLT
+    AQ = orc.A_rows(L, big.eta, big.R, alpha_A, Q, rows)
+    r = AQ - (big.dpsi * d[rows] + bv[rows]) - psi * srbe.VOLT
+    assert np.abs(r).max() < 1e-10 * np.abs(big.dpsi * d + bv).max()
     rms_f = np.sqrt(((F32 - F) ** 2).sum(1).mean() / (F ** 2).sum(1).mean())
     rms_q = np.sqrt(((Q32 - Q) ** 2).mean() / (Q ** 2).mean())
     print("100k slab: FP64 residual %.2e, mixed residual %.2e, mixed RMS force err %.2e, charge err %.2e"

@@ -1,0 +1,115 @@
+"""Parity at the benchmark's own system: the 4 x 4 x 16 nm MD slab (3,072 electrode sites, 2,000
+three-site cations and 2,000 anions = 8,000 ion sites, P = 200, M = 4, alpha 3.5 nm^-1, rc 1.2 nm),
+the CUDA path through the C ABI against the CPU oracle on the same seeded inputs and the same mode
+lists (drawn by the oracle's own sampler).
+
+* FP64: forces (Coulomb of Eqs. 13 and 25 + slab term + LJ + bonds), charges and psi_bar
+  (Eqs. 9-11), b (Eq. 24 with Eq. 19's near and slab parts) within 1e-10 normwise; energy terms
+  within 1e-9.
+* Mixed form (the benchmark's arithmetic; split ion-ion pass on the side stream): RMS force and
+  charge error against the oracle within 1e-3 (the stated bar), printed.
+* Three MD steps of Algorithm 1 (velocity Verlet + the Langevin thermostat of Eq. 39, as the
+  benchmark runs them, CUDA-graph replays included) in both forms against oracle.System.md_step.
+"""
+import numpy as np
+import pytest
+
+from paper_2509_24742_gb300 import srbe, workloads as wl
+
+pytestmark = pytest.mark.gpu
+ALPHA_A = 1.25          # alpha_A (Lz - H) = 6.7 for this box
+TOL = 1e-10
+SEED = 3002
+THERMO = (50.0, 400.0, 9)
+NSTEPS = 3
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0)
+
+
+def rms(a, b):
+    a, b = np.asarray(a).reshape(len(b), -1), np.asarray(b).reshape(len(b), -1)
+    return np.sqrt(((a - b) ** 2).sum(1).mean() / (b ** 2).sum(1).mean())
+
+
+@pytest.fixture(scope="module")
+def slab():
+    return wl.md_11072()
+
+
+@pytest.fixture(scope="module")
+def ref(orc, slab):
+    return orc.System(slab, alpha_A=ALPHA_A)
+
+
+@pytest.fixture(scope="module")
+def one(orc, slab, ref):
+    samples = orc.sample_metropolis(slab.box, slab.alpha, slab.M, slab.P, SEED, 0)
+    m, c = ref.modes(samples)
+    return samples, ref.evaluate(m, c)
+
+
+@pytest.fixture(scope="module")
+def trajectory(orc, slab, ref):
+    """The oracle's NSTEPS steps from the workload's positions and Maxwell velocities."""
+    r, v = slab.r.copy(), slab.v.copy()
+    m, c = ref.modes(orc.sample_metropolis(slab.box, slab.alpha, slab.M, slab.P, SEED, 0))
+    F = orc.evaluate(ref.at(r), ref.factor, m, c)["F"]
+    for step in range(1, NSTEPS + 1):
+        m, c = ref.modes(orc.sample_metropolis(slab.box, slab.alpha, slab.M, slab.P, SEED, step))
+        r, v, ev = ref.md_step(r, v, F, m, c, thermostat=THERMO, step=step)
+        F = ev["F"]
+    return r, v, F, ev["Q"]
+
+
+def test_fp64_matches_oracle_at_the_benchmark_system(slab, one):
+    samples, ev = one
+    with srbe.from_slab(slab, precision=srbe.FP64, alpha_A=ALPHA_A, md=True) as ctx:
+        ctx.set_k(samples)
+        F, Q, psi, E = ctx.forces(energy=True)
+        Q2, psi2, b = ctx.solve_charges()
+        res = ctx.charge_residual()
+    assert rel(F, ev["F"]) < TOL, rel(F, ev["F"])
+    assert rel(Q, ev["Q"]) < TOL, rel(Q, ev["Q"])
+    assert abs(psi * srbe.VOLT - ev["psi_bar"]) < TOL * abs(ev["psi_bar"])
+    assert rel(b * srbe.VOLT, ev["b"]) < TOL
+    assert np.array_equal(Q, Q2) and psi == psi2
+    assert res < 1e-12
+    ref_E = np.concatenate([ev["E"], [ev["E_lj"], ev["E_bond"]]])
+    np.testing.assert_allclose(E, ref_E, rtol=1e-9, atol=1e-9 * np.abs(ref_E).max())
+
+
+def test_mixed_form_error_against_oracle(slab, one):
+    samples, ev = one
+    with srbe.from_slab(slab, precision=srbe.MIXED, alpha_A=ALPHA_A, md=True) as ctx:
+        ctx.set_k(samples)
+        F, Q, psi = ctx.forces()                 # split ion-ion pass, as in the benchmark
+        res = ctx.charge_residual()
+    ef, eq = rms(F, ev["F"]), rms(Q, ev["Q"])
+    print("11,072-site slab, mixed form vs FP64 oracle: RMS force err %.2e, RMS charge err %.2e, "
+          "psi_bar err %.2e, FP64 residual %.2e" % (ef, eq, abs(psi * srbe.VOLT / ev["psi_bar"] - 1), res))
+    assert ef < 1e-3 and eq < 1e-3
+    assert res < 1e-10
+
+
+@pytest.mark.parametrize("precision", [srbe.FP64, srbe.MIXED])
+def test_md_steps_match_oracle_at_the_benchmark_system(slab, trajectory, precision):
+    r_ref, v_ref, F_ref, Q_ref = trajectory
+    with srbe.from_slab(slab, precision=precision, alpha_A=ALPHA_A, md=True) as ctx:
+        ctx.set_thermostat(*THERMO)
+        ctx.step(NSTEPS, SEED)
+        graphs = ctx.graph_state()[0]
+        r, v = ctx.get_positions(velocities=True)
+    L = np.asarray(slab.box[:2])
+    d = r - r_ref
+    d[:, :2] -= L * np.round(d[:, :2] / L)
+    dv = rel(v, v_ref)
+    print("%s: %d MD steps vs oracle: max |dr| %.2e nm, velocity rel err %.2e"
+          % ("FP64" if precision == srbe.FP64 else "mixed", NSTEPS, np.abs(d).max(), dv))
+    assert graphs == 1
+    if precision == srbe.FP64:
+        assert np.abs(d).max() < 1e-9 and dv < 1e-8
+    else:
+        assert np.abs(d).max() < 1e-6 and dv < 1e-4

@@ -8,10 +8,18 @@ same configuration and mode list:
   * U_F = 1/2 sum_k c_k |S1 + S2|^2 against srbe_forces' energy term;
   * the far part of b rebuilt from S1 against srbe_solve_electrode_charges' b (with rc below every
     ion-electrode distance, so that b = b_F + b_slab exactly);
-over two calls in a row (ions, then electrode sites) and a repeat of the first call.
+over two calls in a row (ions, then electrode sites) and a repeat of the first call; both outputs
+also against the CPU oracle's structure factor.  Further cases: the largest mode list (8,192 modes)
+over 1e5 particles, where the scratch array caps the chunk count and every chunk spans many
+128-particle batches, against the oracle on a subset of modes; and a first call made on a
+non-blocking stream in a fresh process (the one-time set-up must be complete before that stream's
+kernels read the table).
 This file is collected last so that a failure here comes after every other test has run."""
 import copy
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -68,6 +76,11 @@ def test_noalloc_structure_factor_matches_existing_entry_points():
     assert np.array_equal(S1_d.cpu().numpy(), S1b_d.cpu().numpy())
 
     # U_F of the existing srbe_forces (kJ/mol) from the two outputs
+    from oracle import oracle as orc
+    for S, pos, w in ((S1, slab.r, slab.q), (S2, slab.R, Q)):
+        ref = orc.sfac(np.asarray(pos, float), np.asarray(w, float), m, L) @ [1, 1j]
+        assert np.linalg.norm(S - ref) < TOL * np.linalg.norm(ref)
+
     UF = 0.5 * float((c * np.abs(S1 + S2) ** 2).sum()) * srbe.K_E
     assert abs(UF - E[3]) < TOL * abs(E[3])
 
@@ -90,3 +103,64 @@ def test_noalloc_rejects_oversized_mode_lists():
         S.structure_factor_noalloc((1.0, 1.0, 1.0), 1, r.data_ptr(), r.data_ptr(), 8193, m.data_ptr(),
                                    out.data_ptr())
     assert e.value.code == S.SRBE_EINVAL
+
+
+def test_noalloc_largest_mode_list_many_batches_per_chunk(orc):
+    """K = 8192 modes over 100,003 particles: the 2 MiB scratch array holds 16 chunks of ~6,300
+    particles each (a ragged last chunk and a ragged last batch)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(8192)
+    L = np.array([3.0, 2.5, 11.0])
+    n, K = 100_003, 8192
+    r = rng.uniform(0, 1, size=(n, 3)) * L
+    w = rng.choice([-0.78, 0.78], size=n)
+    m = rng.integers(-12, 13, size=(K, 3)).astype(np.int32)
+    m[np.all(m == 0, axis=1)] = (0, 0, 1)
+    S_d = torch.empty((K, 2), dtype=torch.float64, device=dev)
+    r_d = torch.tensor(r, device=dev)
+    w_d = torch.tensor(w, device=dev)
+    m_d = torch.tensor(m, device=dev)
+    for _ in range(2):                     # two calls in a row: the second reuses the array
+        S_d.fill_(float("nan"))
+        srbe.structure_factor_noalloc(L, n, r_d.data_ptr(), w_d.data_ptr(), K, m_d.data_ptr(), S_d.data_ptr(),
+                                      torch.cuda.current_stream(dev).cuda_stream)
+        torch.cuda.synchronize()
+        S = S_d.cpu().numpy()
+        sub = np.concatenate([np.arange(64), rng.choice(K, 64, replace=False), [K - 1]])
+        ref = orc.sfac(r, w, m[sub], L)
+        assert np.linalg.norm(S[sub] - ref) < TOL * np.linalg.norm(ref)
+
+
+_FIRST_CALL_ON_SIDE_STREAM = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, %(root)r)
+from paper_2509_24742_gb300 import srbe
+dev = torch.device("cuda", 0)
+rng = np.random.default_rng(3)
+L = np.array([2.0, 2.0, 12.0]); n, K = 4000, 300
+r = rng.uniform(0, 1, size=(n, 3)) * L; w = rng.normal(size=n)
+m = rng.integers(-6, 7, size=(K, 3)).astype(np.int32); m[np.all(m == 0, axis=1)] = (1, 0, 0)
+side = torch.cuda.Stream(dev)          # a pool stream: created non-blocking
+with torch.cuda.stream(side):
+    r_d = torch.tensor(r, device=dev); w_d = torch.tensor(w, device=dev); m_d = torch.tensor(m, device=dev)
+    S_d = torch.empty((K, 2), dtype=torch.float64, device=dev)
+side.synchronize()
+srbe.structure_factor_noalloc(L, n, r_d.data_ptr(), w_d.data_ptr(), K, m_d.data_ptr(), S_d.data_ptr(),
+                              side.cuda_stream)
+side.synchronize()
+kr = 2 * np.pi * r / L
+ph = kr @ m.T.astype(float)
+ref = np.stack([(w[:, None] * np.cos(ph)).sum(0), (w[:, None] * np.sin(ph)).sum(0)], 1)
+err = np.linalg.norm(S_d.cpu().numpy() - ref) / np.linalg.norm(ref)
+print("first call on a non-blocking stream: rel err %%.2e" %% err)
+sys.exit(0 if err < 1e-10 else 1)
+"""
+
+
+def test_noalloc_first_call_on_a_nonblocking_stream():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _FIRST_CALL_ON_SIDE_STREAM % {"root": root}],
+                         capture_output=True, text=True, timeout=600)
+    print(out.stdout, out.stderr[-2000:])
+    assert out.returncode == 0
