@@ -14,14 +14,20 @@ library's stream and the per-phase device times come from the library's own even
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch64 [--replicas R] [--steps K] [--warmup W]
-  python bench.py --workload prec100k | large1m | solve6144 | noise | learned | mlp [--steps K]
+  python bench.py --workload prec100k | large1m | solve6144 | noise | learned | mlp | oneshot784 [--steps K]
 
 batch64 measures the batching form instead: R uneven replicas (default 64; 8k-57k particles,
 1,536-6,144 electrode sites, 0-4 V, Lz/Lx 3-8, P 100-400, each with its own seed) stepped as one
 CUDA-graph launch per batch step, against the same replicas stepped one after another with the
 plain FP64 path.  prec100k and large1m run the precision form on the 100k-particle and 1.2 M-particle
 slabs against FP64; solve6144 times the charge update alone against the HBM roofline; noise gives
-the electrode-charge standard deviation over sampling seeds against M and P.
+the electrode-charge standard deviation over sampling seeds against M and P; learned trains the
+warm-start MLP on plain-method data and times PCG at residual 1e-8 from cold, previous-step and
+learned starts (FP64 and mixed) beside the direct solves and a learned mixed batch; mlp times the
+tensor-core MLP forward alone against the BF16 peak.
+
+The e2e key of the default line goes through srbe_forces_host_io: the next frame of an MD trajectory
+copied into a pinned buffer, positions read from it on the device, forces and charges written back.
 """
 from __future__ import annotations
 
@@ -808,6 +814,54 @@ def mlp_arm(args):
             "host_vs_device_path_max_abs_diff": float(np.abs(y0 - y1).max())}
 
 
+def oneshot_arm(args):
+    """The one-shot case (2 x 2 x 12 nm, 384 electrode sites at 0.246 nm, 400 point ions, P = 100,
+    M = 2, 1 V): force + electrode-charge evaluations per second through srbe_forces_dev (device
+    buffers, no host copies), FP64 and mixed, each evaluation drawing its modes on the device-side
+    path of srbe_sample_k; beside them the CPU oracle's evaluations per second for the same case."""
+    import torch
+    from paper_2509_24742_gb300 import srbe, workloads
+    torch.cuda.set_device(0)
+    slab = workloads.one_shot_784()
+    stream = torch.cuda.Stream()
+    out = {}
+    Fd = torch.empty((slab.n_ion, 3), dtype=torch.float64, device="cuda")
+    Qd = torch.empty(slab.n_ele, dtype=torch.float64, device="cuda")
+    steps = max(20, min(args.steps, 500))
+    for name, prec in (("fp64", srbe.FP64), ("mixed", srbe.MIXED)):
+        with srbe.from_slab(slab, precision=prec, alpha_A=1.7) as c:
+            c.set_stream(stream.cuda_stream)
+            for i in range(args.warmup):
+                c.sample_k(SEED, i)
+                c.forces_dev(Fd.data_ptr(), Qd.data_ptr())
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(steps):
+                c.sample_k(SEED, 1000 + i)
+                c.forces_dev(Fd.data_ptr(), Qd.data_ptr())
+            torch.cuda.synchronize()
+            out[name] = steps / (time.perf_counter() - t0)
+    from oracle import oracle
+    ref = oracle.System(slab, alpha_A=1.7)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < 5.0 or n < 3:
+        m, c = ref.modes(oracle.sample_metropolis(slab.box, slab.alpha, slab.M, slab.P, SEED, n))
+        ref.evaluate(m, c, with_lj=False)
+        n += 1
+    cpu = n / (time.perf_counter() - t0)
+    return {"metric": "SRBE force + electrode-charge evaluations/s, one-shot case", "value": out["mixed"],
+            "unit": "evaluations/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "oneshot784: 2x2x12 nm, 384 electrode sites, 400 ions, P=100, M=2, 1 V",
+                       "timing": "host wall clock around srbe_sample_k + srbe_forces_dev, device synchronised at "
+                                 "both ends (launch-bound at this size)"},
+            "fp64_evaluations_per_s": out["fp64"],
+            "cpu_baseline": {"value": cpu, "unit": "evaluations/s",
+                             "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)), "kind": "oracle",
+                             "sample": "%d oracle evaluations of the same case (A factored once, untimed)" % n}}
+
+
 # ---------------------------------------------------------------------------------------------- CPU oracle
 def oracle_steps(budget_s, max_steps, min_steps=2, warmup=0):
     """Full oracle MD steps (plain FP64 C, OpenMP over independent output elements) on the same
@@ -869,7 +923,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="md11072",
-                    choices=["md11072", "batch64", "prec100k", "solve6144", "large1m", "noise", "learned", "mlp"])
+                    choices=["md11072", "batch64", "prec100k", "solve6144", "large1m", "noise", "learned", "mlp",
+                             "oneshot784"])
     ap.add_argument("--replicas", type=int, default=64)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -898,6 +953,9 @@ def main():
         return
     if args.workload == "mlp":
         print(json.dumps(mlp_arm(args)))
+        return
+    if args.workload == "oneshot784":
+        print(json.dumps(oneshot_arm(args)))
         return
     if world > 1:
         import torch

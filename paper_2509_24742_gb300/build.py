@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsrbe.so")
 SOURCES = ["api.cu", "kspace.cu", "realspace.cu", "solve.cu", "learned.cu", "lattice.cu", "noalloc.cu"]
-HEADERS = ["srbe_internal.cuh"]
+HEADERS = ["srbe_internal.cuh", "tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-Xptxas", "-v", "-I", os.path.join(ROOT, "include")]

@@ -268,6 +268,11 @@ __global__ void k_unproject(int64_t n, const double *__restrict__ Q, const doubl
   if (i < n) y[i] = fma(-scal[kScalPsi], we[i], Q[i]);
 }
 
+__global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
 __global__ void k_interleave(int64_t n, const double *__restrict__ F, double *__restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -997,7 +1002,7 @@ void charges_pass(srbe_ctx *c, bool after_drift) {
   SRBE_CUDA(cudaEventRecord(c->ev_join, c->side));
   phase_begin(c, kPhS1);
   structure_factor(c, c->ni, c->x.p, c->y.p, c->z.p, c->q.p, c->S1.p, nullptr, kScalMion, 0,
-                   after_drift ? c->iu.p : nullptr);
+                   after_drift ? c->iu.p : nullptr, c->q32.p);
   phase_end(c, kPhS1);
   SRBE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   phase_begin(c, kPhRhs);
@@ -1007,7 +1012,10 @@ void charges_pass(srbe_ctx *c, bool after_drift) {
   charge_update(c);
   phase_end(c, kPhSolve);
   // test aid: a NaN in Q[0] before anything reads the charges
-  if (c->inject == 2 && c->ne > 0) SRBE_CUDA(cudaMemsetAsync(c->Q.p, 0xff, sizeof(double), c->stream));
+  if (c->inject == 2 && c->ne > 0) {
+    SRBE_CUDA(cudaMemsetAsync(c->Q.p, 0xff, sizeof(double), c->stream));
+    SRBE_CUDA(cudaMemsetAsync(c->Q32.p, 0xff, sizeof(float), c->stream));
+  }
 }
 
 // check: non-finite forces and charges raise the context's flag (the MD step checks them in its
@@ -1030,7 +1038,7 @@ void forces_pass(srbe_ctx *c, bool energies, bool after_drift, bool check) {
   }
   phase_begin(c, kPhS2);
   if (c->lat.active(c->ne, c->K)) lattice_s2(c, c->S2.p, c->S1.p, kScalMele);
-  else structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele, 1, c->eu.p);
+  else structure_factor(c, c->ne, c->ex.p, c->ey.p, c->ez.p, c->Q.p, c->S2.p, c->S1.p, kScalMele, 1, c->eu.p, c->Q32.p);
   phase_end(c, kPhS2);
   phase_begin(c, kPhForces);
   ion_forces(c, energies);
@@ -1343,6 +1351,8 @@ int srbe_set_positions(srbe_ctx *c, int64_t n_ion, const double *r, const double
       double *aos = e->aos.ensure(3 * n);
       SRBE_CUDA(cudaMemcpyAsync(aos, r, sizeof(double) * 3 * n_ion, cudaMemcpyHostToDevice, c->stream));
       SRBE_CUDA(cudaMemcpyAsync(c->q.p, q, sizeof(double) * n_ion, cudaMemcpyHostToDevice, c->stream));
+      k_to_f32<<<blocks_for(n_ion, 256), 256, 0, c->stream>>>(n_ion, c->q.p, c->q32.ensure(n));
+      c->launches++;
       k_deinterleave<<<blocks_for(n_ion, 256), 256, 0, c->stream>>>(n_ion, aos, c->L[0], c->L[1], c->x.p, c->y.p,
                                                                    c->z.p);
       c->launches++;
@@ -1370,6 +1380,8 @@ int srbe_set_positions_dev(srbe_ctx *c, int64_t n_ion, const double *r_dev, cons
     c->F.ensure(3 * n);
     if (n_ion > 0) {
       SRBE_CUDA(cudaMemcpyAsync(c->q.p, q_dev, sizeof(double) * n_ion, cudaMemcpyDeviceToDevice, c->stream));
+      k_to_f32<<<blocks_for(n_ion, 256), 256, 0, c->stream>>>(n_ion, c->q.p, c->q32.ensure(n));
+      c->launches++;
       k_deinterleave<<<blocks_for(n_ion, 256), 256, 0, c->stream>>>(n_ion, r_dev, c->L[0], c->L[1], c->x.p, c->y.p,
                                                                    c->z.p);
       c->launches++;

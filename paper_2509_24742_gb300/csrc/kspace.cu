@@ -87,8 +87,8 @@ __device__ __forceinline__ void sf_finish(const SfFinish &f, int k, int lane) {
 template <bool F32>
 __global__ void __launch_bounds__(kSfThreads)
 k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-               const uint64_t *__restrict__ u, const double *__restrict__ w, int K, const int4 *__restrict__ modes,
-               double3 invL,
+               const uint64_t *__restrict__ u, const double *__restrict__ w, const float *__restrict__ w32, int K,
+               const int4 *__restrict__ modes, double3 invL,
                const double2 *__restrict__ tab, int64_t chunk, double2 *__restrict__ partial,
                double *__restrict__ mpart, SfFinish fin, int *__restrict__ done) {
   __shared__ uint64_t su[3][kSfThreads];
@@ -116,8 +116,10 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
         su[1][t] = to_turns64(y[i], invL.y);
         su[2][t] = to_turns64(z[i], invL.z);
       }
-      sw[t] = w[i];
-      if (F32) sw32[t] = (float)sw[t];
+      // the mixed form reads the weights' FP32 copy when there is one: an FP64 conversion per
+      // particle would keep this GPU's scarce FP64 pipe busy
+      if (!F32) sw[t] = w[i];
+      else sw32[t] = w32 ? w32[i] : (float)w[i];
       if (blockIdx.y == 0) mz = fma(w[i], z[i], mz);
     }
     __syncthreads();
@@ -231,21 +233,27 @@ __global__ void k_sfac_reduce(SfFinish f) {
   sf_finish(f, k, threadIdx.x & 31);
 }
 
-// chunking of the particle sum: whole 128-particle batches, at most kSfMaxChunks chunks
+// chunking of the particle sum: whole 128-particle batches, at most kSfMaxChunks chunks.  A chunk
+// spans as many batches (up to 8) as keeps at least 8 blocks per SM: each block ends with a few FP64
+// operations (the partial's compensation and the warp sums), which cost 64 cycles of a
+// sub-partition each on this GPU, so longer chunks spread them over more particles.
+constexpr int64_t kSfMinBlocks = 8 * 152;
 int64_t sfac_chunks(int64_t n, int K, int64_t *chunk) {
-  (void)K;
   if (n <= 0) {
     *chunk = kSfThreads;
     return 0;
   }
+  const int64_t ktiles = std::max(1, (K + 31) / 32);
   const int64_t batches = (n + kSfThreads - 1) / kSfThreads;
-  const int64_t per = (batches + kSfMaxChunks - 1) / kSfMaxChunks;
+  int64_t per = (batches + kSfMaxChunks - 1) / kSfMaxChunks;
+  while (per < 8 && ((batches + 2 * per - 1) / (2 * per)) * ktiles >= kSfMinBlocks) per *= 2;
   *chunk = per * kSfThreads;
   return (n + *chunk - 1) / *chunk;
 }
 
 void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *w,
-                      double2 *S, const double2 *S_add, int mslot, int coef_mode, const uint64_t *u) {
+                      double2 *S, const double2 *S_add, int mslot, int coef_mode, const uint64_t *u,
+                      const float *w32) {
   const int K = c->K;
   const int ktiles = std::max(1, (K + 31) / 32);
   int64_t chunk;
@@ -260,11 +268,12 @@ void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, 
     SRBE_REQUIRE(c->sfdone.cap >= (size_t)ktiles, SRBE_ESTATE, "tile counters not reserved for this size");
     dim3 grid((unsigned)nchunk, (unsigned)ktiles);
     if (c->precision == SRBE_MIXED)
-      k_sfac_partial<true><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, u, w, K, c->dm.p, invL, c->tab.p, chunk,
-                                                               c->partial.p, c->mpart.p, f, c->sfdone.p);
+      k_sfac_partial<true><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, u, w, w32, K, c->dm.p, invL, c->tab.p,
+                                                               chunk, c->partial.p, c->mpart.p, f, c->sfdone.p);
     else
-      k_sfac_partial<false><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, u, w, K, c->dm.p, invL, c->tab.p, chunk,
-                                                                c->partial.p, c->mpart.p, f, c->sfdone.p);
+      k_sfac_partial<false><<<grid, kSfThreads, 0, c->stream>>>(n, x, y, z, u, w, nullptr, K, c->dm.p, invL,
+                                                                c->tab.p, chunk, c->partial.p, c->mpart.p, f,
+                                                                c->sfdone.p);
     c->launches++;
     c->mode_evals += n * (int64_t)K;
   } else {

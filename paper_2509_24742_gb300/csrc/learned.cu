@@ -165,11 +165,26 @@ k_mlp_forward_tc(int64_t n, const float *__restrict__ D, const float *__restrict
   bool fail = false;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t row0 = tile * 128;
-    // standardised inputs of the tile (rows beyond n are zero)
-    for (int i = t; i < 128 * kIn; i += 128) {
-      const int r = i / kIn, k = i - r * kIn;
-      const float x = row0 + r < n ? (D[row0 * kIn + i] - sxm[k]) / sxs[k] : 0.f;
-      tc::split_bf16(x, xh[tc::off(r, k)], xl[tc::off(r, k)]);
+    // standardised inputs of the tile, thread t loading its own row (rows beyond n are zero): 16-byte
+    // loads of the row, 16-byte stores of each 8-wide chunk of both operands
+    {
+      const bool live = row0 + t < n;
+      const float4 *src = reinterpret_cast<const float4 *>(D + (row0 + t) * kIn);
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float4 q[kIn / 8];
+#pragma unroll
+        for (int u = 0; u < kIn / 8; ++u) q[u] = live ? __ldg(src + half * (kIn / 8) + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < kIn / 16; ++g) {
+          const int k0 = half * (kIn / 2) + 8 * g;
+          float v[8] = {q[2 * g].x, q[2 * g].y, q[2 * g].z, q[2 * g].w,
+                        q[2 * g + 1].x, q[2 * g + 1].y, q[2 * g + 1].z, q[2 * g + 1].w};
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = live ? (v[j] - sxm[k0 + j]) / sxs[k0 + j] : 0.f;
+          tc::store8_split(xh, xl, t, k0, v);
+        }
+      }
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -194,8 +209,9 @@ k_mlp_forward_tc(int64_t n, const float *__restrict__ D, const float *__restrict
       float v[32];
       tc::ld32(d1 + lanes + (uint32_t)c0, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        tc::split_bf16(silu(v[j] + sb1[c0 + j]), hh[tc::off(t, c0 + j)], hl[tc::off(t, c0 + j)]);
+      for (int j = 0; j < 32; ++j) v[j] = silu(v[j] + sb1[c0 + j]);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) tc::store8_split(hh, hl, t, c0 + 8 * g, v + 8 * g);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();

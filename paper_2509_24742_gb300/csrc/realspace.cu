@@ -1626,7 +1626,7 @@ __device__ __forceinline__ void ion_ii_one(int64_t p, int64_t ni, const CellsDev
 }
 
 template <bool LJ>
-__global__ void __launch_bounds__(kGatherThreads)
+__global__ void __launch_bounds__(kGatherThreads, 5)
 k_ion_ii(int64_t ni, CellsDev ions, ListsDev nl, MdDev md, ForceF32 pf, float4 *__restrict__ Fii) {
   __shared__ float2 shift[256];                     // (ix, iy) image counts as floats, by entry >> 24
   __shared__ float2 ljs[kMaxLjTypes * kMaxLjTypes]; // (sigma^2, 24 eps)
@@ -1640,8 +1640,10 @@ k_ion_ii(int64_t ni, CellsDev ions, ListsDev nl, MdDev md, ForceF32 pf, float4 *
     }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-  ion_ii_one<LJ>(p, ni, ions, nl, md, pf, shift, ljs, wq[warp], lane, Fii);
+  // grid-stride over ions: a grid smaller than one warp per ion keeps part of every SM free for the
+  // kernels on the critical path that run beside this pass
+  for (int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + warp; p < ni; p += (int64_t)gridDim.x * kWarpsPerBlock)
+    ion_ii_one<LJ>(p, ni, ions, nl, md, pf, shift, ljs, wq[warp], lane, Fii);
 }
 
 bool ion_forces_split(const srbe_ctx *c, bool energies) {
@@ -1655,10 +1657,22 @@ void ion_forces_ii(srbe_ctx *c) {
   float4 *fii = c->fii.ensure((size_t)c->ni);
   const ListsDev L = lists_dev(c);
   const int64_t n = c->ni;
+  // A pass of up to about one wave (8 blocks per SM) runs beside b, the charge solve and S2 and has
+  // slack until the main-stream force pass: its grid is capped at 3 blocks per SM (a grid-stride loop
+  // over ions), which leaves room on every SM for those critical-path kernels (11,072-site slab: b
+  // 26 -> 17 us in the step, the pass 33 -> 45 us, the step about 1 % faster; 1 or 2 blocks per SM
+  // make the pass the longer branch).  Larger passes are on the critical path and keep their grid.
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    SRBE_CUDA(cudaGetDevice(&dev));
+    SRBE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const unsigned nblk = f.nblk <= (unsigned)(8 * nsm) ? std::min<unsigned>(f.nblk, (unsigned)(3 * nsm)) : f.nblk;
   if (c->have_md && f.md.ntype)
-    k_ion_ii<true><<<f.nblk, kGatherThreads, 0, c->side>>>(n, f.ions, L, f.md, f.pf, fii);
+    k_ion_ii<true><<<nblk, kGatherThreads, 0, c->side>>>(n, f.ions, L, f.md, f.pf, fii);
   else
-    k_ion_ii<false><<<f.nblk, kGatherThreads, 0, c->side>>>(n, f.ions, L, f.md, f.pf, fii);
+    k_ion_ii<false><<<nblk, kGatherThreads, 0, c->side>>>(n, f.ions, L, f.md, f.pf, fii);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
   SRBE_CUDA(cudaEventRecord(c->ev_ii, c->side));

@@ -363,6 +363,7 @@ static double host_dot(const std::vector<double> &a, const std::vector<double> &
 
 void build_A_and_inverse(srbe_ctx *c) {
   const int64_t ne = c->ne;
+  c->pcg.a32_ready = false;          // the mixed form's FP32 copy of A follows the new A
   const double Lx = c->L[0], Ly = c->L[1], Lz = c->L[2];
   // alpha_A: in-plane-only real-space images are exact only if erfc(alpha_A * gap) is negligible
   double zmin = 1e300, zmax = -1e300;
@@ -521,6 +522,9 @@ struct PcgArgs {
   int *stats;        // [0] iterations, [1] 1 if stopped at maxit above the tolerance (arms the fallback)
   double *res;       // [0] final relative residual (recomputed)
   int *status;       // the context's host-mapped error flags
+  // mixed form (k_pcg_mixed): FP32 A and inner vectors
+  const float *A32;
+  float *r32, *z32, *p32, *Ap32, *d32;
 };
 
 __device__ double grid_dot_sum(const PcgArgs &a, double mine, int slot, cg::grid_group &grid) {
@@ -641,15 +645,166 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   }
 }
 
+// out = A32 x in FP32 (warp per row, 16-byte loads when n is a multiple of 4)
+__device__ void grid_gemv32(const PcgArgs &a, const float *x, float *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = gw; row < a.n; row += nw) {
+    const float *Ar = a.A32 + row * a.n;
+    float acc = 0.f;
+    if ((a.n & 3) == 0) {
+      const float4 *A4 = reinterpret_cast<const float4 *>(Ar);
+      const float4 *x4 = reinterpret_cast<const float4 *>(x);
+      for (int64_t j = lane; j < (a.n >> 2); j += 32) {
+        const float4 m = __ldcs(A4 + j), v = __ldcg(x4 + j);
+        acc = fmaf(m.x, v.x, fmaf(m.y, v.y, fmaf(m.z, v.z, fmaf(m.w, v.w, acc))));
+      }
+    } else {
+      for (int64_t j = lane; j < a.n; j += 32) acc = fmaf(__ldcs(Ar + j), __ldcg(x + j), acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[row] = acc;
+  }
+}
+
+// The mixed form's iterative solve: iterative refinement in FP64 around Jacobi-PCG in FP32.  Each
+// outer pass forms the FP64 residual r = dpsi d + b - A y with A in FP64 and stops once
+// ||r|| <= tol ||dpsi d + b||; otherwise it solves A delta = r with PCG on an FP32 copy of A (half the
+// bytes per matrix-vector product; dot products summed in FP64) until the inner residual has fallen
+// by 1e-4, and adds delta to y in FP64.  maxit bounds the inner iterations over all passes; the
+// iteration count reported is theirs.  Q and psi_bar follow from Eqs. 9-10 as in k_pcg.
+__global__ void __launch_bounds__(256, 1) k_pcg_mixed(PcgArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+  int slot = 0;
+  double vv = 0.0;
+  for (int64_t i = gt; i < a.n; i += gs) {
+    const double v = fma(a.dpsi, a.d[i], a.b[i]);
+    a.p[i] = v;
+    vv += v * v;
+  }
+  vv = grid_dot_sum(a, vv, slot, grid);
+    slot = (slot + 1) & 7;            // its grid barrier also orders the writes of p before the products below
+  int it = 0;
+  bool converged = false;
+  for (int outer = 0; outer < 16; ++outer) {
+    grid_gemv(a, a.y, a.p, a.r, true);
+    grid.sync();
+    double rr = 0.0;
+    for (int64_t i = gt; i < a.n; i += gs) rr += a.r[i] * a.r[i];
+    rr = grid_dot_sum(a, rr, slot, grid);
+    slot = (slot + 1) & 7;
+    if (rr <= a.tol2 * vv) {
+      converged = true;
+      break;
+    }
+    if (it >= a.maxit) break;
+    // inner FP32 PCG on A delta = r
+    double rz = 0.0;
+    for (int64_t i = gt; i < a.n; i += gs) {
+      const float ri = (float)a.r[i], zi = (float)a.dinv[i] * ri;
+      a.r32[i] = ri;
+      a.z32[i] = zi;
+      a.p32[i] = zi;
+      a.d32[i] = 0.f;
+      rz += (double)ri * (double)zi;
+    }
+    rz = grid_dot_sum(a, rz, slot, grid);
+    slot = (slot + 1) & 7;
+    const double stop = 1e-8 * rr;          // inner residual 1e-4 of the outer one
+    double rr32 = rr;
+    while (it < a.maxit && rr32 > stop) {
+      grid_gemv32(a, a.p32, a.Ap32);
+      grid.sync();
+      double pap = 0.0;
+      for (int64_t i = gt; i < a.n; i += gs) pap += (double)a.p32[i] * (double)a.Ap32[i];
+      pap = grid_dot_sum(a, pap, slot, grid);
+    slot = (slot + 1) & 7;
+      const float alpha = (float)(rz / pap);
+      double rz1 = 0.0, rr1 = 0.0;
+      for (int64_t i = gt; i < a.n; i += gs) {
+        a.d32[i] = fmaf(alpha, a.p32[i], a.d32[i]);
+        const float ri = fmaf(-alpha, a.Ap32[i], a.r32[i]);
+        a.r32[i] = ri;
+        const float zi = (float)a.dinv[i] * ri;
+        a.z32[i] = zi;
+        rz1 += (double)ri * (double)zi;
+        rr1 += (double)ri * (double)ri;
+      }
+      rz1 = grid_dot_sum(a, rz1, slot, grid);
+    slot = (slot + 1) & 7;
+      rr32 = grid_dot_sum(a, rr1, slot, grid);
+    slot = (slot + 1) & 7;
+      const float beta = (float)(rz1 / rz);
+      rz = rz1;
+      for (int64_t i = gt; i < a.n; i += gs) a.p32[i] = fmaf(beta, a.p32[i], a.z32[i]);
+      grid.sync();
+      ++it;
+    }
+    for (int64_t i = gt; i < a.n; i += gs) a.y[i] += (double)a.d32[i];
+    grid.sync();
+  }
+  // true residual, neutrality projection and psi_bar (Eqs. 9-10)
+  grid_gemv(a, a.y, a.p, a.r, true);
+  grid.sync();
+  double r2 = 0.0, ey = 0.0;
+  for (int64_t i = gt; i < a.n; i += gs) {
+    r2 += a.r[i] * a.r[i];
+    ey += a.y[i];
+  }
+  r2 = grid_dot_sum(a, r2, slot, grid);
+    slot = (slot + 1) & 7;
+  ey = grid_dot_sum(a, ey, slot, grid);
+    slot = (slot + 1) & 7;
+  const double psi = -ey / a.s_e;
+  for (int64_t i = gt; i < a.n; i += gs) {
+    const double q = fma(psi, a.we[i], a.y[i]);
+    a.Q[i] = q;
+    a.Q32[i] = (float)q;
+  }
+  if (gt == 0) {
+    a.scal[kScalPsi] = psi;
+    a.stats[0] = it;
+    a.res[0] = sqrt(r2 / vv);
+    const int failed = converged || r2 <= a.tol2 * vv ? 0 : 1;
+    a.stats[1] = failed;
+    if (failed) *(volatile int *)(a.status + kStatNotConv) = 1;
+  }
+}
+
+__global__ void k_to_float_n(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
 void charge_update_pcg(srbe_ctx *c) {
   const int64_t n = c->ne;
+  const bool mixed = c->precision == SRBE_MIXED;
   static int blocks_per_sm = 0, nsm = 0;
   if (!blocks_per_sm) {
-    int dev = 0;
+    int dev = 0, b1 = 0, b2 = 0;
     SRBE_CUDA(cudaGetDevice(&dev));
     SRBE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    SRBE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pcg, 256, 0));
+    SRBE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pcg, 256, 0));
+    SRBE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_pcg_mixed, 256, 0));
+    blocks_per_sm = std::min(b1, b2);
     SRBE_REQUIRE(blocks_per_sm > 0, SRBE_ECUDA, "PCG kernel cannot be resident");
+  }
+  if (mixed && !c->pcg.a32_ready) {
+    // the FP32 copy of A, formed once per electrode (outside any capture: the first pass after a
+    // state change runs the ordinary way)
+    float *A32 = c->pcg.A32.ensure((size_t)n * n);
+    k_to_float_n<<<std::min<unsigned>(blocks_for(n * n, 256), 4096u), 256, 0, c->stream>>>(n * n, c->Amat.p, A32);
+    c->pcg.r32.ensure(n);
+    c->pcg.z32.ensure(n);
+    c->pcg.p32.ensure(n);
+    c->pcg.Ap32.ensure(n);
+    c->pcg.d32.ensure(n);
+    c->launches++;
+    SRBE_CUDA(cudaGetLastError());
+    c->pcg.a32_ready = true;
   }
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n * 32 + 255) / 256, (int64_t)blocks_per_sm * nsm));
   PcgArgs a;
@@ -669,6 +824,12 @@ void charge_update_pcg(srbe_ctx *c) {
   a.p = c->pcg.p.p;
   a.Ap = c->pcg.Ap.p;
   a.part = c->pcg.part.ensure((size_t)grid * 10);
+  a.A32 = c->pcg.A32.p;
+  a.r32 = c->pcg.r32.p;
+  a.z32 = c->pcg.z32.p;
+  a.p32 = c->pcg.p32.p;
+  a.Ap32 = c->pcg.Ap32.p;
+  a.d32 = c->pcg.d32.p;
   a.Q = c->Q.p;
   a.Q32 = c->Q32.p;
   a.scal = c->scal.p;
@@ -677,7 +838,8 @@ void charge_update_pcg(srbe_ctx *c) {
   a.status = c->d_status;
   void *args[] = {&a};
   coop_before(c);
-  SRBE_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg, dim3(grid), dim3(256), args, 0, c->stream));
+  SRBE_CUDA(cudaLaunchCooperativeKernel(mixed ? (const void *)k_pcg_mixed : (const void *)k_pcg, dim3(grid), dim3(256),
+                                        args, 0, c->stream));
   coop_after(c);
   c->launches++;
 }
@@ -689,6 +851,7 @@ __global__ void k_diag_inv(int64_t n, const double *__restrict__ A, double *__re
 
 void pcg_prepare(srbe_ctx *c) {
   const int64_t n = c->ne;
+  c->pcg.a32_ready = false;
   c->pcg.dinv.ensure(n);
   c->pcg.y.ensure(n);
   c->pcg.r.ensure(n);

@@ -113,6 +113,9 @@ struct PcgState {
   int warm = 0;                      // 0 zero, 1 previous solution, 2 learned model
   DevBuf<double> dinv, y, r, z, p, Ap, part, res;
   DevBuf<int> stats;
+  // mixed form: FP32 copy of A and FP32 vectors of the inner iteration (iterative refinement)
+  DevBuf<float> A32, r32, z32, p32, Ap32, d32;
+  bool a32_ready = false;
 };
 
 // Learned warm start: MLP parameters, AdamW moments, scratch
@@ -220,6 +223,7 @@ struct srbe_ctx {
   // electrolyte
   int64_t ni = 0;
   srbe::DevBuf<double> x, y, z, q;
+  srbe::DevBuf<float> q32;                     // FP32 copy of q (the mixed form's structure factor)
   srbe::DevBuf<double> vx, vy, vz, minv;
   srbe::DevBuf<double> F;                      // [3][ni] SoA force
   srbe::DevBuf<int32_t> itype, mol;
@@ -397,7 +401,8 @@ void neighbor_force_rebuild(srbe_ctx *c);
 // (c Im S, c Re S) for the ion forces, into ctx->coef / coef32.  u: the particles' fixed-point phase
 // coordinates [3][n] if already known (else they come from x, y, z); z is read for M_z either way
 void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *w,
-                      double2 *S, const double2 *S_add, int mslot, int coef_mode, const uint64_t *u = nullptr);
+                      double2 *S, const double2 *S_add, int mslot, int coef_mode, const uint64_t *u = nullptr,
+                      const float *w32 = nullptr);
 void electrode_rhs(srbe_ctx *c);
 void charge_update(srbe_ctx *c);
 void pcg_prepare(srbe_ctx *c);

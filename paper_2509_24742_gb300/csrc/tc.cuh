@@ -110,5 +110,21 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+// eight consecutive K values of one row (k0 a multiple of 8) split into BF16 (hi, lo) and stored as
+// two 16-byte chunks: the row's contiguous 16 bytes of the blocked layout in each operand
+__device__ __forceinline__ void store8_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int r, int k0, const float *v) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __nv_bfloat16 h0, l0, h1, l1;
+    split_bf16(v[2 * q], h0, l0);
+    split_bf16(v[2 * q + 1], h1, l1);
+    h[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    l[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+  }
+  *reinterpret_cast<uint4 *>(hi + off(r, k0)) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4 *>(lo + off(r, k0)) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 }  // namespace tc
 }  // namespace srbe

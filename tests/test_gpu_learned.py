@@ -39,6 +39,32 @@ def test_pcg_reaches_direct_and_oracle_charges(orc, slab):
     assert rel(F1, F0) < 1e-9
 
 
+@pytest.mark.parametrize("tol", [1e-8, 1e-11])
+def test_mixed_pcg_refinement_reaches_oracle_charges(orc, slab, tol):
+    """The mixed form's PCG (FP64 iterative refinement around FP32 Jacobi-PCG) meets the FP64 residual
+    bar and gives the oracle's Cholesky charges to the accuracy that residual allows."""
+    samples = orc.sample_metropolis(slab.box, slab.alpha, slab.M, slab.P, 3001, 0)
+    ref = orc.System(slab, alpha_A=ALPHA_A)
+    m, c = ref.modes(samples)
+    ev = ref.evaluate(m, c, with_lj=False)
+    with srbe.from_slab(slab, precision=srbe.MIXED, alpha_A=ALPHA_A) as ctx:
+        ctx.set_k(samples)
+        Q0, psi0, b0 = ctx.solve_charges()
+        ctx.set_solver(srbe.PCG, tol=tol, maxit=5000, warm=srbe.WARM_ZERO)
+        Q1, psi1, b1 = ctx.solve_charges()
+        it, res = ctx.solver_stats()
+        res64 = ctx.charge_residual()
+    print("mixed PCG to %.0e: %d inner FP32 iterations, relative residual %.2e (FP64 check %.2e)"
+          % (tol, it, res, res64))
+    assert res <= tol and res64 <= 10 * tol and it > 0
+    # against the oracle's solve of the same right-hand side: the accuracy the residual allows
+    Q_ref, _ = orc.cp_solve(ref.factor, slab.side, slab.dpsi, b1 * srbe.VOLT)
+    assert rel(Q1, Q_ref) < 1e3 * tol
+    # against the oracle's own evaluation: the mixed form's b carries FP32 rounding (~1e-6), the
+    # form's charge bar
+    assert rel(Q1, ev["Q"]) < 1e-5
+
+
 def test_descriptors_match_oracle(slab):
     with srbe.from_slab(slab, alpha_A=ALPHA_A) as ctx:
         ctx.sample_k(1, 0)
