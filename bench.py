@@ -863,10 +863,21 @@ def oneshot_arm(args):
 
 
 # ---------------------------------------------------------------------------------------------- CPU oracle
-def oracle_steps(budget_s, max_steps, min_steps=2, warmup=0):
+def _omp_threads(n):
+    """Sets the OpenMP thread count of the oracle's parallel loops (None: leave it)."""
+    import ctypes
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+        return True
+    except OSError:
+        return False
+
+
+def oracle_steps(budget_s, max_steps, min_steps=2, warmup=0, one_core_budget_s=0.0):
     """Full oracle MD steps (plain FP64 C, OpenMP over independent output elements) on the same
     workload after `warmup` untimed ones; the one-time A build is not timed.  Returns (steps,
-    seconds, threads)."""
+    seconds, threads) and, with one_core_budget_s > 0, (steps, seconds) of further steps with the
+    oracle's loops on one thread."""
     from oracle import oracle
     from paper_2509_24742_gb300 import workloads
     slab = workloads.md_11072()
@@ -890,13 +901,30 @@ def oracle_steps(budget_s, max_steps, min_steps=2, warmup=0):
         step += 1
         F, r, v = one(F, r, v, step)
         n += 1
-    return n, time.perf_counter() - t0, int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = (n, time.perf_counter() - t0, int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)))
+    if one_core_budget_s > 0 and _omp_threads(1):
+        t1 = time.perf_counter()
+        n1 = 0
+        while n1 < 1 or time.perf_counter() - t1 < one_core_budget_s:
+            step += 1
+            F, r, v = one(F, r, v, step)
+            n1 += 1
+        one_core = (n1, time.perf_counter() - t1)
+        _omp_threads(out[2])
+        return out + (one_core,)
+    return out
 
 
 def cpu_baseline():
-    n, t, cores = oracle_steps(budget_s=12.0, max_steps=50)
-    return {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d full oracle MD steps of the same workload (A built once, untimed)" % n}
+    res = oracle_steps(budget_s=12.0, max_steps=50, one_core_budget_s=8.0)
+    n, t, cores = res[:3]
+    out = {"value": n / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d full oracle MD steps of the same workload (A built once, untimed)" % n}
+    if len(res) > 3:
+        n1, t1 = res[3]
+        out["one_core"] = {"value": n1 / t1, "unit": UNIT, "cores": 1,
+                           "sample": "%d further steps with the oracle's OpenMP loops on one thread" % n1}
+    return out
 
 
 def reference_arm(args, rank, world):

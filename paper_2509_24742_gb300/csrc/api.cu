@@ -261,6 +261,13 @@ __global__ void k_site_turns(int64_t n, const double *__restrict__ x, const doub
   u[2 * n + i] = to_turns64(z[i], invL.z);
 }
 
+// FP32 copies of the fixed site positions (the mixed form's b), site order
+__global__ void k_site_f4(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                          const double *__restrict__ z, float4 *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float4((float)x[i], (float)y[i], (float)z[i], 0.f);
+}
+
 // y = Q - psi_bar A^-1 e (inverse of Q = y + psi_bar A^-1 e, Eq. 10)
 __global__ void k_unproject(int64_t n, const double *__restrict__ Q, const double *__restrict__ we,
                             const double *__restrict__ scal, double *__restrict__ y) {
@@ -368,6 +375,11 @@ struct srbe::HostExt {
   int io_K = -1;
   int64_t io_kernels = 0;
   uint64_t io_calls = 0;
+  // the next call's mode list, sampled (and written to the other slot) while the GPU runs this one
+  bool io_pre = false;
+  uint64_t io_pre_seed = 0, io_pre_step = 0;
+  std::vector<int32_t> io_pre_hm, io_pre_samp;
+  std::vector<double> io_pre_hc;
   void drop_io_graphs() {
     for (auto &g : io_exec)
       if (g) {
@@ -1315,6 +1327,8 @@ int srbe_set_electrode(srbe_ctx *c, int64_t n_ele, const double *R, const int8_t
                                                                make_double3(1.0 / c->L[0], 1.0 / c->L[1],
                                                                             1.0 / c->L[2]),
                                                                c->eu.p);
+    k_site_f4<<<blocks_for(n_ele, 256), 256, 0, c->stream>>>(n_ele, c->ex.p, c->ey.p, c->ez.p,
+                                                            c->epf.ensure((size_t)n_ele));
     SRBE_CUDA(cudaGetLastError());
     lattice_setup(c, x, y, z);
     build_A_and_inverse(c);
@@ -1674,14 +1688,24 @@ int srbe_forces_host_io(srbe_ctx *c, uint64_t seed, uint64_t step, double *psi_b
     SRBE_REQUIRE(c->have_ele && c->have_pos, SRBE_ESTATE, "electrode and positions (charges) are required");
     report_status(c);                  // flags of earlier asynchronous calls
     const int slot = (int)(e->io_calls++ & 1);
-    build_host_list(c, seed, step);
+    // the list presampled by the previous call sits in this slot already when it is this step's
+    const bool pre = e->io_pre && e->io_pre_seed == seed && e->io_pre_step == step && !c->explicit_list &&
+                     e->io_epoch == e->epoch && e->io_K == c->K && e->slot_cap >= c->K;
+    e->io_pre = false;
+    if (pre) {
+      c->hm.swap(e->io_pre_hm);
+      c->hc.swap(e->io_pre_hc);
+      c->hsamp.swap(e->io_pre_samp);
+    } else {
+      build_host_list(c, seed, step);
+    }
     if (!c->have_modes || (int)c->hc.size() != c->K) {
       upload_modes(c);                 // a new mode count: sizes the mode buffers (and recaptures)
       c->have_modes = true;
     }
     reserve(c);
     ensure_slot_buffers(c);
-    fill_slot(c, slot);
+    if (!pre) fill_slot(c, slot);
     if (e->io_epoch != e->epoch || e->io_K != c->K || !e->io_exec[slot]) {
       // the first pass after a state change runs the ordinary way (it sizes every buffer), then the
       // pass is captured for the following calls
@@ -1700,6 +1724,23 @@ int srbe_forces_host_io(srbe_ctx *c, uint64_t seed, uint64_t step, double *psi_b
       c->launches += e->io_kernels;
     }
     SRBE_CUDA(cudaEventRecord(e->slot[slot].done, c->stream));
+    if (e->io_exec[1 - slot] && e->io_epoch == e->epoch && !c->explicit_list) {
+      // while the GPU runs: sample step + 1 into the other slot (its last pass has finished), keeping
+      // this step's host list as the context's
+      e->io_pre_hm = c->hm;
+      e->io_pre_hc = c->hc;
+      e->io_pre_samp = c->hsamp;
+      build_host_list(c, seed, step + 1);
+      if ((int)c->hc.size() == c->K) {
+        fill_slot(c, 1 - slot);
+        e->io_pre = true;
+        e->io_pre_seed = seed;
+        e->io_pre_step = step + 1;
+      }
+      c->hm.swap(e->io_pre_hm);
+      c->hc.swap(e->io_pre_hc);
+      c->hsamp.swap(e->io_pre_samp);
+    }
     SRBE_CUDA(cudaStreamSynchronize(c->stream));
     e->forces_valid = true;
     if (psi_bar) *psi_bar = *(volatile double *)e->io_psi / kVolt;

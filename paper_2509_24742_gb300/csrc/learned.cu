@@ -114,8 +114,8 @@ k_descriptors(int64_t ne, const double *__restrict__ ex, const double *__restric
 // kind::f16 MMAs into tensor memory with FP32 accumulation.  Every operand is split into BF16
 // (hi, lo) and each product taken as hi hi + hi lo + lo hi, which keeps about 16 significand bits
 // (the scalar FP32 path keeps 24; the difference stays below 1e-5 of the output here).  One CTA of
-// four warps per SM, persistent over tiles; thread t owns row t of the tile (tensor-memory lane t)
-// for the bias + SiLU epilogues, and thread 0 issues the MMAs.
+// 16 warps per SM, persistent over tiles; in the bias + SiLU epilogues the four warps of a
+// tensor-memory lane quarter split the 128 columns of their 32 rows, and thread 0 issues the MMAs.
 // ------------------------------------------------------------------------------------------------
 constexpr int kTcK1 = kIn / tc::kKstep;    // 5 K steps of layer 1
 constexpr int kTcK2 = kH / tc::kKstep;     // 8 K steps of layer 2
@@ -123,7 +123,10 @@ constexpr size_t kTcSmem = (size_t)(2 * kTcK1 + 2 * kTcK2) * 2 * tc::kBlockBytes
 constexpr int kTcPolls = 1 << 20;          // bounded mbarrier waits
 static_assert(kIn % tc::kKstep == 0 && kH == tc::kRows, "MLP sizes must match the MMA tiles");
 
-__global__ void __launch_bounds__(128, 1)
+constexpr int kTcThreads = 512;            // 16 warps: 4 per tensor-memory lane quarter
+constexpr int kTcGroups = kTcThreads / 128; // column groups of 32 per row in the epilogues
+
+__global__ void __launch_bounds__(kTcThreads, 1)
 k_mlp_forward_tc(int64_t n, const float *__restrict__ D, const float *__restrict__ P, float *__restrict__ out,
                  double *__restrict__ out_y, int *__restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -133,20 +136,25 @@ k_mlp_forward_tc(int64_t n, const float *__restrict__ D, const float *__restrict
   __nv_bfloat16 *xl = xh + kTcK1 * tc::kBlockElems, *hh = xl + kTcK1 * tc::kBlockElems;
   __nv_bfloat16 *hl = hh + kTcK2 * tc::kBlockElems;
   __shared__ float sb1[kH], sb2[kH], sw3[kH], sxm[kIn], sxs[kIn];
+  __shared__ float part[kTcGroups][128];       // the output's partial dot products per column group
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tbase;
-  const int t = threadIdx.x, warp = t >> 5;
-  for (int i = t; i < kH * kIn; i += 128) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows of the tile) and columns 32 (w / 4) .. + 31
+  const int quarter = warp & 3, grp = warp >> 2, row_t = 32 * quarter + lane, c0 = 32 * grp;
+  for (int i = t; i < kH * kIn; i += kTcThreads) {
     const int h = i / kIn, k = i - h * kIn;
     tc::split_bf16(P[oW1 + i], w1h[tc::off(h, k)], w1l[tc::off(h, k)]);
   }
-  for (int i = t; i < kH * kH; i += 128) {
+  for (int i = t; i < kH * kH; i += kTcThreads) {
     const int h = i / kH, k = i - h * kH;
     tc::split_bf16(P[oW2 + i], w2h[tc::off(h, k)], w2l[tc::off(h, k)]);
   }
-  sb1[t] = P[oB1 + t];
-  sb2[t] = P[oB2 + t];
-  sw3[t] = P[oW3 + t];
+  if (t < kH) {
+    sb1[t] = P[oB1 + t];
+    sb2[t] = P[oB2 + t];
+    sw3[t] = P[oW3 + t];
+  }
   if (t < kIn) {
     sxm[t] = P[oXm + t];
     sxs[t] = P[oXs + t];
@@ -158,32 +166,25 @@ k_mlp_forward_tc(int64_t n, const float *__restrict__ D, const float *__restrict
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t d1 = tbase, d2 = tbase + 128, lanes = (uint32_t)(32 * warp) << 16;
+  const uint32_t d1 = tbase, d2 = tbase + 128, lanes = (uint32_t)(32 * quarter) << 16;
   const uint32_t idesc = tc::idesc_bf16(128, 128);
   const int64_t ntiles = (n + 127) / 128;
   uint32_t phase = 0;
   bool fail = false;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t row0 = tile * 128;
-    // standardised inputs of the tile, thread t loading its own row (rows beyond n are zero): 16-byte
-    // loads of the row, 16-byte stores of each 8-wide chunk of both operands
+    // standardised inputs of the tile (rows beyond n are zero): row row_t, 8-wide chunks grp,
+    // grp + 4, grp + 8 (16-byte loads and stores)
     {
-      const bool live = row0 + t < n;
-      const float4 *src = reinterpret_cast<const float4 *>(D + (row0 + t) * kIn);
+      const bool live = row0 + row_t < n;
+      const float4 *src = reinterpret_cast<const float4 *>(D + (row0 + row_t) * kIn);
+      for (int ch = grp; ch < kIn / 8; ch += kTcGroups) {
+        const float4 q0 = live ? __ldg(src + 2 * ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 q1 = live ? __ldg(src + 2 * ch + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        float4 q[kIn / 8];
-#pragma unroll
-        for (int u = 0; u < kIn / 8; ++u) q[u] = live ? __ldg(src + half * (kIn / 8) + u) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int g = 0; g < kIn / 16; ++g) {
-          const int k0 = half * (kIn / 2) + 8 * g;
-          float v[8] = {q[2 * g].x, q[2 * g].y, q[2 * g].z, q[2 * g].w,
-                        q[2 * g + 1].x, q[2 * g + 1].y, q[2 * g + 1].z, q[2 * g + 1].w};
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = live ? (v[j] - sxm[k0 + j]) / sxs[k0 + j] : 0.f;
-          tc::store8_split(xh, xl, t, k0, v);
-        }
+        for (int j = 0; j < 8; ++j) v[j] = live ? (v[j] - sxm[8 * ch + j]) / sxs[8 * ch + j] : 0.f;
+        tc::store8_split(xh, xl, row_t, 8 * ch, v);
       }
     }
     tc::fence_async_smem();
@@ -204,14 +205,14 @@ k_mlp_forward_tc(int64_t n, const float *__restrict__ D, const float *__restrict
     if (fail) break;
     phase ^= 1u;
     tc::fence_after_sync();
-    // H1 = SiLU(Z1 + b1), row t, split into the layer-2 operand
-    for (int c0 = 0; c0 < kH; c0 += 32) {
+    // H1 = SiLU(Z1 + b1) for row row_t, columns c0 .. c0 + 31, split into the layer-2 operand
+    {
       float v[32];
       tc::ld32(d1 + lanes + (uint32_t)c0, v);
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = silu(v[j] + sb1[c0 + j]);
 #pragma unroll
-      for (int g = 0; g < 4; ++g) tc::store8_split(hh, hl, t, c0 + 8 * g, v + 8 * g);
+      for (int g = 0; g < 4; ++g) tc::store8_split(hh, hl, row_t, c0 + 8 * g, v + 8 * g);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -231,20 +232,27 @@ k_mlp_forward_tc(int64_t n, const float *__restrict__ D, const float *__restrict
     if (fail) break;
     phase ^= 1u;
     tc::fence_after_sync();
-    // output = W3 . SiLU(Z2 + b2) + b3, de-standardised
-    float acc = 0.f;
-    for (int c0 = 0; c0 < kH; c0 += 32) {
+    // output = W3 . SiLU(Z2 + b2) + b3: partial sums per column group, added in group order
+    {
       float v[32];
       tc::ld32(d2 + lanes + (uint32_t)c0, v);
+      float acc = 0.f;
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc = fmaf(sw3[c0 + j], silu(v[j] + sb2[c0 + j]), acc);
+      part[grp][row_t] = acc;
     }
     tc::fence_before_sync();
-    const int64_t row = row0 + t;
-    if (row < n) {
-      const float y = (acc + b3) * ys + ym;
-      if (out) out[row] = y;
-      if (out_y) out_y[row] = (double)y;
+    __syncthreads();
+    if (t < 128) {
+      float acc = part[0][t];
+#pragma unroll
+      for (int g = 1; g < kTcGroups; ++g) acc += part[g][t];
+      const int64_t row = row0 + t;
+      if (row < n) {
+        const float y = (acc + b3) * ys + ym;
+        if (out) out[row] = y;
+        if (out_y) out_y[row] = (double)y;
+      }
     }
   }
   if (fail) {
@@ -361,7 +369,7 @@ void mlp_forward(srbe_ctx *c, const float *D_dev, int64_t n, float *out_dev, dou
     SRBE_CUDA(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
   }
   const unsigned grid = (unsigned)std::min<int64_t>((n + 127) / 128, nsm);
-  k_mlp_forward_tc<<<grid, 128, kTcSmem, c->stream>>>(n, D_dev, c->mlp.P.p, out_dev, out_y_dev, c->d_status);
+  k_mlp_forward_tc<<<grid, kTcThreads, kTcSmem, c->stream>>>(n, D_dev, c->mlp.P.p, out_dev, out_y_dev, c->d_status);
   c->launches++;
   SRBE_CUDA(cudaGetLastError());
 }

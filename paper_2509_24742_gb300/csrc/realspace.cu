@@ -724,6 +724,11 @@ __device__ __forceinline__ void ei_list_f32(const PairSite &S, const CellsDev &i
   }
 }
 
+// the FP32 copies of the scalar parameters the mixed form needs (converted once on the host)
+struct ForceF32 {
+  float Lx, Ly, alpha, eta, rc, slab, kb;
+};
+
 // Verlet-list view handed to the gathers
 struct ListsDev {
   const int32_t *ii, *ie, *ei, *ii_n, *ie_n, *ei_n, *cell_s, *ecell;
@@ -741,12 +746,15 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
                 const double2 *__restrict__ coefS, const float2 *__restrict__ coefS32,
                 const double2 *__restrict__ tab, double3 invL, CellsDev ions, ListsDev nl,
                 double Lx, double Ly, double alpha, double eta, double rc, double slab, const double *__restrict__ scal,
-                double *__restrict__ b, float2 *__restrict__ bsplit, const double *__restrict__ bfar) {
+                double *__restrict__ b, float2 *__restrict__ bsplit, const double *__restrict__ bfar,
+                const float4 *__restrict__ epf, ForceF32 pf) {
   __shared__ int2 wq[kWarpsPerBlock][64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t j = ((int64_t)blockIdx.x * kGatherThreads + threadIdx.x) >> 5;
   if (j >= ne) return;                        // whole warps leave together; no block barrier below
-  const double X = ex[j], Y = ey[j], Z = ez[j];
+  // the mixed form takes the site and the scalars in FP32 (no FP64 conversion per lane)
+  const double X = F32 ? 0.0 : ex[j], Y = F32 ? 0.0 : ey[j], Z = F32 ? 0.0 : ez[j];
+  const float4 sf = F32 ? epf[j] : make_float4(0.f, 0.f, 0.f, 0.f);
   const uint64_t ux = eu[j], uy = eu[ne + j], uz = eu[2 * ne + j];
   double acc = 0.0;
   KahanF32 fk;
@@ -774,10 +782,16 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
   // candidates compacted through the warp queue
   PairSite S;
   S.X = X; S.Y = Y; S.Z = Z; S.qi = 0.0; S.Lx = Lx; S.Ly = Ly; S.alpha = alpha; S.eta = eta; S.rc2 = rc * rc;
-  S.Xf = (float)X; S.Yf = (float)Y; S.Zf = (float)Z; S.qf = 0.f;
-  S.Lxf = (float)Lx; S.Lyf = (float)Ly; S.af = (float)alpha; S.etaf = (float)eta;
+  if (F32) {
+    S.Xf = sf.x; S.Yf = sf.y; S.Zf = sf.z;
+    S.Lxf = pf.Lx; S.Lyf = pf.Ly; S.af = pf.alpha; S.etaf = pf.eta;
+  } else {
+    S.Xf = (float)X; S.Yf = (float)Y; S.Zf = (float)Z;
+    S.Lxf = (float)Lx; S.Lyf = (float)Ly; S.af = (float)alpha; S.etaf = (float)eta;
+  }
+  S.qf = 0.f;
   S.ti = 0; S.mi = -1; S.p = -1;
-  const float rcf = (float)rc;
+  const float rcf = F32 ? pf.rc : (float)rc;
   const float cut2 = F32 ? rcf * rcf : (rcf + kPrecheckMargin) * (rcf + kPrecheckMargin);
   KahanF32 fn;
   double near = 0.0;
@@ -807,7 +821,7 @@ k_electrode_rhs(int64_t ne, const double *__restrict__ ex, const double *__restr
     // FP32 to the end of the warp sum: on this GPU every FP64 warp instruction is costly
     const float accf = warp_sum_f(fk.valuef() + fn.valuef());
     if (lane == 0) {
-      const double bj = fma(-slab * Z, scal[kScalMion], (double)accf + (bfar ? bfar[j] : 0.0));
+      const double bj = fma(-slab * ez[j], scal[kScalMion], (double)accf + (bfar ? bfar[j] : 0.0));
       const float hi = (float)bj;
       b[j] = bj;
       bsplit[j] = make_float2(hi, (float)(bj - (double)hi));
@@ -1202,18 +1216,19 @@ void electrode_rhs(srbe_ctx *c) {
   const double slab = 4.0 * kPi / c->V;
   const CellsDev ions = cells_dev(c->icells, c->runtab);
   const unsigned nb = blocks_for(c->ne, kWarpsPerBlock);
+  const ForceF32 pf{(float)c->L[0], (float)c->L[1], (float)c->alpha, (float)c->eta, (float)c->rc, (float)slab, 0.f};
   if (c->precision == SRBE_MIXED)
     k_electrode_rhs<true><<<nb, kGatherThreads, 0, c->stream>>>(c->ne, c->ex.p, c->ey.p, c->ez.p, c->eu.p, K, c->dm.p,
                                                                coef,
                                                                c->coef32.p, c->tab.p, invL, ions, lists_dev(c), c->L[0], c->L[1], c->alpha,
                                                                c->eta, c->rc, slab, c->scal.p, c->bvec.p, c->bsplit.p,
-                                                               bfar);
+                                                               bfar, c->epf.p, pf);
   else
     k_electrode_rhs<false><<<nb, kGatherThreads, 0, c->stream>>>(c->ne, c->ex.p, c->ey.p, c->ez.p, c->eu.p, K, c->dm.p,
                                                                coef,
                                                                 c->coef32.p, c->tab.p, invL, ions, lists_dev(c), c->L[0], c->L[1], c->alpha,
                                                                 c->eta, c->rc, slab, c->scal.p, c->bvec.p, c->bsplit.p,
-                                                                bfar);
+                                                                bfar, c->epf.p, pf);
   c->launches++;
   if (!bfar) c->mode_evals += c->ne * (int64_t)K;
   SRBE_CUDA(cudaGetLastError());
@@ -1225,10 +1240,6 @@ void electrode_rhs(srbe_ctx *c) {
 
 // coefF[k] = (c_k Im S(k), c_k Re S(k)) with S = S1 + S2;
 // F_i = - q_i sum_k c_k k Im(S exp(-i k . r_i)) = - q_i sum_k k (cIm cos - cRe sin)   (Eq. 25)
-// the FP32 copies of the scalar parameters the mixed form needs (converted once on the host)
-struct ForceF32 {
-  float Lx, Ly, alpha, eta, rc, slab, kb;
-};
 
 // exact FP32 -> FP64 widening with integer instructions (FP64-pipe conversions are scarce on this
 // GPU): normal numbers re-biased, zeros kept; subnormal, infinite and NaN inputs take the conversion
@@ -1640,8 +1651,7 @@ k_ion_ii(int64_t ni, CellsDev ions, ListsDev nl, MdDev md, ForceF32 pf, float4 *
     }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // grid-stride over ions: a grid smaller than one warp per ion keeps part of every SM free for the
-  // kernels on the critical path that run beside this pass
+  // one warp per ion (a grid-stride loop, so any grid size covers every ion)
   for (int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + warp; p < ni; p += (int64_t)gridDim.x * kWarpsPerBlock)
     ion_ii_one<LJ>(p, ni, ions, nl, md, pf, shift, ljs, wq[warp], lane, Fii);
 }
@@ -1657,18 +1667,7 @@ void ion_forces_ii(srbe_ctx *c) {
   float4 *fii = c->fii.ensure((size_t)c->ni);
   const ListsDev L = lists_dev(c);
   const int64_t n = c->ni;
-  // A pass of up to about one wave (8 blocks per SM) runs beside b, the charge solve and S2 and has
-  // slack until the main-stream force pass: its grid is capped at 3 blocks per SM (a grid-stride loop
-  // over ions), which leaves room on every SM for those critical-path kernels (11,072-site slab: b
-  // 26 -> 17 us in the step, the pass 33 -> 45 us, the step about 1 % faster; 1 or 2 blocks per SM
-  // make the pass the longer branch).  Larger passes are on the critical path and keep their grid.
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
-    SRBE_CUDA(cudaGetDevice(&dev));
-    SRBE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  }
-  const unsigned nblk = f.nblk <= (unsigned)(8 * nsm) ? std::min<unsigned>(f.nblk, (unsigned)(3 * nsm)) : f.nblk;
+  const unsigned nblk = f.nblk;
   if (c->have_md && f.md.ntype)
     k_ion_ii<true><<<nblk, kGatherThreads, 0, c->side>>>(n, f.ions, L, f.md, f.pf, fii);
   else

@@ -202,6 +202,7 @@ struct srbe_ctx {
   int64_t ne = 0;
   srbe::DevBuf<double> ex, ey, ez, ed;         // positions and d (-1/2 | +1/2)
   srbe::DevBuf<uint64_t> eu;                   // fixed-point phase coordinates [3][ne], site order
+  srbe::DevBuf<float4> epf;                    // FP32 site positions (x, y, z, 0), site order
   srbe::DevBuf<uint64_t> iu;                   // ion phase coordinates [3][ni] written by the drift of a step
   srbe::DevBuf<double> Bmat;                   // projected inverse J A^-1, ne x ne row-major
   srbe::DevBuf<float2> Bsplit;                 // its (hi, lo) FP32 split (mixed form)
