@@ -553,7 +553,7 @@ void reserve(srbe_ctx *c) {
   nb.yb.ensure(nn);
   nb.pfb.ensure(nn);
   nb.cell_s.ensure(nn);
-  nb.flag.ensure(2);
+  nb.flag.ensure(3);
   if (c->lat.nl > 0) c->lat.E.ensure((size_t)K * c->lat.nl);
 }
 

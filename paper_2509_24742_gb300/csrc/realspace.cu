@@ -999,8 +999,9 @@ __global__ void __launch_bounds__(256) k_neighbor_update(NbrKernelArgs a) {
   if (tid == 0) s_rebuild = __ldcg(&a.flag[0]);
   __syncthreads();
   if (!s_rebuild) return;
-  // ---- phase 1: zero the cell counts
+  // ---- phase 1: zero the cell counts and the list-task counter
   for (int64_t c = gtid; c <= a.ncell; c += gsize) a.start[c] = 0;
+  if (gtid == 0) a.flag[2] = 0;
   grid.sync();
   // ---- phase 2: count
   for (int64_t i = gtid; i < a.n; i += gsize) {
@@ -1084,14 +1085,21 @@ __global__ void __launch_bounds__(256) k_neighbor_update(NbrKernelArgs a) {
     a.cell_s[p] = a.cell[i];
   }
   grid.sync();
-  // ---- phase 7: the ion lists (ion-ion and ion-electrode) and the electrode-ion lists as one pool
-  // of tasks, warp per task, so that no warp takes more than ceil(tasks / warps) of them
-  for (int64_t t = gwarp; t < a.n + a.ne; t += nwarps) {
+  // ---- phase 7: the ion-ion, ion-electrode and electrode-ion lists as one pool of tasks (one list
+  // each), handed to warps through an atomic counter in that order, so that the warps finish together
+  // (a list's content does not depend on the warp that builds it)
+  (void)gwarp;
+  (void)nwarps;
+  const int64_t ntask = 2 * a.n + a.ne;
+  for (;;) {
+    int64_t t = 0;
+    if (lane == 0) t = atomicAdd(&a.flag[2], 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= ntask) break;
     if (t < a.n) {
       const int64_t p = t;
       const float4 me = a.pf[p];
-      const int cell = a.cell_s[p];
-      const int nii = build_list(a, a.runs, a.run_first, cell, a.start, a.pf, me.x, me.y, me.z, p,
+      const int nii = build_list(a, a.runs, a.run_first, a.cell_s[p], a.start, a.pf, me.x, me.y, me.z, p,
                                  a.ii + p * a.cap, lane, a.mol ? a.ms : nullptr, a.mol ? a.ms[p] : -1);
       // pad the ion-ion list to a whole number of 32-entry batches with entries that always lie beyond
       // the cutoff (the ion itself seven box lengths away in x and y), so that the mixed form's pass
@@ -1100,14 +1108,15 @@ __global__ void __launch_bounds__(256) k_neighbor_update(NbrKernelArgs a) {
         const int padded = min(a.cap, (nii + 31) & ~31);
         if (nii + lane < padded) a.ii[p * a.cap + nii + lane] = list_entry((int)p, 7, 7);
       }
-      const int nie = build_list(a, a.runs, a.run_first, cell, a.eles.start, a.eles.pf, me.x, me.y, me.z, -1,
+      if (lane == 0) a.ii_n[p] = nii;
+    } else if (t < 2 * a.n) {
+      const int64_t p = t - a.n;
+      const float4 me = a.pf[p];
+      const int nie = build_list(a, a.runs, a.run_first, a.cell_s[p], a.eles.start, a.eles.pf, me.x, me.y, me.z, -1,
                                  a.ie + p * a.cap, lane);
-      if (lane == 0) {
-        a.ii_n[p] = nii;
-        a.ie_n[p] = nie;
-      }
+      if (lane == 0) a.ie_n[p] = nie;
     } else {
-      const int64_t j = t - a.n;
+      const int64_t j = t - 2 * a.n;
       const int nei = build_list(a, a.runs, a.run_first, a.ecell[j], a.start, a.pf, (float)a.ex[j], (float)a.ey[j],
                                  (float)a.ez[j], -1, a.ei + j * a.cap, lane);
       if (lane == 0) a.ei_n[j] = nei;
@@ -1121,7 +1130,7 @@ __global__ void __launch_bounds__(256) k_neighbor_update(NbrKernelArgs a) {
 }
 
 void neighbor_force_rebuild(srbe_ctx *c) {
-  int *f = c->nbr.flag.ensure(2);
+  int *f = c->nbr.flag.ensure(3);
   const int one[2] = {1, 1};
   SRBE_CUDA(cudaMemcpyAsync(f, one, sizeof(one), cudaMemcpyHostToDevice, c->stream));
   SRBE_CUDA(cudaStreamSynchronize(c->stream));

@@ -101,7 +101,7 @@ struct NbrLists {
   DevBuf<double> xb, yb;             // sorted x, y at the last build (unwrapping reference)
   DevBuf<float4> pfb;                // sorted FP32 positions at the last build
   DevBuf<int32_t> cell_s;            // cell of each sorted ion at the last build
-  DevBuf<int> flag;                  // [0] rebuild needed, [1] forced by the host
+  DevBuf<int> flag;                  // [0] rebuild needed, [1] forced by the host, [2] list-task counter
   double skin = 0.1;
 };
 
