@@ -953,37 +953,54 @@ __device__ __forceinline__ int build_list(const NbrKernelArgs &a, const int4 *ru
 
 // Every step: the sorted copies follow the ions (unwrapped against the build positions, so the
 // lists' image shifts stay valid) and any ion that moved more than skin / 2 since the build raises
-// flag[0]; a forced rebuild (flag[1]) skips the refresh and raises flag[0] itself.
+// flag[0]; a forced rebuild (flag[1]) skips the refresh and raises flag[0] itself.  Four threads per
+// sorted ion, one per component (the fourth only completes the group): the FP64 unwrap and
+// fixed-point conversion of a component is a short chain, and three of them in parallel keep the
+// kernel short; the group sums its squared displacements with shuffles for the skin test.
 __global__ void __launch_bounds__(256) k_nbr_refresh(NbrKernelArgs a) {
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (__ldcg(&a.flag[1])) {
     if (gtid == 0) a.flag[0] = 1;
     return;
   }
-  {
-    const int64_t gsize = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = gtid; p < a.n; p += gsize) {
-      const int32_t i = a.order[p];
+  const int64_t p = gtid >> 2;
+  const int d = (int)(gtid & 3);
+  float e2 = 0.f;
+  if (p < a.n && d < 3) {
+    const int32_t i = a.order[p];
+    const float4 b = a.pfb[p];
+    float ed;
+    if (d < 2) {
       // displacement since the build position, back across the periodic wrap (it is far below
       // L / 2 unless the ion was wrapped, then within a skin of +-L): no FP64 division
-      double dx = a.x[i] - a.xb[p], dy = a.y[i] - a.yb[p];
-      if (dx > 0.5 * a.Lx) dx -= a.Lx;
-      else if (dx < -0.5 * a.Lx) dx += a.Lx;
-      if (dy > 0.5 * a.Ly) dy -= a.Ly;
-      else if (dy < -0.5 * a.Ly) dy += a.Ly;
-      const double X = a.xb[p] + dx, Y = a.yb[p] + dy, Z = a.z[i];
-      a.xs[p] = X;
-      a.ys[p] = Y;
+      const double L = d == 0 ? a.Lx : a.Ly;
+      const double base = d == 0 ? a.xb[p] : a.yb[p];
+      double dx = (d == 0 ? a.x[i] : a.y[i]) - base;
+      if (dx > 0.5 * L) dx -= L;
+      else if (dx < -0.5 * L) dx += L;
+      const double X = base + dx;
+      if (d == 0) {
+        a.xs[p] = X;
+        a.pf[p].x = (float)X;
+        ed = (float)X - b.x;
+      } else {
+        a.ys[p] = X;
+        a.pf[p].y = (float)X;
+        ed = (float)X - b.y;
+      }
+      a.us[d * a.n + p] = to_turns64(X, d == 0 ? a.invL.x : a.invL.y);
+    } else {
+      const double Z = a.z[i];
       a.zs[p] = Z;
-      const float4 b = a.pfb[p];
-      a.pf[p] = make_float4((float)X, (float)Y, (float)Z, b.w);
-      a.us[p] = to_turns64(X, a.invL.x);
-      a.us[a.n + p] = to_turns64(Y, a.invL.y);
+      a.pf[p].z = (float)Z;
+      ed = (float)Z - b.z;
       a.us[2 * a.n + p] = to_turns64(Z, a.invL.z);
-      const float ex = (float)X - b.x, ey = (float)Y - b.y, ez = (float)Z - b.z;
-      if (ex * ex + ey * ey + ez * ez > a.half_skin2) atomicOr(&a.flag[0], 1);
     }
+    e2 = ed * ed;
   }
+  // the group of four lanes holds one ion: add its three squared components in the order x, y, z
+  const float ey2 = __shfl_down_sync(0xffffffffu, e2, 1), ez2 = __shfl_down_sync(0xffffffffu, e2, 2);
+  if (d == 0 && p < a.n && (e2 + ey2) + ez2 > a.half_skin2) atomicOr(&a.flag[0], 1);
 }
 
 // The rebuild, one cooperative launch whose phases are separated by grid-wide barriers.  The
@@ -1204,7 +1221,7 @@ void neighbor_update(srbe_ctx *c) {
   }
   const int want = (int)std::max<int64_t>(1, std::min<int64_t>((std::max<int64_t>(n, c->ne) * 32 + 255) / 256,
                                                                  (int64_t)blocks_per_sm * nsm));
-  k_nbr_refresh<<<blocks_for(std::max<int64_t>(n, 1), 64), 64, 0, c->stream>>>(a);
+  k_nbr_refresh<<<blocks_for(4 * std::max<int64_t>(n, 1), 128), 128, 0, c->stream>>>(a);
   SRBE_CUDA(cudaGetLastError());
   void *args[] = {&a};
   coop_before(c);
@@ -1777,75 +1794,66 @@ __device__ __forceinline__ double wrap_periodic(double X, double L) {
 
 // The closing half kick (status != nullptr) also checks the step's forces and charges: a non-finite
 // F of this thread's ion or Q of the electrode site with the same index raises the context's flag.
+// One thread per (ion, component): the FP64 update of a component is a short dependent chain, and
+// on this GPU an FP64 warp instruction holds its sub-partition for many cycles, so three threads
+// per ion shorten the kernel's critical path.  blockIdx.y is the component (0 x, 1 y, 2 z).  Each
+// thread draws the same Philox words for its ion and forms its own one of the three normals (the
+// arithmetic of each component is unchanged: the results are the same bits as one thread per ion).
 __global__ void k_kick_drift(int64_t n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                              double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
                              const double *__restrict__ F, const double *__restrict__ minv, double fac, double dt,
                              int drift, double Lx, double Ly, Thermo th, double3 invL, uint64_t *__restrict__ iu,
                              int64_t ne, const double *__restrict__ Q, int *__restrict__ status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (status && i < ne && !isfinite(Q[i])) *(volatile int *)(status + kStatNonFiniteQ) = 1;
+  const int d = blockIdx.y;
+  if (d == 0 && status && i < ne && !isfinite(Q[i])) *(volatile int *)(status + kStatNonFiniteQ) = 1;
   if (i >= n) return;
+  double *pos = d == 0 ? x : (d == 1 ? y : z);
+  double *vel = d == 0 ? vx : (d == 1 ? vy : vz);
   const double w = fac * minv[i];
-  const double fx = F[i], fy = F[n + i], fz = F[2 * n + i];
-  if (status && !(isfinite(fx) && isfinite(fy) && isfinite(fz))) *(volatile int *)(status + kStatNonFiniteF) = 1;
-  double a = fma(w, fx, vx[i]), b = fma(w, fy, vy[i]), c = fma(w, fz, vz[i]);
+  const double f = F[d * n + i];
+  if (status && !isfinite(f)) *(volatile int *)(status + kStatNonFiniteF) = 1;
+  double a = fma(w, f, vel[i]);
   if (th.on) {
     const int4 st = *th.step;
     const uint64_t step = (uint64_t)(uint32_t)st.x | ((uint64_t)(uint32_t)st.y << 32);
     uint64_t wd[4];
     philox4x64_dev(step, (uint64_t)i, 0, 0, th.seed, 0x4C414E47ull, wd);
-    double g0, g1, g2;   // sigma_i times three standard normals
+    // sigma_i times a standard normal: words 0 and 1 give the x and y normals (Box-Muller, cos and
+    // sin), words 2 and 3 the z normal (cos)
+    const int wr = d < 2 ? 0 : 2;
+    double g;
     if (th.f32) {
-      // the same words, their top 24 bits as FP32 uniforms in (0, 1): every FP64 instruction is
-      // costly on this GPU and the noise needs no more than FP32
-      float u[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) u[q] = ((float)(uint32_t)(wd[q] >> 40) + 0.5f) * 0x1.0p-24f;
-      const float r0 = sqrtf(-2.f * logf(u[0])), r1 = sqrtf(-2.f * logf(u[2]));
-      float s0, c0, s1, c1v;
-      sincospif(2.f * u[1], &s0, &c0);
-      sincospif(2.f * u[3], &s1, &c1v);
-      (void)s1;
-      // sigma in FP32 too, and the three noise terms formed before the FP64 update
+      // the top 24 bits of the words as FP32 uniforms in (0, 1): the noise needs no more than FP32
+      // and every FP64 instruction is costly on this GPU
+      const float u0 = ((float)(uint32_t)(wd[wr] >> 40) + 0.5f) * 0x1.0p-24f;
+      const float u1 = ((float)(uint32_t)(wd[wr + 1] >> 40) + 0.5f) * 0x1.0p-24f;
+      const float r = sqrtf(-2.f * logf(u0));
+      float sn, cs;
+      sincospif(2.f * u1, &sn, &cs);
       const float sg = sqrtf((float)th.s2 * (float)minv[i]);
-      g0 = (double)(sg * (r0 * c0));
-      g1 = (double)(sg * (r0 * s0));
-      g2 = (double)(sg * (r1 * c1v));
+      g = (double)(sg * (r * (d == 1 ? sn : cs)));
     } else {
-      double u[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) u[q] = ((double)(wd[q] >> 11) + 0.5) * 0x1.0p-53;
-      const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
-      double s0, c0, s1, c1v;
-      sincospi(2.0 * u[1], &s0, &c0);
-      sincospi(2.0 * u[3], &s1, &c1v);
-      (void)s1;
+      const double u0 = ((double)(wd[wr] >> 11) + 0.5) * 0x1.0p-53;
+      const double u1 = ((double)(wd[wr + 1] >> 11) + 0.5) * 0x1.0p-53;
+      const double r = sqrt(-2.0 * log(u0));
+      double sn, cs;
+      sincospi(2.0 * u1, &sn, &cs);
       const double sig = sqrt(th.s2 * minv[i]);
-      g0 = sig * (r0 * c0);
-      g1 = sig * (r0 * s0);
-      g2 = sig * (r1 * c1v);
+      g = sig * (r * (d == 1 ? sn : cs));
     }
-    a = fma(th.c1, a, g0);
-    b = fma(th.c1, b, g1);
-    c = fma(th.c1, c, g2);
+    a = fma(th.c1, a, g);
   }
-  vx[i] = a;
-  vy[i] = b;
-  vz[i] = c;
+  vel[i] = a;
   if (drift) {
-    const double X = wrap_periodic(fma(dt, a, x[i]), Lx), Y = wrap_periodic(fma(dt, b, y[i]), Ly);
-    const double Z = fma(dt, c, z[i]);
-    x[i] = X;
-    y[i] = Y;
-    z[i] = Z;
-    // the new positions' fixed-point phase coordinates, once per step for the ion structure factor
-    iu[i] = to_turns64(X, invL.x);
-    iu[n + i] = to_turns64(Y, invL.y);
-    iu[2 * n + i] = to_turns64(Z, invL.z);
+    double X = fma(dt, a, pos[i]);
+    if (d < 2) X = wrap_periodic(X, d == 0 ? Lx : Ly);
+    pos[i] = X;
+    // the new position's fixed-point phase coordinate, once per step for the ion structure factor
+    iu[d * n + i] = to_turns64(X, d == 0 ? invL.x : (d == 1 ? invL.y : invL.z));
   }
 }
 
-// capped steepest descent: r += F min(a, dmax / |F|), x and y wrapped into [0, L)
 __global__ void k_sd_move(int64_t n, double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
                           const double *__restrict__ F, double a, double dmax, double Lx, double Ly) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1898,8 +1906,9 @@ void integrate_kick_drift(srbe_ctx *c, double fac_kick, bool drift) {
   // the closing kick checks the step's forces and charges (one thread per ion and per site)
   const int64_t ne = drift ? 0 : c->ne;
   const int64_t nt = std::max<int64_t>(c->ni, ne);
-  // 64-thread blocks: the FP64 arithmetic spreads over every SM even for a few thousand ions
-  k_kick_drift<<<blocks_for(nt, 64), 64, 0, c->stream>>>(c->ni, c->x.p, c->y.p, c->z.p, c->vx.p, c->vy.p,
+  // 64-thread blocks, one grid row per component: the FP64 arithmetic spreads over every SM even for
+  // a few thousand ions
+  k_kick_drift<<<dim3(blocks_for(nt, 64), 3), 64, 0, c->stream>>>(c->ni, c->x.p, c->y.p, c->z.p, c->vx.p, c->vy.p,
                                                          c->vz.p, c->F.p, c->minv.p, fac_kick, c->dt,
                                                          drift ? 1 : 0, c->L[0], c->L[1], th, invL, iu, ne, c->Q.p,
                                                          drift ? nullptr : c->d_status);
