@@ -524,7 +524,8 @@ struct PcgArgs {
   int *status;       // the context's host-mapped error flags
   // mixed form (k_pcg_mixed): FP32 A and inner vectors
   const float *A32;
-  float *r32, *z32, *p32, *Ap32, *d32;
+  float *r32, *z32, *p32, *Ap32, *d32, *s32, *part32;
+  const float *dinv32;
 };
 
 __device__ double grid_dot_sum(const PcgArgs &a, double mine, int slot, cg::grid_group &grid) {
@@ -550,8 +551,131 @@ __device__ double grid_dot_sum(const PcgArgs &a, double mine, int slot, cg::grid
   return total;
 }
 
-// out = v - A x (minus = true) or A x, rows grid-strided over warps
+// two sums at once (one grid barrier): slots slot and slot + 1 of the block partials
+__device__ double2 grid_dot_sum2(const PcgArgs &a, double m0, double m1, int slot, cg::grid_group &grid) {
+  __shared__ double red2[2][256];
+  const int t = threadIdx.x;
+  red2[0][t] = m0;
+  red2[1][t] = m1;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (t < s) {
+      red2[0][t] += red2[0][t + s];
+      red2[1][t] += red2[1][t + s];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    a.part[slot * gridDim.x + blockIdx.x] = red2[0][0];
+    a.part[(slot + 1) * gridDim.x + blockIdx.x] = red2[1][0];
+  }
+  grid.sync();
+  __shared__ double total2[2];
+  if (t < 64) {
+    const int k = t >> 5, lane = t & 31;
+    double acc = 0.0;
+    for (unsigned b = lane; b < gridDim.x; b += 32) acc += __ldcg(&a.part[(slot + k) * gridDim.x + b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) total2[k] = acc;
+  }
+  __syncthreads();
+  return make_double2(total2[0], total2[1]);
+}
+
+// Matrix-vector products of the iterative solves.  Block b takes the rows b, b + G, b + 2G, ...
+// (G blocks) kGemvRows at a time, and its 8 warps split every row's columns into 8 contiguous
+// segments: each lane keeps kGemvRows independent row loads in flight per load of x, which the
+// warp-per-row form (one dependent chain per lane) did not.  The 8 segment partials of a row are
+// added in segment order.
+constexpr int kGemvRows = 8;
+constexpr int kGemvUnroll = 3;
+template <class V> struct Vec;          // 16-byte vector of the matrix type
+template <> struct Vec<float> {
+  using T = float4;
+  static constexpr int W = 4;
+  __device__ static float dot(T m, T v) { return fmaf(m.x, v.x, fmaf(m.y, v.y, fmaf(m.z, v.z, m.w * v.w))); }
+};
+template <> struct Vec<double> {
+  using T = double2;
+  static constexpr int W = 2;
+  __device__ static double dot(T m, T v) { return fma(m.x, v.x, m.y * v.y); }
+};
+template <class T>
+__device__ void block_rows_gemv(int64_t n, const T *__restrict__ A, const T *__restrict__ x, int64_t r0,
+                                T (*part)[kGemvRows]) {
+  using V = Vec<T>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t G = gridDim.x;
+  T acc[kGemvRows];
+#pragma unroll
+  for (int k = 0; k < kGemvRows; ++k) acc[k] = 0;
+  if (n % V::W == 0) {
+    // 16-byte loads (rows start on 16-byte boundaries), kGemvUnroll column steps of all kGemvRows
+    // rows issued before any is used: the product is bound by the loads in flight, not by the FMAs
+    using VT = typename V::T;
+    const int64_t nv = n / V::W, seg = (nv + 7) / 8, c0 = warp * seg, c1 = min(nv, c0 + seg);
+    const VT *xv = reinterpret_cast<const VT *>(x);
+    const VT zero{};
+    for (int64_t j0 = c0 + lane; j0 < c1; j0 += 32 * kGemvUnroll) {
+      VT m[kGemvUnroll][kGemvRows], v[kGemvUnroll];
+#pragma unroll
+      for (int u = 0; u < kGemvUnroll; ++u) {
+        const int64_t j = j0 + 32 * u;
+        v[u] = j < c1 ? __ldcg(xv + j) : zero;
+#pragma unroll
+        for (int k = 0; k < kGemvRows; ++k) {
+          const int64_t row = r0 + k * G;
+          m[u][k] = (j < c1 && row < n) ? __ldcs(reinterpret_cast<const VT *>(A + row * n) + j) : zero;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kGemvUnroll; ++u)
+#pragma unroll
+        for (int k = 0; k < kGemvRows; ++k) acc[k] += V::dot(m[u][k], v[u]);
+    }
+  } else {
+    const int64_t seg = (n + 7) / 8, c0 = warp * seg, c1 = min(n, c0 + seg);
+    for (int64_t j = c0 + lane; j < c1; j += 32) {
+      const T v = __ldcg(x + j);
+#pragma unroll
+      for (int k = 0; k < kGemvRows; ++k) {
+        const int64_t row = r0 + k * G;
+        if (row < n) acc[k] = fma(__ldcs(A + row * n + j), v, acc[k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kGemvRows; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < kGemvRows; ++k) part[warp][k] = acc[k];
+}
+
+// out = v - A x (minus = true) or A x in FP64
 __device__ void grid_gemv(const PcgArgs &a, const double *x, const double *v, double *out, bool minus) {
+  __shared__ double part[8][kGemvRows];
+  const int64_t G = gridDim.x;
+  for (int64_t r0 = blockIdx.x; r0 < a.n; r0 += G * kGemvRows) {
+    block_rows_gemv<double>(a.n, a.A, x, r0, part);
+    __syncthreads();
+    if (threadIdx.x < kGemvRows) {
+      const int64_t row = r0 + threadIdx.x * G;
+      if (row < a.n) {
+        double s = part[0][threadIdx.x];
+        for (int w = 1; w < 8; ++w) s += part[w][threadIdx.x];
+        out[row] = minus ? v[row] - s : s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// out = v - A x (minus = true) or A x, rows grid-strided over warps (the FP64 form's k_pcg)
+__device__ void grid_gemv_rows(const PcgArgs &a, const double *x, const double *v, double *out, bool minus) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -571,7 +695,7 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   // v = dpsi d + b lives in p for the first product; r = v - A y
   for (int64_t i = gt; i < a.n; i += gs) a.p[i] = fma(a.dpsi, a.d[i], a.b[i]);
   grid.sync();
-  grid_gemv(a, a.y, a.p, a.r, true);
+  grid_gemv_rows(a, a.y, a.p, a.r, true);
   grid.sync();
   double vv = 0.0, rz = 0.0, rr = 0.0;
   for (int64_t i = gt; i < a.n; i += gs) {
@@ -591,7 +715,7 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   grid.sync();
   int it = 0;
   while (it < a.maxit && rr > a.tol2 * vv) {
-    grid_gemv(a, a.p, nullptr, a.Ap, false);
+    grid_gemv_rows(a, a.p, nullptr, a.Ap, false);
     grid.sync();
     double pap = 0.0;
     for (int64_t i = gt; i < a.n; i += gs) pap += a.p[i] * a.Ap[i];
@@ -619,7 +743,7 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   // true residual, neutrality projection and psi_bar (Eqs. 9-10)
   for (int64_t i = gt; i < a.n; i += gs) a.z[i] = fma(a.dpsi, a.d[i], a.b[i]);
   grid.sync();
-  grid_gemv(a, a.y, a.z, a.r, true);
+  grid_gemv_rows(a, a.y, a.z, a.r, true);
   grid.sync();
   double r2 = 0.0, ey = 0.0;
   for (int64_t i = gt; i < a.n; i += gs) {
@@ -645,40 +769,91 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   }
 }
 
-// out = A32 x in FP32 (warp per row, 16-byte loads when n is a multiple of 4)
-__device__ void grid_gemv32(const PcgArgs &a, const float *x, float *out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = gw; row < a.n; row += nw) {
-    const float *Ar = a.A32 + row * a.n;
-    float acc = 0.f;
-    if ((a.n & 3) == 0) {
-      const float4 *A4 = reinterpret_cast<const float4 *>(Ar);
-      const float4 *x4 = reinterpret_cast<const float4 *>(x);
-      for (int64_t j = lane; j < (a.n >> 2); j += 32) {
-        const float4 m = __ldcs(A4 + j), v = __ldcg(x4 + j);
-        acc = fmaf(m.x, v.x, fmaf(m.y, v.y, fmaf(m.z, v.z, fmaf(m.w, v.w, acc))));
-      }
-    } else {
-      for (int64_t j = lane; j < a.n; j += 32) acc = fmaf(__ldcs(Ar + j), __ldcg(x + j), acc);
+// The mixed form's inner sums: FP32, a warp tree, the 8 warps in order, then the block partials in
+// block order (one grid barrier for three sums); two alternating partial slots
+__device__ float3 grid_sum3f(const PcgArgs &a, float v0, float v1, float v2, int slot, cg::grid_group &grid) {
+  __shared__ float wred[3][8];
+  __shared__ float3 tot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+  }
+  if (lane == 0) {
+    wred[0][warp] = v0;
+    wred[1][warp] = v1;
+    wred[2][warp] = v2;
+  }
+  __syncthreads();
+  float *P = a.part32 + (size_t)slot * 3 * gridDim.x;
+  if (threadIdx.x == 0) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int w = 0; w < 8; ++w) {
+      s0 += wred[0][w];
+      s1 += wred[1][w];
+      s2 += wred[2][w];
+    }
+    P[blockIdx.x] = s0;
+    P[gridDim.x + blockIdx.x] = s1;
+    P[2 * gridDim.x + blockIdx.x] = s2;
+  }
+  grid.sync();
+  if (warp == 0) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (unsigned b = lane; b < gridDim.x; b += 32) {
+      s0 += __ldcg(P + b);
+      s1 += __ldcg(P + gridDim.x + b);
+      s2 += __ldcg(P + 2 * gridDim.x + b);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[row] = acc;
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) tot = make_float3(s0, s1, s2);
   }
+  __syncthreads();
+  return tot;
+}
+
+// w = A32 u in FP32 (block rows, warp column segments); returns this thread's share of (w, u)
+__device__ float grid_gemv32_dot(const PcgArgs &a, const float *u, float *w) {
+  __shared__ float part[8][kGemvRows];
+  const int64_t G = gridDim.x;
+  float dl = 0.f;
+  for (int64_t r0 = blockIdx.x; r0 < a.n; r0 += G * kGemvRows) {
+    block_rows_gemv<float>(a.n, a.A32, u, r0, part);
+    __syncthreads();
+    if (threadIdx.x < kGemvRows) {
+      const int64_t row = r0 + threadIdx.x * G;
+      if (row < a.n) {
+        float s = part[0][threadIdx.x];
+        for (int k = 1; k < 8; ++k) s += part[k][threadIdx.x];
+        w[row] = s;
+        dl = fmaf(s, __ldcg(u + row), dl);
+      }
+    }
+    __syncthreads();
+  }
+  return dl;
 }
 
 // The mixed form's iterative solve: iterative refinement in FP64 around Jacobi-PCG in FP32.  Each
 // outer pass forms the FP64 residual r = dpsi d + b - A y with A in FP64 and stops once
-// ||r|| <= tol ||dpsi d + b||; otherwise it solves A delta = r with PCG on an FP32 copy of A (half the
-// bytes per matrix-vector product; dot products summed in FP64) until the inner residual has fallen
-// by 1e-4, and adds delta to y in FP64.  maxit bounds the inner iterations over all passes; the
+// ||r|| <= tol ||dpsi d + b||; otherwise it solves A delta = r on an FP32 copy of A until the inner
+// residual has fallen by 1e-4, and adds delta to y in FP64.  The inner solve is the Chronopoulos-Gear
+// form of preconditioned CG (Chronopoulos and Gear, J. Comput. Appl. Math. 25, 1989): it applies A to
+// the preconditioned residual u = M^-1 r and updates A p by the recurrence s = w + beta s, so the three
+// inner products of an iteration, (r, u), (A u, u) and (r, r), share one grid barrier; an iteration
+// costs two grid barriers instead of four.  maxit bounds the inner iterations over all passes; the
 // iteration count reported is theirs.  Q and psi_bar follow from Eqs. 9-10 as in k_pcg.
 __global__ void __launch_bounds__(256, 1) k_pcg_mixed(PcgArgs a) {
   cg::grid_group grid = cg::this_grid();
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
-  int slot = 0;
+  int slot = 0, fslot = 0;
   double vv = 0.0;
   for (int64_t i = gt; i < a.n; i += gs) {
     const double v = fma(a.dpsi, a.d[i], a.b[i]);
@@ -686,9 +861,10 @@ __global__ void __launch_bounds__(256, 1) k_pcg_mixed(PcgArgs a) {
     vv += v * v;
   }
   vv = grid_dot_sum(a, vv, slot, grid);
-    slot = (slot + 1) & 7;            // its grid barrier also orders the writes of p before the products below
+  slot = (slot + 1) & 7;            // its grid barrier also orders the writes of p before the products below
   int it = 0;
   bool converged = false;
+  float *x = a.d32, *r = a.r32, *u = a.z32, *w = a.Ap32, *p = a.p32, *s = a.s32;
   for (int outer = 0; outer < 16; ++outer) {
     grid_gemv(a, a.y, a.p, a.r, true);
     grid.sync();
@@ -701,49 +877,51 @@ __global__ void __launch_bounds__(256, 1) k_pcg_mixed(PcgArgs a) {
       break;
     }
     if (it >= a.maxit) break;
-    // inner FP32 PCG on A delta = r
-    double rz = 0.0;
+    // inner FP32 solve of A delta = r (delta in x)
+    float gam = 0.f, rr32 = 0.f;
     for (int64_t i = gt; i < a.n; i += gs) {
-      const float ri = (float)a.r[i], zi = (float)a.dinv[i] * ri;
-      a.r32[i] = ri;
-      a.z32[i] = zi;
-      a.p32[i] = zi;
-      a.d32[i] = 0.f;
-      rz += (double)ri * (double)zi;
+      const float ri = (float)a.r[i], ui = a.dinv32[i] * ri;
+      r[i] = ri;
+      u[i] = ui;
+      x[i] = 0.f;
+      p[i] = 0.f;
+      s[i] = 0.f;
+      gam = fmaf(ri, ui, gam);
+      rr32 = fmaf(ri, ri, rr32);
     }
-    rz = grid_dot_sum(a, rz, slot, grid);
-    slot = (slot + 1) & 7;
-    const double stop = 1e-8 * rr;          // inner residual 1e-4 of the outer one
-    double rr32 = rr;
-    while (it < a.maxit && rr32 > stop) {
-      grid_gemv32(a, a.p32, a.Ap32);
-      grid.sync();
-      double pap = 0.0;
-      for (int64_t i = gt; i < a.n; i += gs) pap += (double)a.p32[i] * (double)a.Ap32[i];
-      pap = grid_dot_sum(a, pap, slot, grid);
-    slot = (slot + 1) & 7;
-      const float alpha = (float)(rz / pap);
-      double rz1 = 0.0, rr1 = 0.0;
+    grid.sync();
+    float dl = grid_gemv32_dot(a, u, w);
+    float3 t = grid_sum3f(a, gam, dl, rr32, fslot, grid);
+    fslot ^= 1;
+    float gamma = t.x, alpha = t.x / t.y, beta = 0.f;
+    const float stop = (float)(1e-8 * rr);   // inner residual 1e-4 of the outer one
+    float rrc = t.z;
+    while (it < a.maxit && rrc > stop) {
+      gam = 0.f;
+      rr32 = 0.f;
       for (int64_t i = gt; i < a.n; i += gs) {
-        a.d32[i] = fmaf(alpha, a.p32[i], a.d32[i]);
-        const float ri = fmaf(-alpha, a.Ap32[i], a.r32[i]);
-        a.r32[i] = ri;
-        const float zi = (float)a.dinv[i] * ri;
-        a.z32[i] = zi;
-        rz1 += (double)ri * (double)zi;
-        rr1 += (double)ri * (double)ri;
+        const float pi = fmaf(beta, p[i], u[i]), si = fmaf(beta, s[i], __ldcg(w + i));
+        p[i] = pi;
+        s[i] = si;
+        x[i] = fmaf(alpha, pi, x[i]);
+        const float ri = fmaf(-alpha, si, r[i]);
+        r[i] = ri;
+        const float ui = a.dinv32[i] * ri;
+        u[i] = ui;
+        gam = fmaf(ri, ui, gam);
+        rr32 = fmaf(ri, ri, rr32);
       }
-      rz1 = grid_dot_sum(a, rz1, slot, grid);
-    slot = (slot + 1) & 7;
-      rr32 = grid_dot_sum(a, rr1, slot, grid);
-    slot = (slot + 1) & 7;
-      const float beta = (float)(rz1 / rz);
-      rz = rz1;
-      for (int64_t i = gt; i < a.n; i += gs) a.p32[i] = fmaf(beta, a.p32[i], a.z32[i]);
       grid.sync();
+      dl = grid_gemv32_dot(a, u, w);
+      t = grid_sum3f(a, gam, dl, rr32, fslot, grid);
+      fslot ^= 1;
+      beta = t.x / gamma;
+      alpha = t.x / (t.y - beta * t.x / alpha);
+      gamma = t.x;
+      rrc = t.z;
       ++it;
     }
-    for (int64_t i = gt; i < a.n; i += gs) a.y[i] += (double)a.d32[i];
+    for (int64_t i = gt; i < a.n; i += gs) a.y[i] += (double)x[i];
     grid.sync();
   }
   // true residual, neutrality projection and psi_bar (Eqs. 9-10)
@@ -802,7 +980,9 @@ void charge_update_pcg(srbe_ctx *c) {
     c->pcg.p32.ensure(n);
     c->pcg.Ap32.ensure(n);
     c->pcg.d32.ensure(n);
-    c->launches++;
+    c->pcg.s32.ensure(n);
+    k_to_float_n<<<blocks_for(n, 256), 256, 0, c->stream>>>(n, c->pcg.dinv.p, c->pcg.dinv32.ensure(n));
+    c->launches += 2;
     SRBE_CUDA(cudaGetLastError());
     c->pcg.a32_ready = true;
   }
@@ -830,6 +1010,9 @@ void charge_update_pcg(srbe_ctx *c) {
   a.p32 = c->pcg.p32.p;
   a.Ap32 = c->pcg.Ap32.p;
   a.d32 = c->pcg.d32.p;
+  a.s32 = c->pcg.s32.p;
+  a.dinv32 = c->pcg.dinv32.p;
+  a.part32 = c->pcg.part32.ensure((size_t)grid * 6);
   a.Q = c->Q.p;
   a.Q32 = c->Q32.p;
   a.scal = c->scal.p;

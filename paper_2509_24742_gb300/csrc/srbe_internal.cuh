@@ -114,7 +114,7 @@ struct PcgState {
   DevBuf<double> dinv, y, r, z, p, Ap, part, res;
   DevBuf<int> stats;
   // mixed form: FP32 copy of A and FP32 vectors of the inner iteration (iterative refinement)
-  DevBuf<float> A32, r32, z32, p32, Ap32, d32;
+  DevBuf<float> A32, r32, z32, p32, Ap32, d32, s32, dinv32, part32;
   bool a32_ready = false;
 };
 
