@@ -588,7 +588,7 @@ __device__ double2 grid_dot_sum2(const PcgArgs &a, double m0, double m1, int slo
 // segments: each lane keeps kGemvRows independent row loads in flight per load of x, which the
 // warp-per-row form (one dependent chain per lane) did not.  The 8 segment partials of a row are
 // added in segment order.
-constexpr int kGemvRows = 8;
+constexpr int kGemvRows = 11;
 constexpr int kGemvUnroll = 3;
 template <class V> struct Vec;          // 16-byte vector of the matrix type
 template <> struct Vec<float> {
