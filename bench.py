@@ -263,6 +263,8 @@ def gpu_arm(args, rank, world):
     # untimed set-up: the Verlet skin of the headline form picked by timing (state restored after)
     skin_ms = ctxs[head].autotune_skin(20, SEED, skins=SKINS)
     skin = ctxs[head].skin()
+    tile_ms = ctxs[head].autotune_tiles(20, SEED)
+    tile = ctxs[head].tiles()
 
     def timed(ctx, steps, warm, traced=False):
         """Device time of `steps` MD steps, each bracketed by CUDA events on the context's stream,
@@ -341,6 +343,8 @@ def gpu_arm(args, rank, world):
         "phases_ms_per_step": {p: round(v, 5) for p, v in per_step.items()},
         "verlet_skin_nm": {"chosen": skin, "autotune_ms_per_step": {str(k): round(v, 5) for k, v in
                                                                                  skin_ms.items()}},
+        "structure_factor_tile": {"chosen_blocks_per_sm": tile,
+                                  "autotune_ms_per_step": {str(k): round(v, 5) for k, v in tile_ms.items()}},
         "launch": {"timed_steps": "CUDA-graph replay, one graph launch per step" if graph_state[0] == 1
                    else "ordinary launches", "kernels_per_step": graph_state[1] or None,
                    "traced_pass": {"steps": n_trace, "steps_per_s": n_trace / (ms_trace * 1e-3),
@@ -418,6 +422,9 @@ def prec_arm(args):
     ctx.set_stream(stream.cuda_stream)
     ctx.minimize(N_MIN)
     ctx.set_thermostat(GAMMA, T_BATH, SEED)
+    # the Verlet skin, as for the benchmark slab: the rebuild rate against the list length
+    skin_ms = ctx.autotune_skin(10, SEED, skins=SKINS)
+    skin = ctx.skin()
     ctx.sample_k(SEED, 0)
     F32, Q32, _ = ctx.forces()
     res32 = ctx.charge_residual()
@@ -463,6 +470,8 @@ def prec_arm(args):
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": wl_name, "l2": "flushed between timed steps (256 MB write)",
                        "lattice_electrode": lat},
+            "verlet_skin_nm": {"chosen": skin, "autotune_ms_per_step": {str(k): round(v, 5) for k, v in
+                                                                         skin_ms.items()}},
             "accuracy": {"rms_force_err_vs_fp64_gpu": rms_f, "rms_charge_err_vs_fp64_gpu": rms_q,
                          "fp64_charge_residual_mixed": res32, "fp64_charge_residual_fp64": res64},
             "mixed": out["mixed"], "fp64": out["fp64"], "speedup_vs_fp64": out["mixed"]["steps_per_s"] /
@@ -571,6 +580,9 @@ def batch_arm(args):
     b = srbe.Batch(ctxs)
     tune = b.autotune(3, seeds)
     width = b.width()
+    # then the structure-factor tile (blocks per SM its chunking keeps), one setting for all replicas
+    tune_tiles = b.autotune_tiles(3, seeds)
+    tile = ctxs[0].tiles()
     bs = torch.cuda.ExternalStream(b.stream())
 
     def run_batch(steps):
@@ -629,7 +641,10 @@ def batch_arm(args):
                    "l2": "state larger than L2 (electrode matrices %.1f GB)" %
                          (sum(s.n_ele ** 2 * 24 for s in slabs) / 1e9)},
         "launch": {"graph_launches_per_batch_step": 1, "stream_width": width,
-                   "autotune_ms_per_batch_step": {str(k): round(v, 4) for k, v in tune.items()}},
+                   "autotune_ms_per_batch_step": {str(k): round(v, 4) for k, v in tune.items()},
+                   "structure_factor_tile": {"chosen_blocks_per_sm": tile,
+                                             "autotune_ms_per_batch_step": {str(k): round(v, 4) for k, v in
+                                                                            tune_tiles.items()}}},
         "fp64_charge_residual": {"batch_mixed_max": float(np.nanmax(res)), "batch_mixed_median": float(np.nanmedian(res)),
                                  "plain_fp64_max": float(np.nanmax(res_p)),
                                  "replicas_with_finite_residual": int(np.isfinite(res).sum())},

@@ -337,6 +337,19 @@ double srbe_get_skin(const srbe_ctx *ctx);
 int srbe_autotune_skin(srbe_ctx *ctx, int trial_steps, uint64_t seed, const double *skins, int n_skins,
                        double *ms_per_step);
 
+/* Tile shape of the structure-factor kernel (S1, S2; no counterpart in the paper): the sum over
+ * particles runs in chunks of whole 128-particle batches, as long as the grid keeps at least `occ`
+ * blocks per SM (longer chunks amortise each block's closing reductions, shorter ones give more
+ * blocks to hide latency with).  Default occ = 8.  Results do not depend on it beyond summation
+ * order.  srbe_autotune_tiles times trial_steps MD steps (after two untimed ones) for each candidate
+ * occ (1..64), restores the state after each trial as srbe_autotune_skin does, keeps the fastest and
+ * writes the per-candidate ms per step to ms_per_step (n_occ entries, or NULL); srbe_get_tiles gives
+ * the setting in use.  Errors: SRBE_EINVAL (no candidates, occ out of range, trial_steps < 1),
+ * SRBE_ESTATE (no MD state). */
+int srbe_autotune_tiles(srbe_ctx *ctx, int trial_steps, uint64_t seed, const int *occ, int n_occ,
+                        double *ms_per_step);
+int srbe_get_tiles(const srbe_ctx *ctx);
+
 /* A batch steps many independent replicas (contexts of any size, electrode, voltage, precision,
  * solver and mode count, each with its own seed and so its own k-sample lists) as one unit: each
  * batch step is ONE CUDA graph launch that runs Algorithm 1's step for every replica, the replicas
@@ -356,6 +369,8 @@ int srbe_autotune_skin(srbe_ctx *ctx, int trial_steps, uint64_t seed, const doub
  *   srbe_batch_autotune: for each candidate width, times trial_steps batch steps (after two
  *     untimed ones), restores every replica's state (as srbe_autotune_skin does) and keeps the
  *     fastest width; ms_per_step (n_widths entries, or NULL) receives the timings.
+ *   srbe_batch_autotune_tiles: the same for the structure-factor tile (srbe_autotune_tiles' occ),
+ *     one setting for every replica (each replica's chunk length then follows its own size).
  * Errors: SRBE_EINVAL (bad arguments), SRBE_ESTATE (a replica without electrode, positions or MD
  * state, or with phase tracing on), SRBE_ECUDA (capture or launch failed), SRBE_ENOMEM;
  * srbe_batch_last_error gives the message. */
@@ -370,6 +385,8 @@ void *srbe_batch_stream(const srbe_batch *batch);
 int srbe_batch_step(srbe_batch *batch, int nsteps, const uint64_t *seeds, double *residuals);
 int srbe_batch_autotune(srbe_batch *batch, int trial_steps, const uint64_t *seeds, const int *widths, int n_widths,
                         double *ms_per_step);
+int srbe_batch_autotune_tiles(srbe_batch *batch, int trial_steps, const uint64_t *seeds, const int *occ, int n_occ,
+                              double *ms_per_step);
 
 /* Test aid (no counterpart in the paper): from the next pass on, overwrite one entry of the output
  * with a NaN right after it is computed and before the non-finite check runs: what = 1 the force

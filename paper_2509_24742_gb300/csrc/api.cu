@@ -503,7 +503,7 @@ void upload_table(srbe_ctx *c) {
 void reserve(srbe_ctx *c) {
   const int K = std::max(c->K, 1);
   int64_t ch;
-  const int64_t nch = std::max(sfac_chunks(c->ni, c->K, &ch), sfac_chunks(c->ne, c->K, &ch));
+  const int64_t nch = std::max(sfac_chunks(c->ni, c->K, c->sf_occ, &ch), sfac_chunks(c->ne, c->K, c->sf_occ, &ch));
   c->partial.ensure((size_t)std::max<int64_t>(nch, 1) * K);
   c->mpart.ensure((size_t)std::max<int64_t>(nch, 1));
   c->coef.ensure((size_t)K);
@@ -2523,6 +2523,52 @@ int srbe_batch_step(srbe_batch *b, int nsteps, const uint64_t *seeds, double *re
   });
 }
 
+int srbe_autotune_tiles(srbe_ctx *c, int trial_steps, uint64_t seed, const int *occ, int n_occ,
+                        double *ms_per_step) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(trial_steps >= 1 && occ && n_occ >= 1, SRBE_EINVAL, "need trial steps and candidate tiles");
+    SRBE_REQUIRE(c->have_md && c->have_pos && c->have_ele, SRBE_ESTATE, "the context needs an MD state");
+    for (int i = 0; i < n_occ; ++i)
+      SRBE_REQUIRE(occ[i] >= 1 && occ[i] <= 64, SRBE_EINVAL, "blocks per SM out of [1, 64]");
+    const bool prof = c->profiling;
+    c->profiling = false;
+    initial_forces(c, seed);
+    Snapshot snap;
+    snapshot_io(c, snap, true);
+    cudaEvent_t t0, t1;
+    SRBE_CUDA(cudaEventCreate(&t0));
+    SRBE_CUDA(cudaEventCreate(&t1));
+    double best = 1e300;
+    int best_occ = c->sf_occ;
+    for (int i = 0; i < n_occ; ++i) {
+      c->sf_occ = occ[i];
+      reserve(c);
+      extra(c)->graph_dirty = true;
+      SRBE_REQUIRE(srbe_step(c, 2, seed) == SRBE_OK, SRBE_ECUDA, c->err);
+      SRBE_CUDA(cudaEventRecord(t0, c->stream));
+      SRBE_REQUIRE(srbe_step(c, trial_steps, seed) == SRBE_OK, SRBE_ECUDA, c->err);
+      SRBE_CUDA(cudaEventRecord(t1, c->stream));
+      SRBE_CUDA(cudaEventSynchronize(t1));
+      float ms = 0.f;
+      SRBE_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+      if (ms_per_step) ms_per_step[i] = ms / trial_steps;
+      if (ms / trial_steps < best) {
+        best = ms / trial_steps;
+        best_occ = occ[i];
+      }
+      snapshot_io(c, snap, false);
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    c->sf_occ = best_occ;
+    reserve(c);
+    extra(c)->graph_dirty = true;
+    c->profiling = prof;
+  });
+}
+
+int srbe_get_tiles(const srbe_ctx *c) { return c ? c->sf_occ : 0; }
+
 int srbe_batch_autotune(srbe_batch *b, int trial_steps, const uint64_t *seeds, const int *widths, int n_widths,
                         double *ms_per_step) {
   return batch_guarded(b, [&] {
@@ -2568,6 +2614,62 @@ int srbe_batch_autotune(srbe_batch *b, int trial_steps, const uint64_t *seeds, c
     cudaEventDestroy(t1);
     for (int r = 0; r < n; ++r) SRBE_CUDA(cudaStreamSynchronize(b->ctx[r]->stream));
     b->width = best_w;
+    b->dirty = true;
+  });
+}
+
+int srbe_batch_autotune_tiles(srbe_batch *b, int trial_steps, const uint64_t *seeds, const int *occ, int n_occ,
+                              double *ms_per_step) {
+  return batch_guarded(b, [&] {
+    SRBE_REQUIRE(trial_steps >= 1 && seeds && occ && n_occ >= 1, SRBE_EINVAL,
+                 "need trial_steps >= 1, seeds and candidate tiles");
+    for (int i = 0; i < n_occ; ++i)
+      SRBE_REQUIRE(occ[i] >= 1 && occ[i] <= 64, SRBE_EINVAL, "blocks per SM out of [1, 64]");
+    batch_check_replicas(b);
+    const int n = (int)b->ctx.size();
+    std::vector<Snapshot> snap(n);
+    for (int r = 0; r < n; ++r) {
+      SRBE_CUDA(cudaStreamSynchronize(b->main));
+      initial_forces(b->ctx[r], seeds[r]);
+      snapshot_io(b->ctx[r], snap[r], true);
+    }
+    cudaEvent_t t0, t1;
+    SRBE_CUDA(cudaEventCreate(&t0));
+    SRBE_CUDA(cudaEventCreate(&t1));
+    double best = 1e300;
+    int best_occ = b->ctx.empty() ? 8 : b->ctx[0]->sf_occ;
+    for (int i = 0; i < n_occ; ++i) {
+      // one setting for every replica: each replica's chunking follows its own size from it
+      for (int r = 0; r < n; ++r) {
+        b->ctx[r]->sf_occ = occ[i];
+        reserve(b->ctx[r]);
+      }
+      b->dirty = true;
+      batch_run(b, 2, seeds);                        // ordinary first step, capture, one replay
+      SRBE_CUDA(cudaEventRecord(t0, b->main));
+      batch_run(b, trial_steps, seeds);
+      SRBE_CUDA(cudaEventRecord(t1, b->main));
+      SRBE_CUDA(cudaEventSynchronize(t1));
+      float ms = 0.f;
+      SRBE_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+      if (ms / trial_steps < best) {
+        best = ms / trial_steps;
+        best_occ = occ[i];
+      }
+      if (ms_per_step) ms_per_step[i] = ms / trial_steps;
+      for (int r = 0; r < n; ++r) {
+        srbe_ctx *c = b->ctx[r];
+        SRBE_CUDA(cudaStreamSynchronize(c->stream));
+        snapshot_io(c, snap[r], false);
+      }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    for (int r = 0; r < n; ++r) {
+      SRBE_CUDA(cudaStreamSynchronize(b->ctx[r]->stream));
+      b->ctx[r]->sf_occ = best_occ;
+      reserve(b->ctx[r]);
+    }
     b->dirty = true;
   });
 }

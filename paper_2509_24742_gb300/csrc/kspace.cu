@@ -233,20 +233,28 @@ __global__ void k_sfac_reduce(SfFinish f) {
   sf_finish(f, k, threadIdx.x & 31);
 }
 
-// chunking of the particle sum: whole 128-particle batches, at most kSfMaxChunks chunks.  A chunk
-// spans as many batches (up to 8) as keeps at least 8 blocks per SM: each block ends with a few FP64
-// operations (the partial's compensation and the warp sums), which cost 64 cycles of a
-// sub-partition each on this GPU, so longer chunks spread them over more particles.
-constexpr int64_t kSfMinBlocks = 8 * 152;
-int64_t sfac_chunks(int64_t n, int K, int64_t *chunk) {
+// chunking of the particle sum (the kernel's tile along the particles): whole 128-particle
+// batches, at most kSfMaxChunks chunks.  A chunk spans as many batches (up to 8) as keeps at least
+// `occ` blocks per SM: each block ends with a few FP64 operations (the partial's compensation and the
+// warp sums), which cost 64 cycles of a sub-partition each on this GPU, so longer chunks spread them
+// over more particles, while shorter ones give more blocks to hide latency with.  occ is a context
+// setting (default 8) that srbe_autotune_tiles / srbe_batch_autotune_tiles choose by timing.
+int64_t sfac_chunks(int64_t n, int K, int occ, int64_t *chunk) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    SRBE_CUDA(cudaGetDevice(&dev));
+    SRBE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
   if (n <= 0) {
     *chunk = kSfThreads;
     return 0;
   }
+  const int64_t min_blocks = (int64_t)std::max(1, occ) * nsm;
   const int64_t ktiles = std::max(1, (K + 31) / 32);
   const int64_t batches = (n + kSfThreads - 1) / kSfThreads;
   int64_t per = (batches + kSfMaxChunks - 1) / kSfMaxChunks;
-  while (per < 8 && ((batches + 2 * per - 1) / (2 * per)) * ktiles >= kSfMinBlocks) per *= 2;
+  while (per < 8 && ((batches + 2 * per - 1) / (2 * per)) * ktiles >= min_blocks) per *= 2;
   *chunk = per * kSfThreads;
   return (n + *chunk - 1) / *chunk;
 }
@@ -257,7 +265,7 @@ void structure_factor(srbe_ctx *c, int64_t n, const double *x, const double *y, 
   const int K = c->K;
   const int ktiles = std::max(1, (K + 31) / 32);
   int64_t chunk;
-  const int64_t nchunk = sfac_chunks(n, K, &chunk);
+  const int64_t nchunk = sfac_chunks(n, K, c->sf_occ, &chunk);
   SRBE_REQUIRE(c->partial.cap >= (size_t)std::max<int64_t>(nchunk * K, 1) &&
                    c->mpart.cap >= (size_t)std::max<int64_t>(nchunk, 1),
                SRBE_ESTATE, "scratch buffers not reserved for this size");

@@ -279,6 +279,7 @@ struct srbe_ctx {
   srbe::Lattice lat;                           // lattice electrode path (Eqs. 15, 24 separated per layer)
   bool dense = true;                           // dense A / projected inverse exist
   bool lat_solve = false;                      // charge update through the spectral form of A
+  int sf_occ = 8;                              // structure factor: blocks per SM its chunking keeps (tile)
 
   // Langevin thermostat (Eq. 39): collision rate (1/ps, 0 = off), temperature (K), noise seed
   double lang_gamma = 0.0, lang_T = 0.0;
@@ -441,7 +442,7 @@ void charge_residual(srbe_ctx *c, double *out_dev);
 void phase_begin(srbe_ctx *c, int ph);
 void phase_end(srbe_ctx *c, int ph);
 void reserve(srbe_ctx *c);
-int64_t sfac_chunks(int64_t n, int K, int64_t *chunk);
+int64_t sfac_chunks(int64_t n, int K, int occ, int64_t *chunk);
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 

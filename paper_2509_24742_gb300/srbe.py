@@ -95,6 +95,8 @@ EXPORTS = {
     "srbe_get_skin": ([_vp], _dbl),
     "srbe_get_alpha_A": ([_vp], _dbl),
     "srbe_autotune_skin": ([_vp, _int, _u64, _dp, _int, _dp], _int),
+    "srbe_autotune_tiles": ([_vp, _int, _u64, ctypes.POINTER(_int), _int, _dp], _int),
+    "srbe_get_tiles": ([_vp], _int),
     "srbe_batch_create": ([_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _int),
     "srbe_batch_destroy": ([_vp], _int),
     "srbe_batch_last_error": ([_vp], ctypes.c_char_p),
@@ -103,6 +105,7 @@ EXPORTS = {
     "srbe_batch_stream": ([_vp], _vp),
     "srbe_batch_step": ([_vp, _int, ctypes.POINTER(_u64), _dp], _int),
     "srbe_batch_autotune": ([_vp, _int, ctypes.POINTER(_u64), ctypes.POINTER(_int), _int, _dp], _int),
+    "srbe_batch_autotune_tiles": ([_vp, _int, ctypes.POINTER(_u64), ctypes.POINTER(_int), _int, _dp], _int),
 }
 PHASES = ("upload", "cells", "S1", "rhs", "solve", "S2", "forces", "integrate", "energy", "forces_ii")
 
@@ -431,6 +434,18 @@ class Context:
         self._check(self.lib.srbe_autotune_skin(self.h, int(trial_steps), int(seed), _ptr(sk), sk.size, _ptr(ms)))
         return dict(zip(sk.tolist(), ms.tolist()))
 
+    def autotune_tiles(self, trial_steps, seed, occ=(2, 4, 8, 16)):
+        """Times each candidate structure-factor tile (blocks per SM its chunking keeps), keeps the
+        fastest; returns {occ: ms per step}."""
+        o = np.ascontiguousarray(occ, dtype=np.int32)
+        ms = np.zeros(o.size)
+        self._check(self.lib.srbe_autotune_tiles(self.h, int(trial_steps), int(seed),
+                                                 o.ctypes.data_as(ctypes.POINTER(_int)), o.size, _ptr(ms)))
+        return dict(zip(o.tolist(), ms.tolist()))
+
+    def tiles(self):
+        return self.lib.srbe_get_tiles(self.h)
+
 
 class Batch:
     """Many replicas (Contexts) stepped as one CUDA graph launch per step; the contexts are borrowed
@@ -501,6 +516,16 @@ class Batch:
         self._check(self.lib.srbe_batch_autotune(self.h, int(trial_steps), sp,
                                                  w.ctypes.data_as(ctypes.POINTER(_int)), w.size, _ptr(ms)))
         return dict(zip(w.tolist(), ms.tolist()))
+
+    def autotune_tiles(self, trial_steps, seeds, occ=(2, 4, 8, 16)):
+        """Times each candidate structure-factor tile for every replica at once, keeps the fastest;
+        returns {occ: ms per batch step}."""
+        o = np.ascontiguousarray(occ, dtype=np.int32)
+        ms = np.zeros(o.size)
+        s, sp = self._seeds(seeds)
+        self._check(self.lib.srbe_batch_autotune_tiles(self.h, int(trial_steps), sp,
+                                                       o.ctypes.data_as(ctypes.POINTER(_int)), o.size, _ptr(ms)))
+        return dict(zip(o.tolist(), ms.tolist()))
 
 
 def structure_factor_noalloc(box, n, r_ptr, w_ptr, K, m_ptr, S_ptr, stream_ptr=None):

@@ -1,6 +1,7 @@
 """GPU tests of the batching form through the C ABI: many uneven replicas stepped as one CUDA
 graph launch per step reproduce, bitwise, each replica stepped on its own; the FP64 residual check
-of the constant-potential conditions; the stream-width and Verlet-skin autotuners restore state."""
+of the constant-potential conditions; the stream-width, Verlet-skin and structure-factor tile
+autotuners restore state."""
 import numpy as np
 import pytest
 
@@ -106,6 +107,37 @@ def test_autotuners_restore_state_and_pick_a_candidate():
         d[:, :2] -= L * np.round(d[:, :2] / L)
         assert np.abs(d).max() < 1e-9
         assert np.abs(v1 - v0).max() < 1e-7
+
+
+def test_tile_autotuners_restore_state_and_keep_the_fastest():
+    """The structure-factor tile (blocks per SM its chunking keeps) picked by timing, for a batch and
+    for one context: every candidate is timed, the fastest is kept, the MD state is restored, and the
+    tile changes the forces only by summation order."""
+    slabs = _replicas()
+    ctxs = _contexts(slabs)
+    with srbe.Batch(ctxs) as b:
+        b.step(1, SEEDS)
+        before = _state(ctxs)
+        t = b.autotune_tiles(2, SEEDS, occ=(1, 4, 16))
+        assert set(t) == {1, 4, 16} and all(v > 0 for v in t.values())
+        assert all(c.tiles() == min(t, key=t.get) for c in ctxs)
+        for (r0, v0), (r1, v1) in zip(before, _state(ctxs)):
+            assert np.array_equal(r0, r1) and np.array_equal(v0, v1)
+        one = ctxs[1].autotune_tiles(2, SEEDS[1], occ=(2, 8))
+        assert set(one) == {2, 8} and ctxs[1].tiles() == min(one, key=one.get)
+        res = b.step(2, SEEDS, residuals=True)
+        assert np.all(res < 1e-8)
+    # the FP64 replica's forces at the extreme tiles, same state and modes
+    c = ctxs[0]
+    F = {}
+    for occ in (1, 16):
+        c.autotune_tiles(1, SEEDS[0], occ=(occ,))
+        assert c.tiles() == occ
+        c.sample_k(SEEDS[0], 7)
+        F[occ] = c.forces()[0]
+    assert np.linalg.norm(F[1] - F[16]) <= 1e-12 * np.linalg.norm(F[16])
+    for c in ctxs:
+        c.close()
 
 
 def test_batch_errors():
