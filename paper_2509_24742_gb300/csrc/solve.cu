@@ -674,28 +674,13 @@ __device__ void grid_gemv(const PcgArgs &a, const double *x, const double *v, do
   }
 }
 
-// out = v - A x (minus = true) or A x, rows grid-strided over warps (the FP64 form's k_pcg)
-__device__ void grid_gemv_rows(const PcgArgs &a, const double *x, const double *v, double *out, bool minus) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = gw; row < a.n; row += nw) {
-    const double *Ar = a.A + row * a.n;
-    double acc = 0.0;
-    for (int64_t j = lane; j < a.n; j += 32) acc = fma(__ldcs(Ar + j), __ldcg(x + j), acc);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[row] = minus ? v[row] - acc : acc;
-  }
-}
-
 __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   cg::grid_group grid = cg::this_grid();
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
   // v = dpsi d + b lives in p for the first product; r = v - A y
   for (int64_t i = gt; i < a.n; i += gs) a.p[i] = fma(a.dpsi, a.d[i], a.b[i]);
   grid.sync();
-  grid_gemv_rows(a, a.y, a.p, a.r, true);
+  grid_gemv(a, a.y, a.p, a.r, true);
   grid.sync();
   double vv = 0.0, rz = 0.0, rr = 0.0;
   for (int64_t i = gt; i < a.n; i += gs) {
@@ -715,7 +700,7 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   grid.sync();
   int it = 0;
   while (it < a.maxit && rr > a.tol2 * vv) {
-    grid_gemv_rows(a, a.p, nullptr, a.Ap, false);
+    grid_gemv(a, a.p, nullptr, a.Ap, false);
     grid.sync();
     double pap = 0.0;
     for (int64_t i = gt; i < a.n; i += gs) pap += a.p[i] * a.Ap[i];
@@ -743,7 +728,7 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs a) {
   // true residual, neutrality projection and psi_bar (Eqs. 9-10)
   for (int64_t i = gt; i < a.n; i += gs) a.z[i] = fma(a.dpsi, a.d[i], a.b[i]);
   grid.sync();
-  grid_gemv_rows(a, a.y, a.z, a.r, true);
+  grid_gemv(a, a.y, a.z, a.r, true);
   grid.sync();
   double r2 = 0.0, ey = 0.0;
   for (int64_t i = gt; i < a.n; i += gs) {
