@@ -934,17 +934,23 @@ __device__ __forceinline__ int build_list(const NbrKernelArgs &a, const int4 *ru
       const int ix = image_x(code), iy = image_y(code);
       const float sx = (float)ix * Lxf, sy = (float)iy * Lyf;
       const bool zero_image = ix == 0 && iy == 0;
-      for (int base = b0; base < b1; base += 32) {
-        const int pp = base + lane;
-        bool in = false;
-        int32_t excl = 0;
-        if (pp < b1 && !(zero_image && pp == self)) {
-          const float4 o = pf[pp];
-          const float dx = X - (o.x + sx), dy = Y - (o.y + sy), dz = Z - o.z;
-          in = dx * dx + dy * dy + dz * dz < a.cut2;
-          if (in && ms && ms[pp] == mol) excl = kListExcl;
-        }
-        warp_append(list, a.cap, count, in, list_entry(pp, ix, iy) | excl, lane);
+      // two batches of 32 candidates per pass, both loads issued before either test (the entries
+      // are appended in candidate order, as one batch at a time would)
+      for (int base = b0; base < b1; base += 64) {
+        const int pa = base + lane, pb = base + 32 + lane;
+        const bool va = pa < b1 && !(zero_image && pa == self), vb = pb < b1 && !(zero_image && pb == self);
+        const float4 oa = va ? pf[pa] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 ob = vb ? pf[pb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float dx = X - (oa.x + sx), dy = Y - (oa.y + sy), dz = Z - oa.z;
+        const bool ina = va && dx * dx + dy * dy + dz * dz < a.cut2;
+        dx = X - (ob.x + sx);
+        dy = Y - (ob.y + sy);
+        dz = Z - ob.z;
+        const bool inb = vb && dx * dx + dy * dy + dz * dz < a.cut2;
+        const int32_t exa = ina && ms && ms[pa] == mol ? kListExcl : 0;
+        const int32_t exb = inb && ms && ms[pb] == mol ? kListExcl : 0;
+        warp_append(list, a.cap, count, ina, list_entry(pa, ix, iy) | exa, lane);
+        if (base + 32 < b1) warp_append(list, a.cap, count, inb, list_entry(pb, ix, iy) | exb, lane);
       }
     }
   }
