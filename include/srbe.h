@@ -259,9 +259,12 @@ int srbe_get_phase_times(srbe_ctx *ctx, double *ms, int64_t *count);
  * more; beyond 16,384 sites it is the only solver (A is not stored densely), otherwise
  * SRBE_SOLVER_DIRECT is the default.  Errors: SRBE_ESTATE for a solver the electrode cannot use. */
 /* In the mixed form PCG runs as iterative refinement: the FP64 residual dpsi d + b - A y decides
- * convergence (tol as above), and each correction comes from Jacobi-PCG on an FP32 copy of A (formed
- * once per electrode; half the bytes per product) run until its residual has fallen by 1e-4; maxit
- * bounds these inner iterations, which srbe_get_solver_stats counts.
+ * convergence (tol as above), and each correction comes from Jacobi-preconditioned CG on an FP32 copy
+ * of A (formed once per electrode; half the bytes per product), in the Chronopoulos-Gear arrangement
+ * (one grid-wide reduction per iteration), run until its residual has fallen by 1e-4; maxit bounds
+ * these inner iterations, which srbe_get_solver_stats counts.  The inner sums are FP32, so the
+ * iteration count can differ by a few between builds that group them differently; the FP64 residual
+ * bar does not.
  * A PCG solve that reaches maxit above tol raises SRBE_ENOTCONV (see srbe_synchronize); the same pass
  * then takes its charges from the direct projected inverse (one extra kernel that runs only in that
  * case), so the forces and the MD step that follow use converged charges. */
