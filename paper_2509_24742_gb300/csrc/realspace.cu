@@ -1284,9 +1284,9 @@ __device__ __forceinline__ double widen_f32(float f) {
   return (double)f;
 }
 
-// PART (mixed form without energies only): 0 the whole force; 1 the ion-ion pairs and bonds alone
-// into Fii (sorted order; they need neither Q nor S, so they run beside b, the solve and S2);
-// 2 everything else, plus Fii
+// PART 0: the whole force.  PART 2 (mixed form without energies): everything but the ion-ion pairs
+// and bonds, plus Fii, their forces from k_ion_ii (sorted order; they need neither Q nor S, so that
+// pass runs beside b, the solve and S2)
 template <bool F32, bool EN, int PART>
 __global__ void __launch_bounds__(kGatherThreads)
 k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double *__restrict__ Q,
@@ -1296,8 +1296,8 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
              double3 invL, float3 kvf, double Lx, double Ly, double alpha, double eta, double rc, double slab,
              ForceF32 pf, const double *__restrict__ scal, MdDev md, const double *__restrict__ x_orig,
              const double *__restrict__ y_orig, const double *__restrict__ z_orig, double *__restrict__ F,
-             double *__restrict__ epart, float4 *__restrict__ Fii) {
-  static_assert(PART == 0 || (F32 && !EN), "the split force passes are the mixed form's, without energies");
+             double *__restrict__ epart, const float4 *__restrict__ Fii) {
+  static_assert(PART == 0 || (PART == 2 && F32 && !EN), "the split force pass is the mixed form's, without energies");
   __shared__ double red[kWarpsPerBlock][4];
   __shared__ int2 wq[kWarpsPerBlock][64];
   __shared__ float2 ljs[kMaxLjTypes * kMaxLjTypes];
@@ -1308,7 +1308,7 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
   if (F32) {
     for (int t = threadIdx.x; t < md.ntype * md.ntype; t += blockDim.x) ljs[t] = md.lj32[t];
     // M_z (an FP64 sum over all charges) in FP32, once per block
-    if (PART != 1 && threadIdx.x == 0) s_mz = (float)(scal[kScalMion] + scal[kScalMele]);
+    if (threadIdx.x == 0) s_mz = (float)(scal[kScalMion] + scal[kScalMele]);
   }
   __syncthreads();
   if (p < ni) {
@@ -1323,9 +1323,7 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     // ---- k-space gather
     double fk[3] = {0, 0, 0};
     float ak0 = 0.f, ak1 = 0.f, ak2 = 0.f;
-    if (PART == 1) {
-      // no k-space part in the ion-ion pass
-    } else if (!F32) {
+    if (!F32) {
       for (int k = lane; k < K; k += 32) {
         const int4 m = __ldg(&modes[k]);
         double cs, sn;
@@ -1364,7 +1362,7 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     // Verlet lists; a particle whose list overflowed walks the stencil of its build cell instead
     const int nii = nl.ii_n[p], nie = nl.ie_n[p];
     if (PART == 2) {
-      // the ion-ion pairs came from the PART 1 pass
+      // the ion-ion pairs came from k_ion_ii
     } else if (F32 && nii <= nl.cap)
       ii_list_f32<EN>(S, ions, md, ljs, nl.ii + p * nl.cap, nii, cut2, lane, A);
     else if (nii <= nl.cap)
@@ -1373,9 +1371,7 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
     else
       compacted_pairs(S, ions, nl.cell_s[p], true, cut2, q, lane,
                       [&](int2 e) { pair_ion_ion<F32, EN>(S, ions, md, e, A); });
-    if (PART == 1) {
-      // the ion-electrode pairs wait for Q
-    } else if (F32 && nie <= nl.cap)
+    if (F32 && nie <= nl.cap)
       ie_list_f32<EN>(S, eles, md, ljs, Q32, nl.ie + p * nl.cap, nie, cut2, lane, A);
     else if (nie <= nl.cap)
       compacted_list(S, eles, nl.ie + p * nl.cap, nie, cut2, q, lane,
@@ -1394,19 +1390,16 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
       // reduction over all charges) enters from FP64
       float v[6] = {ak0, ak1, ak2, A.f0, A.f1, A.f2};
 #pragma unroll
-      for (int d = (PART == 1 ? 3 : 0); d < 6; ++d) v[d] = warp_sum_f(v[d]);
+      for (int d = 0; d < 6; ++d) v[d] = warp_sum_f(v[d]);
       if (EN) {
         eii = warp_sum_f(eii);
         eie = warp_sum_f(eie);
         elj = warp_sum_f(elj);
       }
       if (lane == 0) {
-        float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-        if (PART != 1) {
-          Fx = -qf * kvf.x * v[0];
-          Fy = -qf * kvf.y * v[1];
-          Fz = -qf * kvf.z * v[2] - pf.slab * qf * s_mz;
-        }
+        const float Fx = -qf * kvf.x * v[0];
+        const float Fy = -qf * kvf.y * v[1];
+        const float Fz = -qf * kvf.z * v[2] - pf.slab * qf * s_mz;
         float bx = 0.f, by = 0.f, bz = 0.f, eb = 0.f;
         if (PART != 2 && md.ntype && md.bond_start) {
           const float Lxf = pf.Lx, Lyf = pf.Ly, kbf = pf.kb;
@@ -1425,18 +1418,14 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
           }
         }
         const float ke = (float)kKe;
-        if (PART == 1) {
-          Fii[p] = make_float4(v[3] + bx, v[4] + by, v[5] + bz, 0.f);
-        } else {
-          if (PART == 2) {
-            bx = fii_p.x;
-            by = fii_p.y;
-            bz = fii_p.z;
-          }
-          F[i] = widen_f32(ke * Fx + v[3] + bx);
-          F[ni + i] = widen_f32(ke * Fy + v[4] + by);
-          F[2 * ni + i] = widen_f32(ke * Fz + v[5] + bz);
+        if (PART == 2) {
+          bx = fii_p.x;
+          by = fii_p.y;
+          bz = fii_p.z;
         }
+        F[i] = widen_f32(ke * Fx + v[3] + bx);
+        F[ni + i] = widen_f32(ke * Fy + v[4] + by);
+        F[2 * ni + i] = widen_f32(ke * Fz + v[5] + bz);
         e_ii = eii;
         e_ie = eie;
         e_lj = elj;
