@@ -27,6 +27,16 @@ struct KahanF {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// Double-float (hi, lo) addition by Knuth's TwoSum, FP32 instructions only (~2^-48 relative): the
+// mixed form combines its compensated partial sums this way, since on this GPU each FP64 addition
+// holds a sub-partition's FP64 pipe for many cycles and the combines form a serial chain.
+__device__ __forceinline__ float2 df_sum(float2 a, float2 b) {
+  const float s = a.x + b.x, bb = s - a.x, err = (a.x - (s - bb)) + (b.x - bb);
+  const float lo = err + a.y + b.y;
+  const float h = s + lo;
+  return make_float2(h, lo - (h - s));
+}
+
 // Finishes mode k (k < K) or, for k == K, the dipole: lanes take chunks lane, lane + 32, ..., then a
 // butterfly sum (every lane ends with the same value); lane 0 writes S (+ S_add) and the gather
 // coefficients, or the dipole into scal[mslot].  Partials are read through L2 (__ldcg): in the
@@ -143,20 +153,31 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
       }
     }
   }
-  if (F32) {
-    are = fre.value();
-    aim = fim.value();
-  }
-  red[warp][lane] = make_double2(are, aim);
+  // the mixed form keeps each Kahan sum with its compensation as a double-float (s, -c) and adds the
+  // four warps' sums in warp order with FP32 instructions; its partials are (re hi, re lo, im hi,
+  // im lo) in the same 16 bytes as the FP64 form's (re, im)
+  __shared__ float4 red32[4][32];
+  if (F32) red32[warp][lane] = make_float4(fre.s, -fre.c, fim.s, -fim.c);
+  else red[warp][lane] = make_double2(are, aim);
   __syncthreads();
   if (warp == 0 && kidx < K) {
-    double2 a = red[0][lane];
+    if (F32) {
+      float2 re = make_float2(red32[0][lane].x, red32[0][lane].y), im = make_float2(red32[0][lane].z, red32[0][lane].w);
 #pragma unroll
-    for (int q = 1; q < 4; ++q) {
-      a.x += red[q][lane].x;
-      a.y += red[q][lane].y;
+      for (int q = 1; q < 4; ++q) {
+        re = df_sum(re, make_float2(red32[q][lane].x, red32[q][lane].y));
+        im = df_sum(im, make_float2(red32[q][lane].z, red32[q][lane].w));
+      }
+      reinterpret_cast<float4 *>(partial)[(int64_t)blockIdx.x * K + kidx] = make_float4(re.x, re.y, im.x, im.y);
+    } else {
+      double2 a = red[0][lane];
+#pragma unroll
+      for (int q = 1; q < 4; ++q) {
+        a.x += red[q][lane].x;
+        a.y += red[q][lane].y;
+      }
+      partial[(int64_t)blockIdx.x * K + kidx] = a;
     }
-    partial[(int64_t)blockIdx.x * K + kidx] = a;
   }
   if (blockIdx.y == 0) {
     // fixed-order block reduction of sum w z
@@ -179,35 +200,78 @@ k_sfac_partial(int64_t n, const double *__restrict__ x, const double *__restrict
   __threadfence();
   // lane = mode of the tile, warp w takes chunks w, w + 4, ... (coalesced 512-byte rows of the
   // partials), then the four warp sums are added in warp order
-  double2 acc = make_double2(0.0, 0.0);
-  if (kidx < K) {
-    // eight loads in flight per thread before the adds (same order of additions)
-    int c = warp;
-    for (; c + 28 < fin.nchunk; c += 32) {
-      double2 p[8];
+  // the mode's sum over the chunks, in chunk order (lane = mode, warp w takes chunks w, w + 4, ...,
+  // then the four warp sums in warp order), held by warp 0 as (re, im)
+  double re = 0.0, im = 0.0;
+  if (F32) {
+    // double-float sums, FP32 instructions only; one conversion to FP64 per mode
+    float2 dre = make_float2(0.f, 0.f), dim = make_float2(0.f, 0.f);
+    if (kidx < K) {
+      const float4 *p32 = reinterpret_cast<const float4 *>(partial);
+      int c = warp;
+      for (; c + 28 < fin.nchunk; c += 32) {
+        float4 p[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) p[u] = __ldcg(partial + (int64_t)(c + 4 * u) * K + kidx);
+        for (int u = 0; u < 8; ++u) p[u] = __ldcg(p32 + (int64_t)(c + 4 * u) * K + kidx);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        acc.x += p[u].x;
-        acc.y += p[u].y;
+        for (int u = 0; u < 8; ++u) {
+          dre = df_sum(dre, make_float2(p[u].x, p[u].y));
+          dim = df_sum(dim, make_float2(p[u].z, p[u].w));
+        }
+      }
+      for (; c < fin.nchunk; c += 4) {
+        const float4 p = __ldcg(p32 + (int64_t)c * K + kidx);
+        dre = df_sum(dre, make_float2(p.x, p.y));
+        dim = df_sum(dim, make_float2(p.z, p.w));
       }
     }
-    for (; c < fin.nchunk; c += 4) {
-      const double2 p = __ldcg(partial + (int64_t)c * K + kidx);
-      acc.x += p.x;
-      acc.y += p.y;
+    red32[warp][lane] = make_float4(dre.x, dre.y, dim.x, dim.y);
+    __syncthreads();
+    if (warp == 0 && kidx < K) {
+      float2 sre = make_float2(red32[0][lane].x, red32[0][lane].y);
+      float2 sim = make_float2(red32[0][lane].z, red32[0][lane].w);
+#pragma unroll
+      for (int q = 1; q < 4; ++q) {
+        sre = df_sum(sre, make_float2(red32[q][lane].x, red32[q][lane].y));
+        sim = df_sum(sim, make_float2(red32[q][lane].z, red32[q][lane].w));
+      }
+      re = (double)sre.x + (double)sre.y;
+      im = (double)sim.x + (double)sim.y;
+    }
+  } else {
+    double2 acc = make_double2(0.0, 0.0);
+    if (kidx < K) {
+      // eight loads in flight per thread before the adds (same order of additions)
+      int c = warp;
+      for (; c + 28 < fin.nchunk; c += 32) {
+        double2 p[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) p[u] = __ldcg(partial + (int64_t)(c + 4 * u) * K + kidx);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          acc.x += p[u].x;
+          acc.y += p[u].y;
+        }
+      }
+      for (; c < fin.nchunk; c += 4) {
+        const double2 p = __ldcg(partial + (int64_t)c * K + kidx);
+        acc.x += p.x;
+        acc.y += p.y;
+      }
+    }
+    red[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && kidx < K) {
+      re = red[0][lane].x;
+      im = red[0][lane].y;
+#pragma unroll
+      for (int q = 1; q < 4; ++q) {
+        re += red[q][lane].x;
+        im += red[q][lane].y;
+      }
     }
   }
-  red[warp][lane] = acc;
-  __syncthreads();
   if (warp == 0 && kidx < K) {
-    double re = red[0][lane].x, im = red[0][lane].y;
-#pragma unroll
-    for (int q = 1; q < 4; ++q) {
-      re += red[q][lane].x;
-      im += red[q][lane].y;
-    }
     if (fin.S_add) {
       re += fin.S_add[kidx].x;
       im += fin.S_add[kidx].y;
