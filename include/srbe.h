@@ -346,11 +346,12 @@ int srbe_autotune_skin(srbe_ctx *ctx, int trial_steps, uint64_t seed, const doub
  * blocks to hide latency with).  Default occ = 8.  Results do not depend on it beyond summation
  * order.  srbe_autotune_tiles times trial_steps MD steps (after two untimed ones) for each candidate
  * occ (1..64), restores the state after each trial as srbe_autotune_skin does, keeps the fastest and
- * writes the per-candidate ms per step to ms_per_step (n_occ entries, or NULL); srbe_get_tiles gives
- * the setting in use.  Errors: SRBE_EINVAL (no candidates, occ out of range, trial_steps < 1),
- * SRBE_ESTATE (no MD state). */
+ * writes the per-candidate ms per step to ms_per_step (n_occ entries, or NULL); srbe_set_tiles sets
+ * it directly and srbe_get_tiles gives the setting in use.  Errors: SRBE_EINVAL (no candidates, occ
+ * out of range, trial_steps < 1), SRBE_ESTATE (no MD state, srbe_autotune_tiles only). */
 int srbe_autotune_tiles(srbe_ctx *ctx, int trial_steps, uint64_t seed, const int *occ, int n_occ,
                         double *ms_per_step);
+int srbe_set_tiles(srbe_ctx *ctx, int occ);
 int srbe_get_tiles(const srbe_ctx *ctx);
 
 /* A batch steps many independent replicas (contexts of any size, electrode, voltage, precision,

@@ -2569,6 +2569,13 @@ int srbe_autotune_tiles(srbe_ctx *c, int trial_steps, uint64_t seed, const int *
 
 int srbe_get_tiles(const srbe_ctx *c) { return c ? c->sf_occ : 0; }
 
+int srbe_set_tiles(srbe_ctx *c, int occ) {
+  return guarded(c, [&] {
+    SRBE_REQUIRE(occ >= 1 && occ <= 64, SRBE_EINVAL, "blocks per SM out of [1, 64]");
+    c->sf_occ = occ;                 // the next pass sizes the partial sums for it (reserve)
+  });
+}
+
 int srbe_batch_autotune(srbe_batch *b, int trial_steps, const uint64_t *seeds, const int *widths, int n_widths,
                         double *ms_per_step) {
   return batch_guarded(b, [&] {

@@ -97,6 +97,7 @@ EXPORTS = {
     "srbe_autotune_skin": ([_vp, _int, _u64, _dp, _int, _dp], _int),
     "srbe_autotune_tiles": ([_vp, _int, _u64, ctypes.POINTER(_int), _int, _dp], _int),
     "srbe_get_tiles": ([_vp], _int),
+    "srbe_set_tiles": ([_vp, _int], _int),
     "srbe_batch_create": ([_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp)], _int),
     "srbe_batch_destroy": ([_vp], _int),
     "srbe_batch_last_error": ([_vp], ctypes.c_char_p),
@@ -445,6 +446,10 @@ class Context:
 
     def tiles(self):
         return self.lib.srbe_get_tiles(self.h)
+
+    def set_tiles(self, occ):
+        """Blocks per SM the structure factor's particle chunking keeps (1..64, default 8)."""
+        self._check(self.lib.srbe_set_tiles(self.h, int(occ)))
 
 
 class Batch:

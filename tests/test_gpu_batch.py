@@ -131,11 +131,13 @@ def test_tile_autotuners_restore_state_and_keep_the_fastest():
     c = ctxs[0]
     F = {}
     for occ in (1, 16):
-        c.autotune_tiles(1, SEEDS[0], occ=(occ,))
+        c.set_tiles(occ)
         assert c.tiles() == occ
         c.sample_k(SEEDS[0], 7)
         F[occ] = c.forces()[0]
     assert np.linalg.norm(F[1] - F[16]) <= 1e-12 * np.linalg.norm(F[16])
+    with pytest.raises(srbe.SrbeError):
+        c.set_tiles(0)
     for c in ctxs:
         c.close()
 
