@@ -1303,7 +1303,13 @@ k_ion_forces(int64_t ni, CellsDev ions, CellsDev eles, ListsDev nl, const double
   __shared__ float2 ljs[kMaxLjTypes * kMaxLjTypes];
   __shared__ float s_mz;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  // blocks take their groups of 8 ions alternately from the two ends of the sorted order: the ions
+  // next to the electrode walls (long ion-electrode lists) sit at both ends (cells are z-major), so
+  // both walls' groups start early instead of the far wall's ending the launch (each ion's result
+  // does not depend on which block computes it)
+  const int64_t bq = blockIdx.x >> 1;
+  const int64_t bg = (blockIdx.x & 1) ? (int64_t)gridDim.x - 1 - bq : bq;
+  const int64_t p = bg * kWarpsPerBlock + warp;
   double e_ii = 0, e_ie = 0, e_lj = 0, e_b = 0;
   if (F32) {
     for (int t = threadIdx.x; t < md.ntype * md.ntype; t += blockDim.x) ljs[t] = md.lj32[t];
