@@ -94,6 +94,30 @@ def test_mixed_form_error_against_oracle(slab, one):
     assert res < 1e-10
 
 
+def test_mixed_structure_factors_and_dipole_at_the_gpu_charges(orc, slab, ref, one):
+    """The mixed form's structure factors (Eq. 15 over the ions and over the electrode sites) and
+    dipole: the Fourier energy U_F = 1/2 sum_k c_k |S1 + S2|^2 and the slab energy 2 pi M_z^2 / V (M_z
+    over ions and electrodes) match the oracle's for the charges the GPU produced, and the forces match
+    the oracle's forces for those charges; repeated passes give the same bits, and the benchmark's
+    split force pass agrees with the single pass."""
+    samples, _ = one
+    with srbe.from_slab(slab, precision=srbe.MIXED, alpha_A=ALPHA_A, md=True) as ctx:
+        ctx.set_k(samples)
+        F, Q, psi, E = ctx.forces(energy=True)
+        F2, Q2, psi2, E2 = ctx.forces(energy=True)
+        F3, Q3, psi3 = ctx.forces()                # the split force pass of the benchmark
+    m, c = ref.modes(samples)
+    ev = orc.evaluate(slab, ref.factor, m, c, Q_fixed=Q)
+    e_uf = abs(E[3] / ev["E"][3] - 1)
+    e_us = abs(E[5] / ev["E"][5] - 1)
+    ef = rms(F, ev["F"])
+    print("mixed form at the GPU charges: U_F rel err %.2e, U_slab rel err %.2e, RMS force err at the GPU's charges %.2e" % (e_uf, e_us, ef))
+    assert e_uf < 1e-5 and e_us < 1e-9
+    assert ef < 1e-4
+    assert np.array_equal(F, F2) and np.array_equal(Q, Q2) and np.array_equal(E, E2)
+    assert np.array_equal(Q, Q3) and rms(F3, F) < 1e-6
+
+
 @pytest.mark.parametrize("precision", [srbe.FP64, srbe.MIXED])
 def test_md_steps_match_oracle_at_the_benchmark_system(slab, trajectory, precision):
     r_ref, v_ref, F_ref, Q_ref = trajectory
